@@ -1,0 +1,214 @@
+"""The checks that pin the reference codec to things other than itself.
+
+Each function raises AssertionError when the codec under test disagrees with:
+  * the hand-derived fixtures in tests/golden/ (paper Section 3 boundaries and rules),
+  * CPython's strict ``utf-8`` / ``utf-16-le`` codecs (an independent library decoder),
+  * the brute-force second formulation in tests/helpers/bruteforce.c, or
+  * closed forms of the length formulas.
+They take the codec and the brute-force library as arguments so that the mutation test can
+run the same battery against deliberately broken copies of the codec.
+"""
+from __future__ import annotations
+
+import os
+
+import numpy as np
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+def _rows(name):
+    with open(os.path.join(GOLDEN, name)) as f:
+        for line in f:
+            line = line.strip()
+            if not line or line.startswith("#"):
+                continue
+            yield [c.strip() for c in line.split("|")]
+
+
+def golden_scalars():
+    out = []
+    for cp, b8, w16, _why in _rows("utf8_utf16_scalars.txt"):
+        cp = int(cp[2:], 16)
+        u8 = bytes(int(x, 16) for x in b8.split())
+        u16 = np.array([int(x, 16) for x in w16.split()], dtype=np.uint16)
+        out.append((cp, u8, u16))
+    return out
+
+
+def golden_invalid(name, width):
+    out = []
+    for data, kind, off, _why in _rows(name):
+        vals = [int(x, 16) for x in data.split()]
+        arr = np.array(vals, dtype=np.uint8 if width == 8 else np.uint16)
+        out.append((arr, kind, int(off)))
+    return out
+
+
+def check_golden(codec):
+    scal = golden_scalars()
+    assert len(scal) >= 18
+    for cp, u8, u16 in scal:
+        # the fixture itself agrees with CPython
+        assert chr(cp).encode("utf-8") == u8, hex(cp)
+        assert chr(cp).encode("utf-16-le") == u16.tobytes(), hex(cp)
+        assert codec.validate_utf8(u8) == ("OK", len(u8)), hex(cp)
+        assert codec.validate_utf16le(u16) == ("OK", len(u16)), hex(cp)
+        assert codec.utf16_length_from_utf8(u8) == len(u16), hex(cp)
+        assert codec.utf8_length_from_utf16le(u16) == len(u8), hex(cp)
+        r, d = codec.convert_utf8_to_utf16le(u8)
+        assert r == ("OK", len(u16)) and np.array_equal(d, u16), hex(cp)
+        r, d = codec.convert_utf16le_to_utf8(u16)
+        assert r == ("OK", len(u8)) and d.tobytes() == u8, hex(cp)
+    # all the fixture's characters in one string, then cut at every capacity
+    all8 = b"".join(s[1] for s in scal)
+    all16 = np.concatenate([s[2] for s in scal])
+    r, d = codec.convert_utf8_to_utf16le(all8)
+    assert r == ("OK", all16.size) and np.array_equal(d, all16)
+    for cap in range(all16.size):
+        r, d = codec.convert_utf8_to_utf16le(all8, cap)
+        assert r == ("OUTPUT_TOO_SMALL", all16.size) and np.array_equal(d, all16[:cap])
+    for cap in range(len(all8)):
+        r, d = codec.convert_utf16le_to_utf8(all16, cap)
+        assert r == ("OUTPUT_TOO_SMALL", len(all8)) and d.tobytes() == all8[:cap]
+
+    for arr, kind, off in golden_invalid("utf8_invalid.txt", 8):
+        assert codec.validate_utf8(arr) == (kind, off), arr.tobytes().hex()
+        r, _ = codec.convert_utf8_to_utf16le(arr, 16)
+        assert r == (kind, off), arr.tobytes().hex()
+        # CPython's strict decoder reports the same first offset
+        try:
+            arr.tobytes().decode("utf-8")
+            raise AssertionError("CPython accepted " + arr.tobytes().hex())
+        except UnicodeDecodeError as e:
+            assert e.start == off, arr.tobytes().hex()
+    for arr, kind, off in golden_invalid("utf16_invalid.txt", 16):
+        assert codec.validate_utf16le(arr) == (kind, off), arr
+        r, _ = codec.convert_utf16le_to_utf8(arr, 16)
+        assert r == (kind, off), arr
+        try:
+            arr.tobytes().decode("utf-16-le")
+            raise AssertionError("CPython accepted %r" % arr)
+        except UnicodeDecodeError as e:
+            assert e.start == 2 * off, arr
+
+
+def all_scalars():
+    cps = np.concatenate([np.arange(0, 0xD800), np.arange(0xE000, 0x110000)]).astype(np.uint32)
+    assert cps.size == 1_112_064
+    return cps
+
+
+def check_all_scalars(codec):
+    """Round trip of every Unicode scalar value against CPython's encoders."""
+    cps = all_scalars()
+    s = cps.astype("<u4").tobytes().decode("utf-32-le")
+    u8 = np.frombuffer(s.encode("utf-8"), dtype=np.uint8)
+    u16 = np.frombuffer(s.encode("utf-16-le"), dtype=np.uint16)
+    assert codec.validate_utf8(u8) == ("OK", u8.size)
+    assert codec.validate_utf16le(u16) == ("OK", u16.size)
+    assert codec.utf16_length_from_utf8(u8) == u16.size
+    assert codec.utf8_length_from_utf16le(u16) == u8.size
+    r, d = codec.convert_utf8_to_utf16le(u8)
+    assert r == ("OK", u16.size)
+    assert np.array_equal(d, u16)
+    r, d = codec.convert_utf16le_to_utf8(u16)
+    assert r == ("OK", u8.size)
+    assert np.array_equal(d, u8)
+    # per-character sizes (Section 3): 1 byte below U+80, 2 below U+800, 3 below U+10000, else 4
+    sizes = np.where(cps < 0x80, 1, np.where(cps < 0x800, 2, np.where(cps < 0x10000, 3, 4)))
+    assert int(sizes.sum()) == u8.size
+
+
+def check_bruteforce(bf, max_len=3):
+    """Every UTF-8 string of 1..max_len bytes against the second formulation."""
+    assert bf.mixed_dead_prefixes() == 0
+    for n in range(1, max_len + 1):
+        mism, stats = bf.utf8(n, nthreads=os.cpu_count() or 4, roundtrip=True)
+        assert mism == 0, (n, mism, bytes(int(x) for x in stats[9:9 + int(stats[13])]).hex())
+    # known totals: valid one-byte strings are the 128 ASCII bytes; two-byte strings are
+    # ASCII pairs (128^2) plus two-byte characters (30 leads C2-DF x 64 continuations)
+    _, s1 = bf.utf8(1, 1, False)
+    _, s2 = bf.utf8(2, 1, False)
+    assert s1[0] == 128
+    assert s2[0] == 128 * 128 + 30 * 64
+
+
+def check_cpython_offsets(bf, three_byte_leads=range(0xC0, 0x100)):
+    """CPython's first-error offsets on every 1- and 2-byte string and on every 3-byte string
+    whose first byte is in three_byte_leads."""
+    for n in (1, 2):
+        kind, off = bf.table(n)
+        for x in range(1 << (8 * n)):
+            s = bytes((x >> (8 * k)) & 0xFF for k in range(n))
+            try:
+                s.decode("utf-8")
+                ok, start = True, 255
+            except UnicodeDecodeError as e:
+                ok, start = False, e.start
+            assert (kind[x] == 0) == ok, s.hex()
+            assert off[x] == start, s.hex()
+    kind, off = bf.table(3)
+    for b0 in three_byte_leads:
+        for t in range(65536):
+            x = b0 | (t << 8)
+            s = bytes((b0, t & 0xFF, t >> 8))
+            try:
+                s.decode("utf-8")
+                ok, start = True, 255
+            except UnicodeDecodeError as e:
+                ok, start = False, e.start
+            if (kind[x] == 0) != ok or off[x] != start:
+                raise AssertionError(s.hex())
+
+
+def check_utf16_pairs(bf, codec, full=True):
+    if full:
+        mism, stats = bf.utf16_pairs(nthreads=os.cpu_count() or 4)
+        assert mism == 0, hex(int(stats[1]))
+        # valid pairs: two non-surrogates, or a high followed by a low
+        assert stats[0] == (65536 - 2048) ** 2 + 1024 * 1024
+    # CPython on pairs drawn from the boundaries and all surrogate words
+    words = np.array(
+        sorted(set([0, 0x41, 0x7F, 0x80, 0x7FF, 0x800, 0xD7FF, 0xE000, 0xFFFD, 0xFFFF]
+                   + list(range(0xD800, 0xD810)) + list(range(0xDBF0, 0xDC10))
+                   + list(range(0xDFF0, 0xE000)))), dtype=np.uint16)
+    kind, off = bf.utf16_pair_table(words)
+    for i, a in enumerate(words):
+        for j, b in enumerate(words):
+            s = np.array([a, b], dtype=np.uint16).tobytes()
+            try:
+                s.decode("utf-16-le")
+                ok, start = True, 255
+            except UnicodeDecodeError as e:
+                ok, start = False, e.start // 2
+            assert (kind[i, j] == 0) == ok and off[i, j] == start, (hex(a), hex(b))
+    # every valid surrogate pair converts to the scalar CPython decodes it to
+    hi = np.repeat(np.arange(0xD800, 0xDC00, dtype=np.uint16), 1024)
+    lo = np.tile(np.arange(0xDC00, 0xE000, dtype=np.uint16), 1024)
+    pairs = np.stack([hi, lo], axis=1).reshape(-1)
+    r, d = codec.convert_utf16le_to_utf8(pairs)
+    expect = pairs.tobytes().decode("utf-16-le").encode("utf-8")
+    assert r == ("OK", len(expect)) and d.tobytes() == expect
+
+
+def check_length_closed_forms(codec):
+    """Length formulas on strings whose answer is known without decoding."""
+    rng = np.random.default_rng(7)
+    for cp_lo, cp_hi, u8_per, u16_per in [
+        (0x00, 0x80, 1, 1), (0x80, 0x800, 2, 1), (0x800, 0xD800, 3, 1),
+        (0xE000, 0x10000, 3, 1), (0x10000, 0x110000, 4, 2)]:
+        cps = rng.integers(cp_lo, cp_hi, size=1000).astype("<u4")
+        s = cps.tobytes().decode("utf-32-le")
+        u8 = np.frombuffer(s.encode("utf-8"), dtype=np.uint8)
+        u16 = np.frombuffer(s.encode("utf-16-le"), dtype=np.uint16)
+        assert u8.size == 1000 * u8_per and u16.size == 1000 * u16_per
+        assert codec.utf16_length_from_utf8(u8) == 1000 * u16_per
+        assert codec.utf8_length_from_utf16le(u16) == 1000 * u8_per
+    # formulas on arbitrary (invalid) input: one word per non-continuation byte plus one per
+    # byte F0-FF; two bytes per surrogate word
+    junk = np.arange(256, dtype=np.uint8)
+    assert codec.utf16_length_from_utf8(junk) == 256 - 64 + 16
+    sur = np.arange(0xD800, 0xE000, dtype=np.uint16)
+    assert codec.utf8_length_from_utf16le(sur) == 2 * 2048
+    assert codec.utf16_length_from_utf8(b"") == 0 and codec.utf8_length_from_utf16le(b"") == 0
