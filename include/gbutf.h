@@ -1,0 +1,119 @@
+/*
+ * gbutf.h -- C ABI of the GB300 (sm_103a) UTF-8 / UTF-16LE validation and transcoding library.
+ *
+ * The operations are the ones the paper ("Unicode at Gigabytes per Second") sets out to make
+ * fast: validate UTF-8 and UTF-16, and transcode between them, always validating (Section 1
+ * states the problem, Section 3 defines both formats and the six UTF-8 validity rules,
+ * Section 5 states that every transcoding also validates).  The output-length functions give
+ * the exact size of the other encoding (Section 3 per-character sizes).
+ *
+ * Conventions shared by every call:
+ *   - Units.  n, cap, offsets and counts are in code units of the buffer they describe: bytes
+ *     for UTF-8, 16-bit words for UTF-16LE.  Offsets and counts are 64-bit.
+ *   - Memory.  src, dst, len and result pointers are DEVICE pointers owned by the caller
+ *     (result may also be pinned host memory mapped into the device address space).  The
+ *     library never allocates on a call; it only uses the workspace held by the context.
+ *   - Alignment.  uint16_t buffers must be 2-byte aligned; any other alignment is accepted.
+ *   - Streams.  Every call is asynchronous on `stream`; the result is valid once the stream
+ *     has reached the call.  One context serves one stream at a time: calls made through the
+ *     same context on different streams must not overlap (use one context per stream).
+ *   - Return value.  GBU_OK if the work was enqueued, GBU_BAD_ARGUMENT (NULL pointer with
+ *     n > 0, misaligned uint16_t pointer, n beyond the context's capacity) or GBU_CUDA_ERROR
+ *     (the launch failed).  Nothing is enqueued when the return value is not GBU_OK.
+ *   - n == 0 is valid: the result is {GBU_OK, 0}; result is still written (by a tiny kernel).
+ *
+ * Result of a validation or transcoding (gbu_result):
+ *   status GBU_OK            count = n (validation) or code units written (transcoding)
+ *   status 1..6              the input is invalid; count = offset of the first invalid code
+ *                            unit of src (the first unit of the ill-formed sequence)
+ *   status GBU_OUTPUT_TOO_SMALL  the input is valid but needs count > cap output units;
+ *                            dst[0:cap] holds the first cap units of the conversion
+ *   status GBU_TIMEOUT       a device-side wait gave up (see gbu_set_wait_limit); the output
+ *                            and the context's workspace must be considered lost (call
+ *                            gbu_reset before reusing the context)
+ * On an input error, dst[0 : L] holds the conversion of the valid prefix src[0:count], where L
+ * is its output length (clipped to cap); dst beyond L is unspecified but no unit at or past
+ * cap is ever written.  When an input breaks several rules, the kind reported is the one the
+ * bytes read so far break first in reading order: after each byte of a UTF-8 sequence the
+ * values it could still encode form an interval, and the sequence is ill-formed as soon as
+ * that whole interval breaks rule 4, 5 or 6; a missing continuation byte, also at the end of
+ * the buffer, is GBU_TOO_SHORT.
+ */
+#ifndef GBUTF_H
+#define GBUTF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  GBU_OK = 0,
+  GBU_HEADER_BITS = 1,     /* rule 1: a byte whose five most significant bits are all ones */
+  GBU_TOO_SHORT = 2,       /* rule 2: a leading byte without its continuation bytes        */
+  GBU_TOO_LONG = 3,        /* rule 3: a continuation byte with no leading byte             */
+  GBU_OVERLONG = 4,        /* rule 4: a value that a shorter sequence encodes              */
+  GBU_TOO_LARGE = 5,       /* rule 5: a value of 1,114,112 (0x110000) or more              */
+  GBU_SURROGATE = 6,       /* rule 6 in UTF-8 (D800-DFFF); an unpaired UTF-16 surrogate    */
+  GBU_OUTPUT_TOO_SMALL = 16,
+  GBU_BAD_ARGUMENT = 17,
+  GBU_CUDA_ERROR = 18,
+  GBU_TIMEOUT = 19
+} gbu_status;
+
+typedef struct {
+  int32_t status;   /* gbu_status */
+  int32_t reserved; /* 0 */
+  uint64_t count;   /* see above */
+} gbu_result;       /* 16 bytes */
+
+typedef struct gbu_ctx gbu_ctx;
+typedef struct CUstream_st *gbu_stream; /* a cudaStream_t; NULL = the legacy default stream */
+
+/* Creates a context on `device` whose workspace (tile states and counters, allocated once
+ * here) serves inputs of up to max_units code units.  Returns NULL on failure. */
+gbu_ctx *gbu_create(int device, uint64_t max_units);
+/* Frees the context's workspace.  The caller must make sure no work using it is pending. */
+void gbu_destroy(gbu_ctx *ctx);
+/* Re-initialises the workspace (after GBU_TIMEOUT).  Synchronous. */
+int gbu_reset(gbu_ctx *ctx);
+/* Bound on each device-side spin wait, in polling rounds (default 2^22; tests use small
+ * values together with gbu_debug_skip_publish to exercise the timeout path). */
+void gbu_set_wait_limit(gbu_ctx *ctx, uint32_t rounds);
+/* Test hook: the tile with this index never publishes its scan state, so the tiles after it
+ * wait until the limit and the call reports GBU_TIMEOUT.  -1 (default) disables the hook. */
+void gbu_debug_skip_publish(gbu_ctx *ctx, int64_t tile);
+
+/* UTF-8 validation (Section 3, rules 1-6). */
+int gbu_validate_utf8(gbu_ctx *ctx, const uint8_t *src, uint64_t n, gbu_result *result,
+                      gbu_stream stream);
+/* UTF-16LE validation (Section 3: every D800-DBFF word is followed by a DC00-DFFF word and
+ * every DC00-DFFF word follows a D800-DBFF word). */
+int gbu_validate_utf16le(gbu_ctx *ctx, const uint16_t *src, uint64_t n, gbu_result *result,
+                         gbu_stream stream);
+
+/* Output lengths (Section 3 per-character sizes), defined for any input and computed without
+ * validation: UTF-16 words = bytes that are not continuation bytes (10xxxxxx) + bytes F0-FF;
+ * UTF-8 bytes = 1 per word below 0x80, 2 below 0x800, 2 per surrogate word, else 3.  Both are
+ * exact for valid input.  *len is a device uint64_t. */
+int gbu_utf16_length_from_utf8(gbu_ctx *ctx, const uint8_t *src, uint64_t n, uint64_t *len,
+                               gbu_stream stream);
+int gbu_utf8_length_from_utf16le(gbu_ctx *ctx, const uint16_t *src, uint64_t n, uint64_t *len,
+                                 gbu_stream stream);
+
+/* Validating transcoders (Section 3 formats; Section 5: transcoding includes validation).
+ * dst holds cap code units of the output format. */
+int gbu_convert_utf8_to_utf16le(gbu_ctx *ctx, const uint8_t *src, uint64_t n, uint16_t *dst,
+                                uint64_t cap, gbu_result *result, gbu_stream stream);
+int gbu_convert_utf16le_to_utf8(gbu_ctx *ctx, const uint16_t *src, uint64_t n, uint8_t *dst,
+                                uint64_t cap, gbu_result *result, gbu_stream stream);
+
+/* Number of kernel launches the library made through this context so far (for accounting). */
+uint64_t gbu_launch_count(const gbu_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GBUTF_H */

@@ -1,0 +1,11 @@
+"""GB300-native (sm_103a) UTF-8 / UTF-16LE validation and transcoding.
+
+The work runs in the CUDA library built from ``csrc/`` (C ABI: ``include/gbutf.h``);
+``binding`` is a thin ctypes layer over it.
+"""
+from .binding import (  # noqa: F401
+    STATUS, STATUS_CODE, Codec, GbuError, GbuResult, gbu_convert_utf16le_to_utf8,
+    gbu_convert_utf8_to_utf16le, gbu_create, gbu_debug_skip_publish, gbu_destroy,
+    gbu_launch_count, gbu_reset, gbu_set_wait_limit, gbu_utf16_length_from_utf8,
+    gbu_utf8_length_from_utf16le, gbu_validate_utf16le, gbu_validate_utf8, lib, library_path,
+    result_tuple)

@@ -1,0 +1,232 @@
+"""Thin ctypes binding of the C ABI in include/gbutf.h.
+
+The ``gbu_*`` functions mirror the C entry points one to one (pointers and sizes as Python
+ints); ``Codec`` adds argument marshalling for torch tensors.  Every step of the work runs in
+the CUDA library: this module only passes pointers, sizes and stream handles.  If the
+library has not been built, loading fails with an error instead of falling back to anything.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+from . import build as _build
+
+STATUS = {
+    0: "OK", 1: "HEADER_BITS", 2: "TOO_SHORT", 3: "TOO_LONG", 4: "OVERLONG", 5: "TOO_LARGE",
+    6: "SURROGATE", 16: "OUTPUT_TOO_SMALL", 17: "BAD_ARGUMENT", 18: "CUDA_ERROR", 19: "TIMEOUT",
+}
+STATUS_CODE = {v: k for k, v in STATUS.items()}
+
+
+class GbuResult(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("reserved", ctypes.c_int32), ("count", ctypes.c_uint64)]
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB_PATH
+
+
+def lib() -> ctypes.CDLL:
+    """The loaded CUDA library; raises if it was not built (no fallback exists)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.LIB_PATH
+            if not os.path.exists(path):
+                raise RuntimeError(
+                    f"CUDA library {path} is missing: build it with "
+                    "paper_2111_08692_gb300.build.build() (there is no CPU fallback)")
+            L = ctypes.CDLL(path)
+            vp, u64, i32, u32, i64 = (ctypes.c_void_p, ctypes.c_uint64, ctypes.c_int, ctypes.c_uint32,
+                                      ctypes.c_int64)
+            L.gbu_create.restype = vp
+            L.gbu_create.argtypes = [i32, u64]
+            L.gbu_destroy.restype = None
+            L.gbu_destroy.argtypes = [vp]
+            L.gbu_reset.restype = i32
+            L.gbu_reset.argtypes = [vp]
+            L.gbu_set_wait_limit.restype = None
+            L.gbu_set_wait_limit.argtypes = [vp, u32]
+            L.gbu_debug_skip_publish.restype = None
+            L.gbu_debug_skip_publish.argtypes = [vp, i64]
+            L.gbu_launch_count.restype = u64
+            L.gbu_launch_count.argtypes = [vp]
+            for name in ("gbu_validate_utf8", "gbu_validate_utf16le", "gbu_utf16_length_from_utf8",
+                         "gbu_utf8_length_from_utf16le"):
+                f = getattr(L, name)
+                f.restype = i32
+                f.argtypes = [vp, vp, u64, vp, vp]
+            for name in ("gbu_convert_utf8_to_utf16le", "gbu_convert_utf16le_to_utf8"):
+                f = getattr(L, name)
+                f.restype = i32
+                f.argtypes = [vp, vp, u64, vp, u64, vp, vp]
+            _lib = L
+    return _lib
+
+
+# ---- the C entry points, same names -------------------------------------------------------
+
+def gbu_create(device: int, max_units: int) -> int:
+    return lib().gbu_create(device, max_units)
+
+
+def gbu_destroy(ctx: int) -> None:
+    lib().gbu_destroy(ctx)
+
+
+def gbu_reset(ctx: int) -> int:
+    return lib().gbu_reset(ctx)
+
+
+def gbu_set_wait_limit(ctx: int, rounds: int) -> None:
+    lib().gbu_set_wait_limit(ctx, rounds)
+
+
+def gbu_debug_skip_publish(ctx: int, tile: int) -> None:
+    lib().gbu_debug_skip_publish(ctx, tile)
+
+
+def gbu_launch_count(ctx: int) -> int:
+    return int(lib().gbu_launch_count(ctx))
+
+
+def gbu_validate_utf8(ctx, src, n, result, stream) -> int:
+    return lib().gbu_validate_utf8(ctx, src, n, result, stream)
+
+
+def gbu_validate_utf16le(ctx, src, n, result, stream) -> int:
+    return lib().gbu_validate_utf16le(ctx, src, n, result, stream)
+
+
+def gbu_utf16_length_from_utf8(ctx, src, n, length, stream) -> int:
+    return lib().gbu_utf16_length_from_utf8(ctx, src, n, length, stream)
+
+
+def gbu_utf8_length_from_utf16le(ctx, src, n, length, stream) -> int:
+    return lib().gbu_utf8_length_from_utf16le(ctx, src, n, length, stream)
+
+
+def gbu_convert_utf8_to_utf16le(ctx, src, n, dst, cap, result, stream) -> int:
+    return lib().gbu_convert_utf8_to_utf16le(ctx, src, n, dst, cap, result, stream)
+
+
+def gbu_convert_utf16le_to_utf8(ctx, src, n, dst, cap, result, stream) -> int:
+    return lib().gbu_convert_utf16le_to_utf8(ctx, src, n, dst, cap, result, stream)
+
+
+# ---- torch marshalling --------------------------------------------------------------------
+
+class GbuError(RuntimeError):
+    pass
+
+
+def _check(rc: int, what: str):
+    if rc != 0:
+        raise GbuError(f"{what}: {STATUS.get(rc, rc)}")
+
+
+def result_tuple(t) -> tuple[str, int]:
+    """(status name, count) of a result tensor (2 x int64: status word, count)."""
+    v = t.detach().to("cpu").view(-1).tolist()
+    return STATUS.get(int(v[0]) & 0xFFFFFFFF, int(v[0])), int(v[1]) & 0xFFFFFFFFFFFFFFFF
+
+
+class Codec:
+    """One library context on one CUDA device, driven with torch tensors.
+
+    Methods enqueue work on ``stream`` (default: torch's current stream) and return the
+    device tensor that will hold the result; ``result_tuple`` reads it.  One Codec serves one
+    stream at a time (its workspace is shared by its calls)."""
+
+    def __init__(self, device: int | None = None, max_units: int = 1 << 31):
+        import torch
+        self.torch = torch
+        if device is None:
+            device = torch.cuda.current_device()
+        self.device = device
+        self.ctx = gbu_create(device, max_units)
+        if not self.ctx:
+            raise GbuError("gbu_create failed")
+
+    def close(self):
+        if self.ctx:
+            gbu_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # helpers
+    def _stream(self, stream):
+        if stream is None:
+            stream = self.torch.cuda.current_stream(self.device)
+        return stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+
+    def new_result(self):
+        return self.torch.empty(2, dtype=self.torch.int64, device=f"cuda:{self.device}")
+
+    @staticmethod
+    def _ptr(t):
+        return t.data_ptr() if t is not None and t.numel() else 0
+
+    def launches(self) -> int:
+        return gbu_launch_count(self.ctx)
+
+    def set_wait_limit(self, rounds: int):
+        gbu_set_wait_limit(self.ctx, rounds)
+
+    def debug_skip_publish(self, tile: int):
+        gbu_debug_skip_publish(self.ctx, tile)
+
+    def reset(self):
+        _check(gbu_reset(self.ctx), "gbu_reset")
+
+    # operations (tensors are 1-D, contiguous, on this device)
+    def validate_utf8(self, src, result=None, stream=None):
+        result = self.new_result() if result is None else result
+        _check(gbu_validate_utf8(self.ctx, self._ptr(src), src.numel(), result.data_ptr(),
+                                 self._stream(stream)), "gbu_validate_utf8")
+        return result
+
+    def validate_utf16le(self, src, result=None, stream=None):
+        result = self.new_result() if result is None else result
+        _check(gbu_validate_utf16le(self.ctx, self._ptr(src), src.numel(), result.data_ptr(),
+                                    self._stream(stream)), "gbu_validate_utf16le")
+        return result
+
+    def utf16_length_from_utf8(self, src, out=None, stream=None):
+        out = self.torch.empty(1, dtype=self.torch.int64, device=f"cuda:{self.device}") if out is None else out
+        _check(gbu_utf16_length_from_utf8(self.ctx, self._ptr(src), src.numel(), out.data_ptr(),
+                                          self._stream(stream)), "gbu_utf16_length_from_utf8")
+        return out
+
+    def utf8_length_from_utf16le(self, src, out=None, stream=None):
+        out = self.torch.empty(1, dtype=self.torch.int64, device=f"cuda:{self.device}") if out is None else out
+        _check(gbu_utf8_length_from_utf16le(self.ctx, self._ptr(src), src.numel(), out.data_ptr(),
+                                            self._stream(stream)), "gbu_utf8_length_from_utf16le")
+        return out
+
+    def convert_utf8_to_utf16le(self, src, dst, result=None, stream=None, cap=None):
+        result = self.new_result() if result is None else result
+        cap = dst.numel() if cap is None else cap
+        _check(gbu_convert_utf8_to_utf16le(self.ctx, self._ptr(src), src.numel(), self._ptr(dst), cap,
+                                           result.data_ptr(), self._stream(stream)),
+               "gbu_convert_utf8_to_utf16le")
+        return result
+
+    def convert_utf16le_to_utf8(self, src, dst, result=None, stream=None, cap=None):
+        result = self.new_result() if result is None else result
+        cap = dst.numel() if cap is None else cap
+        _check(gbu_convert_utf16le_to_utf8(self.ctx, self._ptr(src), src.numel(), self._ptr(dst), cap,
+                                           result.data_ptr(), self._stream(stream)),
+               "gbu_convert_utf16le_to_utf8")
+        return result

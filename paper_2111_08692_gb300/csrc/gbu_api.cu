@@ -1,0 +1,255 @@
+// gbu_api.cu -- the C ABI declared in include/gbutf.h: contexts, argument checks, launches.
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <atomic>
+
+#include "gbu_device.cuh"
+#include "gbu_kernels.h"
+#include "gbutf.h"
+
+using gbu::NT;
+using gbu::TILE_BYTES;
+
+namespace {
+
+enum Kernel { K_V8 = 0, K_L8, K_C8, K_V16, K_L16, K_C16, K_COUNT };
+
+const void *kernel_ptr(int k) {
+  return k < K_V16 ? gbu::utf8_kernel_ptr(k) : gbu::utf16_kernel_ptr(k - K_V16);
+}
+size_t kernel_smem(int k) {
+  return k < K_V16 ? gbu::utf8_smem_bytes(k) : gbu::utf16_smem_bytes(k - K_V16);
+}
+
+// Restores the caller's current device on scope exit.
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    int cur;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+}  // namespace
+
+struct gbu_ctx {
+  int device;
+  uint64_t max_units;
+  int num_sms;
+  gbu::WsHeader *ws;   // device
+  uint64_t *states;    // device
+  uint32_t max_states;
+  uint32_t wait_limit;
+  long long skip_tile;
+  int blocks_per_sm[K_COUNT];
+  std::atomic<uint64_t> launches;
+};
+
+static int init_workspace(gbu_ctx *c) {
+  gbu::WsHeader h;
+  memset(&h, 0, sizeof(h));
+  h.epoch = 1;
+  h.errkey = gbu::NO_ERROR;
+  if (cudaMemcpy(c->ws, &h, sizeof(h), cudaMemcpyHostToDevice) != cudaSuccess) return GBU_CUDA_ERROR;
+  if (cudaMemset(c->states, 0, (size_t)c->max_states * sizeof(uint64_t)) != cudaSuccess)
+    return GBU_CUDA_ERROR;
+  if (cudaDeviceSynchronize() != cudaSuccess) return GBU_CUDA_ERROR;
+  return GBU_OK;
+}
+
+extern "C" gbu_ctx *gbu_create(int device, uint64_t max_units) {
+  DeviceGuard g(device);
+  gbu_ctx *c = new gbu_ctx();
+  c->device = device;
+  c->max_units = max_units;
+  c->wait_limit = 1u << 22;
+  c->skip_tile = -1;
+  c->launches = 0;
+  if (cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) {
+    delete c;
+    return nullptr;
+  }
+  // the largest window count: UTF-16 input of max_units words (2 bytes each), plus the extra
+  // tile that UTF-8 kernels use past the end
+  const uint64_t bytes = 2 * max_units + 64;
+  const uint64_t tiles = bytes / TILE_BYTES + 4;
+  if (tiles > 0xFFFFFFF0ull) {
+    delete c;
+    return nullptr;
+  }
+  c->max_states = (uint32_t)tiles;
+  if (cudaMalloc(&c->ws, sizeof(gbu::WsHeader)) != cudaSuccess) {
+    delete c;
+    return nullptr;
+  }
+  if (cudaMalloc(&c->states, (size_t)c->max_states * sizeof(uint64_t)) != cudaSuccess) {
+    cudaFree(c->ws);
+    delete c;
+    return nullptr;
+  }
+  for (int k = 0; k < K_COUNT; ++k) {
+    const void *f = kernel_ptr(k);
+    const size_t smem = kernel_smem(k);
+    int bps = 0;
+    if (cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, f, NT, smem) != cudaSuccess || bps < 1) {
+      cudaFree(c->states);
+      cudaFree(c->ws);
+      delete c;
+      return nullptr;
+    }
+    c->blocks_per_sm[k] = bps;
+  }
+  if (init_workspace(c) != GBU_OK) {
+    cudaFree(c->states);
+    cudaFree(c->ws);
+    delete c;
+    return nullptr;
+  }
+  return c;
+}
+
+extern "C" void gbu_destroy(gbu_ctx *c) {
+  if (!c) return;
+  DeviceGuard g(c->device);
+  cudaFree(c->states);
+  cudaFree(c->ws);
+  delete c;
+}
+
+extern "C" int gbu_reset(gbu_ctx *c) {
+  if (!c) return GBU_BAD_ARGUMENT;
+  DeviceGuard g(c->device);
+  return init_workspace(c);
+}
+
+extern "C" void gbu_set_wait_limit(gbu_ctx *c, uint32_t rounds) {
+  if (c) c->wait_limit = rounds ? rounds : 1;
+}
+
+extern "C" void gbu_debug_skip_publish(gbu_ctx *c, int64_t tile) {
+  if (c) c->skip_tile = tile;
+}
+
+extern "C" uint64_t gbu_launch_count(const gbu_ctx *c) { return c ? c->launches.load() : 0; }
+
+// Builds the launch parameters for an input of n code units of unit_bytes bytes each.
+static int make_params(gbu_ctx *c, const void *src, uint64_t n, uint32_t unit_bytes, bool extra_tile,
+                       gbu::Params *p) {
+  if (!c) return GBU_BAD_ARGUMENT;
+  if (n > c->max_units) return GBU_BAD_ARGUMENT;
+  if (n > 0 && !src) return GBU_BAD_ARGUMENT;
+  if (unit_bytes == 2 && ((uintptr_t)src & 1)) return GBU_BAD_ARGUMENT;
+  memset(p, 0, sizeof(*p));
+  const uintptr_t a = (uintptr_t)src;
+  p->base = (const uint8_t *)(a & ~(uintptr_t)15);
+  p->off0 = (uint32_t)(a & 15);
+  p->n = n;
+  p->vbytes = p->off0 + n * unit_bytes;
+  const uint64_t span = n == 0 ? 0 : p->vbytes + (extra_tile ? 3 : 0);
+  const uint64_t ntiles = (span + TILE_BYTES - 1) / TILE_BYTES;
+  if (ntiles > c->max_states) return GBU_BAD_ARGUMENT;
+  p->ntiles = (uint32_t)ntiles;
+  p->ws = c->ws;
+  p->states = c->states;
+  p->max_states = c->max_states;
+  p->wait_limit = c->wait_limit;
+  p->skip_tile = c->skip_tile;
+  return GBU_OK;
+}
+
+// Tiles are dealt to CTAs round-robin (CTA b takes tiles b, b + grid, b + 2*grid, ...), so
+// the look-back of one round waits on tiles of the same or an earlier round.  That is only
+// safe when every CTA of the grid is resident at once, which a cooperative launch guarantees
+// (the grid never exceeds the occupancy-derived limit).
+static int launch(gbu_ctx *c, int k, const gbu::Params &p, gbu_stream stream) {
+  DeviceGuard g(c->device);
+  uint64_t grid = (uint64_t)c->num_sms * (uint64_t)c->blocks_per_sm[k];
+  if (p.ntiles < grid) grid = p.ntiles;
+  if (grid < 1) grid = 1;
+  void *args[] = {(void *)&p};
+  cudaError_t e = cudaLaunchCooperativeKernel(kernel_ptr(k), dim3((unsigned)grid), dim3(NT), args,
+                                              kernel_smem(k), (cudaStream_t)stream);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return GBU_CUDA_ERROR;
+  }
+  c->launches.fetch_add(1);
+  return GBU_OK;
+}
+
+static void set_dst(gbu::Params *p, void *dst, uint64_t cap, uint32_t out_unit_bytes) {
+  const uintptr_t a = (uintptr_t)dst;
+  p->dbase = (uint8_t *)(a & ~(uintptr_t)15);
+  p->dshift = (uint32_t)((a & 15) / out_unit_bytes);
+  p->cap = cap;
+}
+
+extern "C" int gbu_validate_utf8(gbu_ctx *c, const uint8_t *src, uint64_t n, gbu_result *result,
+                                 gbu_stream stream) {
+  gbu::Params p;
+  int rc = make_params(c, src, n, 1, true, &p);
+  if (rc != GBU_OK) return rc;
+  if (!result) return GBU_BAD_ARGUMENT;
+  p.result = result;
+  return launch(c, K_V8, p, stream);
+}
+
+extern "C" int gbu_validate_utf16le(gbu_ctx *c, const uint16_t *src, uint64_t n, gbu_result *result,
+                                    gbu_stream stream) {
+  gbu::Params p;
+  int rc = make_params(c, src, n, 2, false, &p);
+  if (rc != GBU_OK) return rc;
+  if (!result) return GBU_BAD_ARGUMENT;
+  p.result = result;
+  return launch(c, K_V16, p, stream);
+}
+
+extern "C" int gbu_utf16_length_from_utf8(gbu_ctx *c, const uint8_t *src, uint64_t n, uint64_t *len,
+                                          gbu_stream stream) {
+  gbu::Params p;
+  int rc = make_params(c, src, n, 1, false, &p);
+  if (rc != GBU_OK) return rc;
+  if (!len) return GBU_BAD_ARGUMENT;
+  p.len_out = len;
+  return launch(c, K_L8, p, stream);
+}
+
+extern "C" int gbu_utf8_length_from_utf16le(gbu_ctx *c, const uint16_t *src, uint64_t n, uint64_t *len,
+                                            gbu_stream stream) {
+  gbu::Params p;
+  int rc = make_params(c, src, n, 2, false, &p);
+  if (rc != GBU_OK) return rc;
+  if (!len) return GBU_BAD_ARGUMENT;
+  p.len_out = len;
+  return launch(c, K_L16, p, stream);
+}
+
+extern "C" int gbu_convert_utf8_to_utf16le(gbu_ctx *c, const uint8_t *src, uint64_t n, uint16_t *dst,
+                                           uint64_t cap, gbu_result *result, gbu_stream stream) {
+  gbu::Params p;
+  int rc = make_params(c, src, n, 1, true, &p);
+  if (rc != GBU_OK) return rc;
+  if (!result || (cap > 0 && !dst) || ((uintptr_t)dst & 1)) return GBU_BAD_ARGUMENT;
+  p.result = result;
+  set_dst(&p, dst, cap, 2);
+  return launch(c, K_C8, p, stream);
+}
+
+extern "C" int gbu_convert_utf16le_to_utf8(gbu_ctx *c, const uint16_t *src, uint64_t n, uint8_t *dst,
+                                           uint64_t cap, gbu_result *result, gbu_stream stream) {
+  gbu::Params p;
+  int rc = make_params(c, src, n, 2, false, &p);
+  if (rc != GBU_OK) return rc;
+  if (!result || (cap > 0 && !dst)) return GBU_BAD_ARGUMENT;
+  p.result = result;
+  set_dst(&p, dst, cap, 1);
+  return launch(c, K_C16, p, stream);
+}
