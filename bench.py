@@ -1,0 +1,459 @@
+#!/usr/bin/env python3
+"""Benchmark: UTF-8 <-> UTF-16LE validation and transcoding of 1 GiB buffers on GB300.
+
+One step = for each of the five profiles (ascii, latin, cyrillic, cjk, emoji), on a resident
+1 GiB UTF-8 buffer and a resident 1 GiB UTF-16LE buffer:
+    validate_utf8, utf16_length_from_utf8, convert_utf8_to_utf16le,
+    validate_utf16le, utf8_length_from_utf16le, convert_utf16le_to_utf8
+(30 library calls, 32.2 GB of input).  `value` is input GB/s over the whole job (all ranks).
+Inputs are larger than L2 (1 GiB vs 129 MB), so no L2 flush is needed between steps.
+
+Prints one JSON line (rank 0).  `--impl reference` times the reference codec (oracle/, a
+scalar CPU program) on bounded samples of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "UTF-8↔UTF-16 GB/s input & % HBM roofline; batched strings/s; p99 latency"
+OPS = ("validate_utf8", "utf16_length_from_utf8", "convert_utf8_to_utf16le",
+       "validate_utf16le", "utf8_length_from_utf16le", "convert_utf16le_to_utf8")
+UTF8_INPUT_OPS = ("validate_utf8", "utf16_length_from_utf8", "convert_utf8_to_utf16le")
+FALLBACK_HBM_GBS = 6800.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--size", type=int, default=1 << 30, help="bytes per UTF-8 (and UTF-16) buffer")
+    ap.add_argument("--profiles", default="ascii,latin,cyrillic,cjk,emoji")
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--cpu-sample", type=int, default=32 << 20, help="bytes per buffer for the CPU baseline")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("LOCAL_RANK", "0")), ws
+
+
+def workload_config(args, profiles):
+    return {
+        "workload": f"single {args.size >> 20} MiB buffers per profile ({', '.join(profiles)}): "
+                    "validate + length + transcode, UTF-8->UTF-16LE and UTF-16LE->UTF-8",
+        "buffer_bytes": args.size,
+        "profiles": list(profiles),
+        "ops_per_profile": list(OPS),
+        "input_bytes_per_step": 6 * args.size * len(profiles),
+        "l2": "inputs larger than L2 (no flush needed)",
+        "parallelism": "replicas" if args.gpus > 1 else "single GPU",
+    }
+
+
+# ---- clocks --------------------------------------------------------------------------------
+
+class ClockSampler:
+    """Samples nvidia-smi SM clocks and throttle reasons every 200 ms while running."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, local_rank: int):
+        vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+        ids = [v for v in vis.split(",") if v.strip()]
+        self.gpu = ids[local_rank].strip() if local_rank < len(ids) and ids[local_rank].strip().isdigit() \
+            else str(local_rank)
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.thread.join(timeout=2)
+
+    def summary(self):
+        sms, maxs, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sms.append(float(f[1]))
+                maxs.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, f[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        if not sms:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        return {"sm_mhz": statistics.median(sms), "sm_max_mhz": max(maxs), "reasons": sorted(reasons),
+                "samples": len(sms)}
+
+
+# ---- roofline bookkeeping -------------------------------------------------------------------
+
+def measured_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def ncu_traffic(op: str):
+    """DRAM bytes per launch (read + write) from the committed ncu summary, if it was taken
+    on the current kernel sources (the summary records their hash), else None."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.txt")
+    if not os.path.exists(path):
+        return None, None
+    from paper_2111_08692_gb300.build import sources_hash
+    want = sources_hash()
+    for line in open(path):
+        parts = line.split()
+        if len(parts) >= 5 and parts[0] == op and parts[1] == want:
+            # op  hash  profile  bytes_per_launch_at_scale  scale_note...
+            return float(parts[3]), parts[2]
+    return None, None
+
+
+# ---- our arm ------------------------------------------------------------------------------
+
+def run_ours(args):
+    rank, local_rank, world = dist_env()
+    profiles = [p for p in args.profiles.split(",") if p]
+    import workloads as W
+    if local_rank == 0:
+        W.prepare_single_buffers(profiles, args.size)  # spawn pool, before any CUDA work
+    import numpy as np
+    import torch
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+        dist.barrier()
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    from paper_2111_08692_gb300 import Codec, result_tuple
+    from paper_2111_08692_gb300.build import build
+    build()
+    codec = Codec(local_rank, max_units=args.size + 4096)
+    stream = torch.cuda.current_stream(dev)
+
+    bufs = []
+    for prof in profiles:
+        u8, u16 = W.single_buffer_1gib(prof, args.size, mmap=True)
+        s8 = torch.from_numpy(np.asarray(u8)).to(dev)
+        s16 = torch.from_numpy(np.asarray(u16).view(np.int16)).to(dev)
+        n16 = int(codec.utf16_length_from_utf8(s8).item())
+        n8 = int(codec.utf8_length_from_utf16le(s16).item())
+        d16 = torch.empty(n16, dtype=torch.int16, device=dev)
+        d8 = torch.empty(n8, dtype=torch.uint8, device=dev)
+        res = torch.empty((6, 2), dtype=torch.int64, device=dev)
+        ln = torch.empty((2, 1), dtype=torch.int64, device=dev)
+        bufs.append(dict(profile=prof, s8=s8, s16=s16, d16=d16, d8=d8, res=res, len=ln, n16=n16, n8=n8,
+                         u8=u8, u16=u16))
+    torch.cuda.synchronize()
+
+    def call(b, op):
+        if op == "validate_utf8":
+            codec.validate_utf8(b["s8"], result=b["res"][0])
+        elif op == "utf16_length_from_utf8":
+            codec.utf16_length_from_utf8(b["s8"], out=b["len"][0])
+        elif op == "convert_utf8_to_utf16le":
+            codec.convert_utf8_to_utf16le(b["s8"], b["d16"], result=b["res"][2])
+        elif op == "validate_utf16le":
+            codec.validate_utf16le(b["s16"], result=b["res"][3])
+        elif op == "utf8_length_from_utf16le":
+            codec.utf8_length_from_utf16le(b["s16"], out=b["len"][1])
+        else:
+            codec.convert_utf16le_to_utf8(b["s16"], b["d8"], result=b["res"][5])
+
+    def algo_bytes(b, op):
+        if op in ("validate_utf8", "utf16_length_from_utf8"):
+            return b["s8"].numel()
+        if op in ("validate_utf16le", "utf8_length_from_utf16le"):
+            return 2 * b["s16"].numel()
+        if op == "convert_utf8_to_utf16le":
+            return b["s8"].numel() + 2 * b["n16"]
+        return 2 * b["s16"].numel() + b["n8"]
+
+    def step(events=None):
+        for b in bufs:
+            for op in OPS:
+                if events is not None:
+                    e0 = torch.cuda.Event(enable_timing=True)
+                    e1 = torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    call(b, op)
+                    e1.record(stream)
+                    events.append((b["profile"], op, e0, e1))
+                else:
+                    call(b, op)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    # correctness of what is timed: every call succeeded and the lengths agree
+    for b in bufs:
+        r = [result_tuple(b["res"][i]) for i in (0, 2, 3, 5)]
+        assert r[0] == ("OK", b["s8"].numel()) and r[1] == ("OK", b["n16"]), (b["profile"], r)
+        assert r[2] == ("OK", b["s16"].numel()) and r[3] == ("OK", b["n8"]), (b["profile"], r)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+
+    launches0 = codec.launches()
+    events = []
+    with ClockSampler(local_rank) as clk:
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        for _ in range(args.steps):
+            step(events)
+        t1.record(stream)
+        torch.cuda.synchronize()
+    launches = codec.launches() - launches0
+    total_ms = t0.elapsed_time(t1)
+    if dist:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+        dist.barrier()
+
+    in_bytes_step = sum(b["s8"].numel() * 3 + 2 * b["s16"].numel() * 3 for b in bufs)
+    ms_per_step = total_ms / args.steps
+    value = world * in_bytes_step / (ms_per_step * 1e-3) / 1e9
+
+    # per-kernel durations (same stream, inside the timed region)
+    per = {}
+    for prof, op, e0, e1 in events:
+        per.setdefault(op, {}).setdefault(prof, []).append(e0.elapsed_time(e1))
+    peak, peak_kind = measured_peak()
+    breakdown = {}
+    op_tot = {}
+    for op in OPS:
+        breakdown[op] = {}
+        tot_ms, tot_bytes = 0.0, 0
+        for b in bufs:
+            ms = statistics.mean(per[op][b["profile"]])
+            ab = algo_bytes(b, op)
+            inb = b["s8"].numel() if op in UTF8_INPUT_OPS else 2 * b["s16"].numel()
+            breakdown[op][b["profile"]] = {"ms": round(ms, 4), "input_gbs": round(inb / ms / 1e6, 1),
+                                           "traffic_gbs": round(ab / ms / 1e6, 1),
+                                           "frac": round(ab / ms / 1e6 / peak, 3)}
+            tot_ms += ms
+            tot_bytes += ab
+        op_tot[op] = (tot_ms, tot_bytes)
+    dom = max(op_tot, key=lambda o: op_tot[o][0])
+    dom_ms, dom_bytes = op_tot[dom]
+    achieved = dom_bytes / dom_ms / 1e6  # GB/s: bytes per launch averaged over the profiles
+    traffic, traffic_note = ncu_traffic(dom)
+    roofline = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": peak,
+                "peak_kind": peak_kind, "unit": "GB/s", "frac": round(achieved / peak, 4),
+                "traffic": traffic, "algorithmic_bytes_per_launch": dom_bytes / len(bufs)}
+    if traffic_note:
+        roofline["traffic_profile"] = traffic_note
+
+    cfg = workload_config(args, profiles)
+    cfg["launch"] = codec.launch_config()
+    line = {"metric": METRIC, "value": round(value, 2), "unit": "GB/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_per_step, 3),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
+            "data": "synthetic (seeded profiles standing in for the paper's lipsum texts)",
+            "config": cfg, "roofline": roofline,
+            "gpu_launches": int(launches), "clocks": clk.summary(), "breakdown": breakdown}
+
+    if not args.no_e2e and args.e2e_steps > 0:
+        line["e2e"] = run_e2e(args, codec, bufs, stream, dist, world, call)
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(bufs, args.cpu_sample)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    codec.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+def run_e2e(args, codec, bufs, stream, dist, world, call):
+    """Same workload through host memory: each step copies its inputs from pinned host
+    buffers, runs the 30 calls, and copies results and both transcoded outputs back."""
+    import numpy as np
+    import torch
+    host = []
+    for b in bufs:
+        h8 = torch.empty(b["s8"].numel(), dtype=torch.uint8, pin_memory=True)
+        h8.copy_(torch.from_numpy(np.asarray(b["u8"])))
+        h16 = torch.empty(b["s16"].numel(), dtype=torch.int16, pin_memory=True)
+        h16.copy_(torch.from_numpy(np.asarray(b["u16"]).view(np.int16)))
+        o16 = torch.empty(b["n16"], dtype=torch.int16, pin_memory=True)
+        o8 = torch.empty(b["n8"], dtype=torch.uint8, pin_memory=True)
+        hres = torch.empty((6, 2), dtype=torch.int64, pin_memory=True)
+        hlen = torch.empty((2, 1), dtype=torch.int64, pin_memory=True)
+        host.append((h8, h16, o16, o8, hres, hlen))
+
+    def step():
+        for b, (h8, h16, o16, o8, hres, hlen) in zip(bufs, host):
+            b["s8"].copy_(h8, non_blocking=True)
+            b["s16"].copy_(h16, non_blocking=True)
+            for op in OPS:
+                call(b, op)
+            hres.copy_(b["res"], non_blocking=True)
+            hlen.copy_(b["len"], non_blocking=True)
+            o16.copy_(b["d16"], non_blocking=True)
+            o8.copy_(b["d8"], non_blocking=True)
+
+    step()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.e2e_steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    if dist:
+        t = torch.tensor([ms], device=bufs[0]["s8"].device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    in_bytes = sum(b["s8"].numel() * 3 + 2 * b["s16"].numel() * 3 for b in bufs)
+    h2d = sum(b["s8"].numel() + 2 * b["s16"].numel() for b in bufs)
+    d2h = sum(2 * b["n16"] + b["n8"] + 6 * 16 + 2 * 8 for b in bufs)
+    return {"value": round(world * in_bytes * args.e2e_steps / (ms * 1e-3) / 1e9, 2), "unit": "GB/s",
+            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "steps": args.e2e_steps,
+            "ms_per_step": round(ms / args.e2e_steps, 3)}
+
+
+def cpu_baseline(bufs, sample):
+    """The reference codec, as it stands, on one host core: the six operations on the first
+    `sample` bytes of every profile's UTF-8 buffer and the first sample/2 words of its UTF-16
+    buffer (cut back to a character boundary by CPython's codec)."""
+    import numpy as np
+    import oracle
+    o = oracle.default()
+    work = []
+    for b in bufs:
+        a8 = np.asarray(b["u8"][:sample])
+        a8 = np.frombuffer(a8.tobytes().decode("utf-8", errors="ignore").encode("utf-8"), np.uint8)
+        a16 = np.asarray(b["u16"][:sample // 2])
+        a16 = np.frombuffer(a16.tobytes().decode("utf-16-le", errors="ignore").encode("utf-16-le"), np.uint16)
+        work.append((a8, a16))
+    t = time.perf_counter()
+    nbytes = 0
+    for a8, a16 in work:
+        o.validate_utf8(a8)
+        o.utf16_length_from_utf8(a8)
+        o.convert_utf8_to_utf16le(a8)
+        o.validate_utf16le(a16)
+        o.utf8_length_from_utf16le(a16)
+        o.convert_utf16le_to_utf8(a16)
+        nbytes += 3 * a8.size + 3 * 2 * a16.size
+    dt = time.perf_counter() - t
+    return {"value": round(nbytes / dt / 1e9, 3), "unit": "GB/s", "cores": 1, "kind": "oracle",
+            "sample": f"first {sample >> 20} MiB of each profile's UTF-8 and UTF-16 buffer, the same six "
+                      f"operations, single thread ({dt:.1f} s)"}
+
+
+# ---- the reference arm ----------------------------------------------------------------------
+
+def run_reference(args):
+    rank, local_rank, world = dist_env()
+    if rank != 0:
+        return
+    profiles = [p for p in args.profiles.split(",") if p]
+    import numpy as np
+    import oracle
+    import workloads as W
+    W.prepare_single_buffers(profiles, args.size)
+    o = oracle.default()
+    sample = min(args.cpu_sample, args.size) // 4
+    work = []
+    for prof in profiles:
+        u8, u16 = W.single_buffer_1gib(prof, args.size, mmap=True)
+        a8 = np.frombuffer(np.asarray(u8[:sample]).tobytes().decode("utf-8", errors="ignore").encode(), np.uint8)
+        a16 = np.frombuffer(np.asarray(u16[:sample // 2]).tobytes().decode("utf-16-le", errors="ignore")
+                            .encode("utf-16-le"), np.uint16)
+        work.append((a8, a16))
+
+    def step():
+        n = 0
+        for a8, a16 in work:
+            o.validate_utf8(a8)
+            o.utf16_length_from_utf8(a8)
+            o.convert_utf8_to_utf16le(a8)
+            o.validate_utf16le(a16)
+            o.utf8_length_from_utf16le(a16)
+            o.convert_utf16le_to_utf8(a16)
+            n += 3 * a8.size + 6 * a16.size
+        return n
+
+    for _ in range(args.warmup):
+        step()
+    t = time.perf_counter()
+    nbytes = sum(step() for _ in range(args.steps))
+    dt = time.perf_counter() - t
+    value = nbytes / dt / 1e9
+    sample_desc = (f"first {sample >> 20} MiB of each profile's UTF-8 and UTF-16 buffer per step, the same "
+                   "six operations, single thread")
+    line = {"impl": "reference", "metric": METRIC, "value": round(value, 3), "unit": "GB/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dt / args.steps * 1e3, 3),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
+            "data": "synthetic (seeded profiles standing in for the paper's lipsum texts)",
+            "config": workload_config(args, profiles),
+            "cpu_baseline": {"value": round(value, 3), "unit": "GB/s", "cores": 1, "kind": "oracle",
+                             "sample": sample_desc},
+            "e2e": {"value": round(value, 3), "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -113,6 +113,12 @@ int gbu_convert_utf16le_to_utf8(gbu_ctx *ctx, const uint16_t *src, uint64_t n, u
 /* Number of kernel launches the library made through this context so far (for accounting). */
 uint64_t gbu_launch_count(const gbu_ctx *ctx);
 
+/* Launch geometry, for diagnostics: writes up to n values into out (host memory): the SM
+ * count, then the CTAs per SM of the kernels behind validate_utf8, utf16_length_from_utf8,
+ * convert_utf8_to_utf16le, validate_utf16le, utf8_length_from_utf16le and
+ * convert_utf16le_to_utf8, then the threads per CTA.  Returns the number of values written. */
+int gbu_launch_config(const gbu_ctx *ctx, int32_t *out, int n);
+
 #ifdef __cplusplus
 }
 #endif

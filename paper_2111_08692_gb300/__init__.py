@@ -6,6 +6,6 @@ The work runs in the CUDA library built from ``csrc/`` (C ABI: ``include/gbutf.h
 from .binding import (  # noqa: F401
     STATUS, STATUS_CODE, Codec, GbuError, GbuResult, gbu_convert_utf16le_to_utf8,
     gbu_convert_utf8_to_utf16le, gbu_create, gbu_debug_skip_publish, gbu_destroy,
-    gbu_launch_count, gbu_reset, gbu_set_wait_limit, gbu_utf16_length_from_utf8,
+    gbu_launch_config, gbu_launch_count, gbu_reset, gbu_set_wait_limit, gbu_utf16_length_from_utf8,
     gbu_utf8_length_from_utf16le, gbu_validate_utf16le, gbu_validate_utf8, lib, library_path,
     result_tuple)

@@ -57,6 +57,8 @@ def lib() -> ctypes.CDLL:
             L.gbu_debug_skip_publish.argtypes = [vp, i64]
             L.gbu_launch_count.restype = u64
             L.gbu_launch_count.argtypes = [vp]
+            L.gbu_launch_config.restype = i32
+            L.gbu_launch_config.argtypes = [vp, vp, i32]
             for name in ("gbu_validate_utf8", "gbu_validate_utf16le", "gbu_utf16_length_from_utf8",
                          "gbu_utf8_length_from_utf16le"):
                 f = getattr(L, name)
@@ -94,6 +96,12 @@ def gbu_debug_skip_publish(ctx: int, tile: int) -> None:
 
 def gbu_launch_count(ctx: int) -> int:
     return int(lib().gbu_launch_count(ctx))
+
+
+def gbu_launch_config(ctx: int) -> list[int]:
+    buf = (ctypes.c_int32 * 16)()
+    m = lib().gbu_launch_config(ctx, buf, 16)
+    return [int(buf[i]) for i in range(m)]
 
 
 def gbu_validate_utf8(ctx, src, n, result, stream) -> int:
@@ -180,6 +188,12 @@ class Codec:
 
     def launches(self) -> int:
         return gbu_launch_count(self.ctx)
+
+    def launch_config(self) -> dict:
+        v = gbu_launch_config(self.ctx)
+        names = ("validate_utf8", "utf16_length_from_utf8", "convert_utf8_to_utf16le",
+                 "validate_utf16le", "utf8_length_from_utf16le", "convert_utf16le_to_utf8")
+        return {"sms": v[0], "ctas_per_sm": dict(zip(names, v[1:7])), "threads_per_cta": v[7]}
 
     def set_wait_limit(self, rounds: int):
         gbu_set_wait_limit(self.ctx, rounds)

@@ -39,6 +39,18 @@ def _inputs():
         + glob.glob(os.path.join(INCLUDE, "*.h")) + [os.path.abspath(__file__)]
 
 
+def sources_hash() -> str:
+    """Short hash of the kernel sources and headers (ties profile summaries to a build)."""
+    import hashlib
+    h = hashlib.sha1()
+    files = sorted(glob.glob(os.path.join(CSRC, "*")) + glob.glob(os.path.join(INCLUDE, "*.h")))
+    for f in files:
+        if os.path.isfile(f):
+            h.update(os.path.basename(f).encode())
+            h.update(open(f, "rb").read())
+    return h.hexdigest()[:12]
+
+
 def up_to_date() -> bool:
     if not os.path.exists(LIB_PATH):
         return False

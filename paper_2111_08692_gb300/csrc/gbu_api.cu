@@ -10,7 +10,7 @@
 #include "gbu_kernels.h"
 #include "gbutf.h"
 
-using gbu::NT;
+using gbu::NTHREADS;
 using gbu::TILE_BYTES;
 
 namespace {
@@ -99,7 +99,7 @@ extern "C" gbu_ctx *gbu_create(int device, uint64_t max_units) {
     const size_t smem = kernel_smem(k);
     int bps = 0;
     if (cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, f, NT, smem) != cudaSuccess || bps < 1) {
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, f, NTHREADS, smem) != cudaSuccess || bps < 1) {
       cudaFree(c->states);
       cudaFree(c->ws);
       delete c;
@@ -140,6 +140,17 @@ extern "C" void gbu_debug_skip_publish(gbu_ctx *c, int64_t tile) {
 
 extern "C" uint64_t gbu_launch_count(const gbu_ctx *c) { return c ? c->launches.load() : 0; }
 
+extern "C" int gbu_launch_config(const gbu_ctx *c, int32_t *out, int n) {
+  if (!c || !out) return 0;
+  int32_t v[K_COUNT + 2];
+  v[0] = c->num_sms;
+  for (int k = 0; k < K_COUNT; ++k) v[1 + k] = c->blocks_per_sm[k];
+  v[K_COUNT + 1] = NTHREADS;
+  int m = n < K_COUNT + 2 ? n : K_COUNT + 2;
+  for (int i = 0; i < m; ++i) out[i] = v[i];
+  return m;
+}
+
 // Builds the launch parameters for an input of n code units of unit_bytes bytes each.
 static int make_params(gbu_ctx *c, const void *src, uint64_t n, uint32_t unit_bytes, bool extra_tile,
                        gbu::Params *p) {
@@ -165,18 +176,18 @@ static int make_params(gbu_ctx *c, const void *src, uint64_t n, uint32_t unit_by
   return GBU_OK;
 }
 
-// Tiles are dealt to CTAs round-robin (CTA b takes tiles b, b + grid, b + 2*grid, ...), so
-// the look-back of one round waits on tiles of the same or an earlier round.  That is only
-// safe when every CTA of the grid is resident at once, which a cooperative launch guarantees
-// (the grid never exceeds the occupancy-derived limit).
+// Read-only kernels deal tiles to CTAs round-robin and never wait on another CTA;
+// transcoders claim tiles from a ticket counter, so a tile only waits (in the look-back) on
+// tiles that running CTAs already hold.  Neither needs the grid to be co-resident; the grid
+// is sized to what fits on the device at once.
 static int launch(gbu_ctx *c, int k, const gbu::Params &p, gbu_stream stream) {
   DeviceGuard g(c->device);
   uint64_t grid = (uint64_t)c->num_sms * (uint64_t)c->blocks_per_sm[k];
   if (p.ntiles < grid) grid = p.ntiles;
   if (grid < 1) grid = 1;
   void *args[] = {(void *)&p};
-  cudaError_t e = cudaLaunchCooperativeKernel(kernel_ptr(k), dim3((unsigned)grid), dim3(NT), args,
-                                              kernel_smem(k), (cudaStream_t)stream);
+  cudaError_t e = cudaLaunchKernel(kernel_ptr(k), dim3((unsigned)grid), dim3(NTHREADS), args,
+                                   kernel_smem(k), (cudaStream_t)stream);
   if (e != cudaSuccess) {
     cudaGetLastError();
     return GBU_CUDA_ERROR;

@@ -1,15 +1,17 @@
 // gbu_device.cuh -- device-side building blocks shared by the UTF-8 and UTF-16 kernels.
 //
-// Every kernel of the library is a persistent grid that walks fixed-size tiles of the input:
-//   * tiles are claimed with a global ticket counter, so a CTA only ever waits on tiles that
-//     running CTAs already hold (forward progress does not depend on CTA scheduling);
-//   * each tile's bytes, plus a 16-byte halo on both sides, are copied into a shared-memory
-//     ring by the bulk-copy engine (cp.async.bulk + mbarrier), NSTAGE tiles ahead;
-//   * transcoders give every tile its output offset with a single-pass decoupled look-back
-//     scan (Merrill & Garland, "Single-pass Parallel Prefix Scan with Decoupled Look-back",
-//     2016): a tile publishes its aggregate, then its inclusive prefix, in one 64-bit word;
-//   * output is staged in shared memory and written back with cp.async.bulk stores for the
-//     16-byte-aligned middle and plain stores for the two ragged ends;
+// Every kernel is a persistent grid of warp-specialised CTAs that walk fixed-size tiles:
+//   * one producer warp per CTA claims tiles (a global ticket counter for transcoders,
+//     round-robin for read-only kernels), copies each tile plus a 16-byte halo on both sides
+//     into a shared-memory ring with the bulk-copy engine (cp.async.bulk + mbarrier), and
+//     hands the stage to the consumers through a "ready" mbarrier;
+//   * for transcoders the producer also counts the tile's output units as soon as it lands,
+//     publishes that aggregate, and runs the single-pass decoupled look-back (Merrill &
+//     Garland, "Single-pass Parallel Prefix Scan with Decoupled Look-back", 2016) that turns
+//     it into the tile's output offset -- ahead of the consumers, so its latency is hidden;
+//   * eight consumer warps decode their 16-byte chunks, stage the output in shared memory
+//     and write it back with cp.async.bulk stores for the 16-byte-aligned middle and plain
+//     stores for the ragged ends, then release the stage through an "empty" mbarrier;
 //   * the first error is a 64-bit atomicMin over input positions; the last CTA to finish
 //     (a completion counter) turns it into the exact offset and kind and writes the result.
 // Every spin wait is bounded; when a bound is hit the kernel records GBU_TIMEOUT and keeps
@@ -23,11 +25,13 @@
 
 namespace gbu {
 
-constexpr int NT = 256;                       // threads per CTA
-constexpr int NSTAGE = 3;                     // depth of the input ring
+constexpr int NCW = 8;                        // consumer warps per CTA
+constexpr int NC = NCW * 32;                  // consumer threads
+constexpr int NTHREADS = NC + 32;             // + one producer warp
+constexpr int PRODUCER_WARP = NCW;
 constexpr int HALO = 16;                      // halo bytes on each side of a tile
-constexpr uint32_t CHUNK = 16;                // input bytes per thread per tile
-constexpr uint32_t TILE_BYTES = NT * CHUNK;   // 4096 input bytes per tile
+constexpr uint32_t CHUNK = 16;                // input bytes per consumer thread per tile
+constexpr uint32_t TILE_BYTES = NC * CHUNK;   // 4096 input bytes per tile
 constexpr uint32_t WIN_BYTES = TILE_BYTES + 2 * HALO;
 
 // Scan state word: [63:62] flag, [61:44] epoch, [43:0] value.
@@ -39,12 +43,16 @@ constexpr uint64_t ST_VALUE_MASK = (1ull << 44) - 1;
 
 constexpr unsigned long long NO_ERROR = ~0ull;
 
-// Workspace header, one per context (device memory, zeroed at creation).  The last CTA of a
-// launch resets ticket/done/errkey/total and advances the epoch, so consecutive launches on
-// one stream need no memset.
+// Polling rounds before a wait on the bulk-copy engine or on another warp of the CTA gives up
+// (each try_wait round also suspends for a hardware-chosen time, so this is seconds).
+constexpr uint32_t LOCAL_WAIT_ROUNDS = 1u << 24;
+
+// Workspace header, one per context (device memory, initialised at creation).  The last CTA
+// of a launch resets ticket/done/errkey/total/status and advances the epoch, so consecutive
+// launches on one stream need no memset.
 struct WsHeader {
   uint32_t epoch;                 // tags scan states of the current launch (1 .. 2^18-1)
-  uint32_t ticket;                // next tile to claim
+  uint32_t ticket;                // next tile to claim (transcoders)
   uint32_t done;                  // CTAs that have finished
   uint32_t status;                // sticky: 1 = a wait gave up (GBU_TIMEOUT)
   unsigned long long errkey;      // smallest input position of a thread chunk with an error
@@ -67,7 +75,7 @@ struct Params {
   WsHeader *ws;
   uint64_t *states;        // one scan state per tile
   uint32_t max_states;     // entries in states[]
-  uint32_t wait_limit;     // polling rounds before a wait gives up
+  uint32_t wait_limit;     // polling rounds before a look-back wait gives up
   long long skip_tile;     // test hook: this tile never publishes (-1: off)
 };
 
@@ -145,6 +153,11 @@ __device__ __forceinline__ void fence_proxy_async_smem() {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 
+// barrier among the NC consumer threads only (the producer warp does not take part)
+__device__ __forceinline__ void consumer_sync() {
+  asm volatile("bar.sync 1, %0;" ::"n"(NC) : "memory");
+}
+
 __device__ __forceinline__ uint64_t ld_relaxed_u64(const uint64_t *p) {
   uint64_t v;
   asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
@@ -175,155 +188,23 @@ __device__ __forceinline__ uint64_t warp_sum_u64(uint64_t v) {
   return v;
 }
 
-// ---- shared memory common to every kernel -------------------------------------------------
-
-struct __align__(16) LoopSmem {
-  uint64_t bar[NSTAGE];
-  uint32_t ticket[NSTAGE];
-  uint32_t warp_sums[NT / 32 + 2];
-  uint32_t tile_err[2];          // smallest erroring thread index per tile (NT: none), by
-                                 // iteration parity so that a reset never races a new tile
-  unsigned long long excl;       // exclusive output prefix of the current tile
-  unsigned long long cta_total;  // CTA-local sum (length kernels)
-  int is_last;
-};
-
-// Inclusive scan over the CTA (one value per thread).  Returns the exclusive prefix of this
-// thread; *total receives the CTA sum.  Contains two __syncthreads.
-__device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t x, uint32_t *warp_sums,
-                                                         uint32_t *total) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  uint32_t incl = x;
+__device__ __forceinline__ unsigned long long warp_min_u64(unsigned long long v) {
 #pragma unroll
-  for (int d = 1; d < 32; d <<= 1) {
-    uint32_t y = __shfl_up_sync(0xffffffffu, incl, d);
-    if (lane >= d) incl += y;
+  for (int d = 16; d >= 1; d >>= 1) {
+    const unsigned long long o = __shfl_xor_sync(0xffffffffu, v, d);
+    v = o < v ? o : v;
   }
-  if (lane == 31) warp_sums[warp] = incl;
-  __syncthreads();
-  if (warp == 0) {
-    uint32_t s = lane < NT / 32 ? warp_sums[lane] : 0u;
-    uint32_t si = s;
-#pragma unroll
-    for (int d = 1; d < NT / 32; d <<= 1) {
-      uint32_t y = __shfl_up_sync(0xffffffffu, si, d);
-      if (lane >= d) si += y;
-    }
-    if (lane < NT / 32) warp_sums[lane] = si - s;
-    if (lane == NT / 32 - 1) warp_sums[NT / 32] = si;
-  }
-  __syncthreads();
-  *total = warp_sums[NT / 32];
-  return warp_sums[warp] + incl - x;
+  return v;
 }
 
 // Records a failed wait: the launch reports GBU_TIMEOUT.
 __device__ __forceinline__ void note_timeout(WsHeader *ws) { atomicOr(&ws->status, 1u); }
 
-// Decoupled look-back for tile `tile` with aggregate `agg`; executed by all 32 lanes of one
-// warp.  Returns the tile's exclusive prefix.  Waits are bounded by p.wait_limit rounds.
-__device__ __forceinline__ uint64_t lookback(const Params &p, uint32_t tile, uint64_t agg,
-                                          uint32_t epoch) {
-  const int lane = threadIdx.x & 31;
-  const uint64_t tag = (uint64_t)epoch << ST_EPOCH_SHIFT;
-  const bool skip = (long long)tile == p.skip_tile;
-  if (tile == 0) {
-    if (lane == 0 && !skip) st_relaxed_u64(&p.states[0], ST_FLAG_INC | tag | (agg & ST_VALUE_MASK));
-    return 0;
-  }
-  if (lane == 0 && !skip) st_relaxed_u64(&p.states[tile], ST_FLAG_AGG | tag | (agg & ST_VALUE_MASK));
-  uint64_t excl = 0;
-  long long pred = (long long)tile - 1;
-  while (true) {
-    const long long idx = pred - lane;
-    uint64_t s = ST_FLAG_INC;  // before tile 0: an inclusive prefix of 0
-    if (idx >= 0) {
-      uint32_t rounds = 0;
-      uint32_t ns = 32;
-      while (true) {
-        s = ld_relaxed_u64(&p.states[idx]);
-        if ((s >> 62) != 0 && (uint32_t)((s >> ST_EPOCH_SHIFT) & ST_EPOCH_MASK) == epoch) break;
-        if (++rounds >= p.wait_limit || ((rounds & 63) == 0 && ld_relaxed_u32(&p.ws->status))) {
-          note_timeout(p.ws);
-          s = ST_FLAG_INC;  // give up: treat as an inclusive prefix of 0
-          break;
-        }
-        __nanosleep(ns);
-        if (ns < 1024) ns <<= 1;
-      }
-    }
-    const bool inc = (s >> 62) == 2;
-    const uint32_t incmask = __ballot_sync(0xffffffffu, inc);
-    const int first_inc = incmask ? __ffs(incmask) - 1 : 32;
-    const uint64_t v = lane <= first_inc ? (s & ST_VALUE_MASK) : 0ull;
-    excl += warp_sum_u64(v);
-    if (incmask) break;
-    pred -= 32;
-  }
-  if (lane == 0 && !skip)
-    st_relaxed_u64(&p.states[tile], ST_FLAG_INC | tag | ((excl + agg) & ST_VALUE_MASK));
-  return excl;
-}
-
-// ---- the tile window ---------------------------------------------------------------------
-
-// Issues the bulk copy of tile `tile`'s window into `buf`: virtual bytes
-// [tile*T - HALO, tile*T + T + HALO), restricted to whole 16-byte segments of the source
-// that lie inside [off0, vbytes).  Called by one thread.  The rest of the window is filled
-// by fill_window_edges after the copy has landed.
-__device__ __forceinline__ void issue_window(const Params &p, uint32_t tile, uint8_t *buf,
-                                             uint64_t *bar) {
-  const long long w0 = (long long)tile * TILE_BYTES - HALO;
-  const long long w1 = w0 + WIN_BYTES;
-  const long long seg_lo = (long long)((p.off0 + 15u) & ~15u);
-  const long long seg_hi = (long long)(p.vbytes & ~15ull);
-  const long long b0 = w0 > seg_lo ? w0 : seg_lo;
-  const long long b1 = w1 < seg_hi ? w1 : seg_hi;
-  if (b1 > b0) {
-    mbar_arrive_expect_tx(bar, (uint32_t)(b1 - b0));
-    bulk_load(buf + (b0 - w0), p.base + b0, (uint32_t)(b1 - b0), bar);
-  } else {
-    mbar_arrive(bar);
-  }
-}
-
-// True if the window of `tile` has bytes that the bulk copy does not cover.
-__device__ __forceinline__ bool window_has_edges(const Params &p, uint32_t tile) {
-  const long long w0 = (long long)tile * TILE_BYTES - HALO;
-  const long long w1 = w0 + WIN_BYTES;
-  const long long seg_lo = (long long)((p.off0 + 15u) & ~15u);
-  const long long seg_hi = (long long)(p.vbytes & ~15ull);
-  return w0 < seg_lo || w1 > seg_hi;
-}
-
-// Fills the window bytes outside the bulk-copied range: source bytes where the virtual
-// position is inside [off0, vbytes), zero elsewhere.  All threads; ends with __syncthreads.
-__device__ __forceinline__ void fill_window_edges(const Params &p, uint32_t tile, uint8_t *buf) {
-  const long long w0 = (long long)tile * TILE_BYTES - HALO;
-  const long long w1 = w0 + WIN_BYTES;
-  const long long seg_lo = (long long)((p.off0 + 15u) & ~15u);
-  const long long seg_hi = (long long)(p.vbytes & ~15ull);
-  long long b0 = w0 > seg_lo ? w0 : seg_lo;
-  long long b1 = w1 < seg_hi ? w1 : seg_hi;
-  if (b1 < b0) b1 = b0 = w0;  // nothing copied
-  for (long long v = w0 + threadIdx.x; v < w1; v += NT) {
-    if (v >= b0 && v < b1) continue;
-    uint8_t byte = 0;
-    if (v >= (long long)p.off0 && v < (long long)p.vbytes) byte = p.base[v];
-    buf[v - w0] = byte;
-  }
-  __syncthreads();
-}
-
-// Polling rounds before a wait on the bulk-copy engine gives up (each try_wait round also
-// suspends for a hardware-chosen time, so this is seconds).
-constexpr uint32_t COPY_WAIT_ROUNDS = 1u << 24;
-
-// Bounded wait for the bulk copy of a stage (all threads).  Returns false on timeout.
-__device__ __forceinline__ bool wait_stage(const Params &p, uint64_t *bar, uint32_t parity) {
+// Bounded wait on an mbarrier phase.  Returns false (and records a timeout) if it gave up.
+__device__ __forceinline__ bool mbar_wait(const Params &p, uint64_t *bar, uint32_t parity) {
   uint32_t rounds = 0;
   while (!mbar_try_wait(bar, parity)) {
-    if (++rounds >= COPY_WAIT_ROUNDS) {
+    if (++rounds >= LOCAL_WAIT_ROUNDS) {
       note_timeout(p.ws);
       return false;
     }
@@ -331,28 +212,291 @@ __device__ __forceinline__ bool wait_stage(const Params &p, uint64_t *bar, uint3
   return true;
 }
 
-// After the loop gave up at iteration `it`, waits (bounded) for the copies that were issued
-// for iterations it .. it+NSTAGE-1 and never consumed.  Thread 0 only.
-__device__ __forceinline__ void drain_stages(const Params &p, LoopSmem &ls, uint32_t it) {
-  for (uint32_t j = 0; j < (uint32_t)NSTAGE; ++j) {
-    const uint32_t k = it + j;
-    const int s = k % NSTAGE;
-    if (ls.ticket[s] >= p.ntiles) continue;
-    uint32_t rounds = 0;
-    while (!mbar_try_wait(&ls.bar[s], (k / NSTAGE) & 1) && ++rounds < COPY_WAIT_ROUNDS) {
+// ---- shared memory common to every kernel -------------------------------------------------
+
+struct TileInfo {
+  uint32_t tile;             // tile of this stage use (>= ntiles: no more tiles)
+  uint32_t total;            // output units of the tile (transcoders)
+  unsigned long long excl;   // output units before the tile (transcoders)
+};
+
+template <int NS>
+struct __align__(16) PipeSmem {
+  uint64_t full[NS];    // bulk copy landed
+  uint64_t ready[NS];   // producer done with the stage: consumers may read it
+  uint64_t empty[NS];   // consumers done with the stage: producer may refill it
+  TileInfo info[NS];
+  uint32_t warp_sums[NCW + 2];
+  unsigned long long red[NTHREADS / 32];
+  int is_last;
+};
+
+template <int NS>
+__device__ __forceinline__ void pipe_init(PipeSmem<NS> &ps, uint32_t empty_count) {
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < NS; ++s) {
+      mbar_init(&ps.full[s], 1);
+      mbar_init(&ps.ready[s], 1);
+      mbar_init(&ps.empty[s], empty_count);
+    }
+    fence_mbar_init();
+  }
+  __syncthreads();
+}
+
+// Exclusive scan over the NC consumer threads.  Returns this thread's exclusive prefix and
+// the consumer-wide total.  Two consumer barriers.
+__device__ __forceinline__ uint32_t consumer_exclusive_scan(uint32_t x, uint32_t *warp_sums,
+                                                            uint32_t *total) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint32_t incl = x;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, incl, d);
+    if (lane >= d) incl += y;
+  }
+  if (lane == 31) warp_sums[warp] = incl;
+  consumer_sync();
+  if (warp == 0) {
+    const uint32_t s = lane < NCW ? warp_sums[lane] : 0u;
+    uint32_t si = s;
+#pragma unroll
+    for (int d = 1; d < NCW; d <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, si, d);
+      if (lane >= d) si += y;
+    }
+    if (lane < NCW) warp_sums[lane] = si - s;
+    if (lane == NCW - 1) warp_sums[NCW] = si;
+  }
+  consumer_sync();
+  *total = warp_sums[NCW];
+  return warp_sums[warp] + incl - x;
+}
+
+// ---- the tile window ---------------------------------------------------------------------
+
+struct WindowSpan {
+  long long w0, w1;  // virtual byte range of the window
+  long long b0, b1;  // part covered by the bulk copy (b0 == b1: none)
+};
+
+// The window of `tile` is virtual bytes [tile*T - HALO, tile*T + T + HALO); the bulk copy
+// takes the whole 16-byte source segments that lie inside [off0, vbytes).
+__device__ __forceinline__ WindowSpan window_span(const Params &p, uint32_t tile) {
+  WindowSpan w;
+  w.w0 = (long long)tile * TILE_BYTES - HALO;
+  w.w1 = w.w0 + WIN_BYTES;
+  const long long seg_lo = (long long)((p.off0 + 15u) & ~15u);
+  const long long seg_hi = (long long)(p.vbytes & ~15ull);
+  w.b0 = w.w0 > seg_lo ? w.w0 : seg_lo;
+  w.b1 = w.w1 < seg_hi ? w.w1 : seg_hi;
+  if (w.b1 <= w.b0) w.b0 = w.b1 = w.w0;
+  return w;
+}
+
+// Issues the bulk copy of `tile`'s window into `buf` (one thread).
+__device__ __forceinline__ void issue_window(const Params &p, uint32_t tile, uint8_t *buf,
+                                             uint64_t *bar) {
+  const WindowSpan w = window_span(p, tile);
+  if (w.b1 > w.b0) {
+    mbar_arrive_expect_tx(bar, (uint32_t)(w.b1 - w.b0));
+    bulk_load(buf + (w.b0 - w.w0), p.base + w.b0, (uint32_t)(w.b1 - w.b0), bar);
+  } else {
+    mbar_arrive(bar);
+  }
+}
+
+// Fills the window bytes the bulk copy does not cover: source bytes where the virtual
+// position is inside [off0, vbytes), zero elsewhere.  One warp; ends with __syncwarp.
+__device__ __forceinline__ void fill_window_edges_warp(const Params &p, uint32_t tile, uint8_t *buf) {
+  const WindowSpan w = window_span(p, tile);
+  if (w.b0 == w.w0 && w.b1 == w.w1) return;
+  for (long long v = w.w0 + (threadIdx.x & 31); v < w.w1; v += 32) {
+    if (v >= w.b0 && v < w.b1) continue;
+    uint8_t byte = 0;
+    if (v >= (long long)p.off0 && v < (long long)p.vbytes) byte = p.base[v];
+    buf[v - w.w0] = byte;
+  }
+  __syncwarp();
+}
+
+// ---- the producer warp -------------------------------------------------------------------
+
+__device__ __forceinline__ bool mbar_test(uint64_t *bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// mbar_test as seen by lane 0, the same for the whole warp (a phase can complete between two
+// lanes' tests; the producer's control flow must not diverge on that).
+__device__ __forceinline__ bool mbar_test_warp(uint64_t *bar, uint32_t parity) {
+  uint32_t ok = 0;
+  if ((threadIdx.x & 31) == 0) ok = mbar_test(bar, parity);
+  return __shfl_sync(0xffffffffu, ok, 0) != 0;
+}
+
+// Resumable decoupled look-back (one warp).  poll() reads the 32 states before `pred` once;
+// it returns true when the exclusive prefix is complete.  The caller interleaves polls with
+// other work instead of spinning.
+struct LookBack {
+  long long pred;       // next predecessor to read (lane 0's)
+  uint64_t excl;        // sum collected so far
+  uint32_t polls;       // polls that found a predecessor not yet published
+  __device__ __forceinline__ void start(uint32_t tile) {
+    pred = (long long)tile - 1;
+    excl = 0;
+    polls = 0;
+  }
+  __device__ __forceinline__ bool poll(const Params &p, uint32_t epoch) {
+    const int lane = threadIdx.x & 31;
+    const long long idx = pred - lane;
+    uint64_t s = ST_FLAG_INC;  // before tile 0: an inclusive prefix of 0
+    bool ok = true;
+    if (idx >= 0) {
+      s = ld_relaxed_u64(&p.states[idx]);
+      ok = (s >> 62) != 0 && (uint32_t)((s >> ST_EPOCH_SHIFT) & ST_EPOCH_MASK) == epoch;
+    }
+    if (!__all_sync(0xffffffffu, ok)) {
+      if (++polls >= p.wait_limit || ((polls & 63) == 0 && ld_relaxed_u32(&p.ws->status))) {
+        note_timeout(p.ws);
+        return true;  // give up: the prefix collected so far is used
+      }
+      return false;
+    }
+    const uint32_t incmask = __ballot_sync(0xffffffffu, (s >> 62) == 2);
+    const int first_inc = incmask ? __ffs(incmask) - 1 : 32;
+    excl += warp_sum_u64(lane <= first_inc ? (s & ST_VALUE_MASK) : 0ull);
+    if (incmask) return true;
+    pred -= 32;
+    return false;
+  }
+};
+
+// Runs the producer warp as a non-blocking event loop over the NS-stage ring:
+//   * issue: while a stage is free (its previous use released by the consumers), claim the
+//     next tile (a global ticket when SCAN, else round-robin) and start its bulk copy;
+//   * land: when the copy of the oldest unlanded use arrives, fill the window's edges and,
+//     when SCAN, count the tile (count(tile, window) -> output units, whole warp) and publish
+//     that aggregate at once, so that later tiles' look-backs never wait on this CTA's queue;
+//   * finish: advance the look-back of the oldest landed use by one poll; when it completes,
+//     publish the inclusive prefix, record the tile's offset and hand the stage over.
+// Uses are handed over in the order they were issued; one use past the last tile carries
+// the end marker.  If nothing progresses for LOCAL_WAIT_ROUNDS polls the launch records
+// GBU_TIMEOUT and the remaining uses are handed over as end markers.
+template <int NS, bool SCAN, class Count>
+__device__ __forceinline__ void run_producer(const Params &p, PipeSmem<NS> &ps,
+                                             uint8_t (*win)[WIN_BYTES], uint32_t epoch,
+                                             Count count) {
+  const int lane = threadIdx.x & 31;
+  const uint64_t tag = (uint64_t)epoch << ST_EPOCH_SHIFT;
+  uint32_t issued = 0, landed = 0, finished = 0, idle = 0;
+  bool ended = false, lb_active = false;
+  LookBack lb;
+  while (true) {
+    bool progress = false;
+    // issue
+    while (!ended && issued < finished + NS) {
+      const int s = issued % NS;
+      if (issued >= (uint32_t)NS && !mbar_test_warp(&ps.empty[s], ((issued / NS) - 1) & 1)) break;
+      uint32_t tile = 0;
+      if (lane == 0) {
+        tile = SCAN ? atomicAdd(&p.ws->ticket, 1u) : blockIdx.x + issued * gridDim.x;
+        ps.info[s].tile = tile;
+        if (tile < p.ntiles) issue_window(p, tile, win[s], &ps.full[s]);
+      }
+      tile = __shfl_sync(0xffffffffu, tile, 0);
+      ended = tile >= p.ntiles;
+      ++issued;
+      progress = true;
+    }
+    // land
+    while (landed < issued) {
+      const int s = landed % NS;
+      // lane 0 wrote info[s]; broadcast its value (a shuffle does not order shared memory)
+      const uint32_t t = __shfl_sync(0xffffffffu, lane == 0 ? ps.info[s].tile : 0u, 0);
+      if (t < p.ntiles) {
+        if (!mbar_test_warp(&ps.full[s], (landed / NS) & 1)) break;
+        fill_window_edges_warp(p, t, win[s]);
+        if (SCAN) {
+          const uint32_t agg = count(t, win[s]);
+          if (lane == 0) {
+            ps.info[s].total = agg;
+            atomicAdd(&p.ws->total, (unsigned long long)agg);
+            if ((long long)t != p.skip_tile)
+              st_relaxed_u64(&p.states[t], (t == 0 ? ST_FLAG_INC : ST_FLAG_AGG) | tag |
+                                               ((uint64_t)agg & ST_VALUE_MASK));
+          }
+        }
+      }
+      ++landed;
+      progress = true;
+    }
+    // finish
+    if (finished < landed) {
+      const int s = finished % NS;
+      const uint32_t t = __shfl_sync(0xffffffffu, lane == 0 ? ps.info[s].tile : 0u, 0);
+      bool done = true;
+      if (SCAN && t < p.ntiles && t > 0) {
+        if (!lb_active) {
+          lb.start(t);
+          lb_active = true;
+        }
+        done = lb.poll(p, epoch);
+        progress = true;
+      }
+      if (done) {
+        lb_active = false;
+        if (lane == 0) {
+          if (SCAN && t < p.ntiles) {
+            const uint64_t ex = t > 0 ? lb.excl : 0;
+            ps.info[s].excl = ex;
+            if (t > 0 && (long long)t != p.skip_tile)
+              st_relaxed_u64(&p.states[t], ST_FLAG_INC | tag |
+                                               ((ex + ps.info[s].total) & ST_VALUE_MASK));
+          }
+          mbar_arrive(&ps.ready[s]);
+        }
+        __syncwarp();
+        ++finished;
+        progress = true;
+      }
+    }
+    if (ended && finished == issued) break;
+    if (progress) {
+      idle = 0;
+    } else if (++idle >= LOCAL_WAIT_ROUNDS) {
+      note_timeout(p.ws);
+      // hand every unfinished use over as an end marker so that the consumers stop
+      for (; finished < issued; ++finished) {
+        const int s = finished % NS;
+        if (lane == 0) {
+          ps.info[s].tile = 0xFFFFFFFFu;
+          mbar_arrive(&ps.ready[s]);
+        }
+      }
+      break;
+    } else {
+      __nanosleep(20);
     }
   }
 }
 
 // ---- output staging ----------------------------------------------------------------------
 
-// Writes the staged output of one tile.  The tile's `cnt` output units start at global unit
-// S; in the staging buffer unit i corresponds to global unit (S & ~(V-1) aligned with dshift)
-// as set up by the caller: staged index h + k holds global unit S + k, with
-// h = (dshift + S) & (V - 1).  Units at or past cap are not written.  Whole 16-byte chunks
-// go out with one bulk store (issued by thread 0, committed as one bulk group); the ragged
-// head and tail are written by other threads.  Every thread that wrote the staging buffer
-// must have executed fence_proxy_async_smem() before the __syncthreads preceding this call.
+// Writes the staged output of one tile (called by all NC consumer threads).  The tile's `cnt`
+// output units start at global unit S; staged index h + k holds global unit S + k, where
+// h = (dshift + S) & (V - 1) puts staged chunk boundaries on 16-byte destination boundaries.
+// Units at or past cap are not written.  Whole 16-byte chunks go out with one bulk store
+// issued (and committed as one bulk group) by consumer thread 0; the ragged head and tail are
+// written by the other threads.  Every thread that wrote the staging buffer must have run
+// fence_proxy_async_smem() before the consumer barrier preceding this call.
 template <typename U>
 __device__ __forceinline__ void store_staged(const Params &p, const U *staging, uint64_t S,
                                              uint32_t cnt) {
@@ -367,36 +511,66 @@ __device__ __forceinline__ void store_staged(const Params &p, const U *staging, 
   const uint32_t first_full = (h + V - 1) / V;
   const uint32_t last_full = end / V;
   if (first_full < last_full) {
-    if (threadIdx.x == 0) {
+    if (threadIdx.x == 0)
       bulk_store(gdst + first_full * V, staging + first_full * V, (last_full - first_full) * 16u);
-    }
     const uint32_t head_end = first_full * V;
-    for (uint32_t i = h + threadIdx.x; i < head_end; i += NT) gdst[i] = staging[i];
-    for (uint32_t i = last_full * V + threadIdx.x; i < end; i += NT) gdst[i] = staging[i];
+    for (uint32_t i = h + threadIdx.x; i < head_end; i += NC) gdst[i] = staging[i];
+    for (uint32_t i = last_full * V + threadIdx.x; i < end; i += NC) gdst[i] = staging[i];
   } else {
-    for (uint32_t i = h + threadIdx.x; i < end; i += NT) gdst[i] = staging[i];
+    for (uint32_t i = h + threadIdx.x; i < end; i += NC) gdst[i] = staging[i];
   }
   if (threadIdx.x == 0) bulk_commit();
 }
 
 // ---- completion ---------------------------------------------------------------------------
 
-// Called by every CTA after its loop.  Returns true in exactly one CTA (the last to finish),
+// Reduces per-thread error positions and totals over the CTA and folds them into the
+// workspace (all NTHREADS threads).
+template <int NS>
+__device__ __forceinline__ void cta_fold(const Params &p, PipeSmem<NS> &ps, unsigned long long err,
+                                         unsigned long long total, bool want_err, bool want_total) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (want_err) {
+    err = warp_min_u64(err);
+    if (lane == 0) ps.red[warp] = err;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      unsigned long long m = NO_ERROR;
+      for (int w = 0; w < NTHREADS / 32; ++w) m = ps.red[w] < m ? ps.red[w] : m;
+      if (m != NO_ERROR) atomicMin(&p.ws->errkey, m);
+    }
+    __syncthreads();
+  }
+  if (want_total) {
+    total = warp_sum_u64(total);
+    if (lane == 0) ps.red[warp] = total;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      unsigned long long t = 0;
+      for (int w = 0; w < NTHREADS / 32; ++w) t += ps.red[w];
+      if (t) atomicAdd(&p.ws->total, t);
+    }
+    __syncthreads();
+  }
+}
+
+// Called by every CTA after its loops.  Returns true in exactly one CTA (the last to finish),
 // after which that CTA may read the accumulated header fields.  All threads participate.
-__device__ __forceinline__ bool finish_cta(const Params &p, LoopSmem &ls) {
+template <int NS>
+__device__ __forceinline__ bool finish_cta(const Params &p, PipeSmem<NS> &ps) {
   __syncthreads();
   if (threadIdx.x == 0) {
     __threadfence();
     const uint32_t prev = atomicAdd(&p.ws->done, 1u);
-    ls.is_last = prev == gridDim.x - 1;
-    if (ls.is_last) __threadfence();
+    ps.is_last = prev == gridDim.x - 1;
+    if (ps.is_last) __threadfence();
   }
   __syncthreads();
-  return ls.is_last != 0;
+  return ps.is_last != 0;
 }
 
-// Resets the per-launch header fields and advances the epoch (last CTA, thread 0 after the
-// result is written; the whole CTA when the epoch wraps and the states must be cleared).
+// Resets the per-launch header fields and advances the epoch (last CTA, all threads; the
+// whole CTA clears the scan states when the epoch wraps).
 __device__ __forceinline__ void reset_workspace(const Params &p) {
   __shared__ uint32_t wrap;
   if (threadIdx.x == 0) {
@@ -406,18 +580,17 @@ __device__ __forceinline__ void reset_workspace(const Params &p) {
     ws->errkey = NO_ERROR;
     ws->total = 0;
     ws->status = 0;
-    uint32_t e = ws->epoch + 1;
+    const uint32_t e = ws->epoch + 1;
     wrap = e > ST_EPOCH_MASK;
     ws->epoch = wrap ? 1u : e;
   }
   __syncthreads();
   if (wrap) {
-    for (uint32_t i = threadIdx.x; i < p.max_states; i += NT) p.states[i] = 0;
+    for (uint32_t i = threadIdx.x; i < p.max_states; i += NTHREADS) p.states[i] = 0;
   }
   __threadfence();
 }
 
-// Writes a gbu_result (one 16-byte store where the pointer allows it).
 __device__ __forceinline__ void write_result(gbu_result *r, int32_t status, uint64_t count) {
   r->status = status;
   r->reserved = 0;

@@ -3,8 +3,8 @@
 // What is computed (paper Section 3): a leading byte's top bits give the sequence length
 // (0xxxxxxx, 110xxxxx, 1110xxxx, 11110xxx); continuation bytes are 10xxxxxx; the six rules
 // make a byte sequence valid.  Section 4's design (64-byte blocks, a 12-byte shuffle-table
-// routine) is a 128-bit-register idiom; here each thread owns 16 input bytes and works on
-// 32-bit words:
+// routine) is a 128-bit-register idiom; here each consumer thread owns 16 input bytes of a
+// tile and works on 32-bit words:
 //   * classification (SWAR): per byte, flags "continuation", ">= C0", ">= E0", ">= F0" as the
 //     most significant bit of each byte of a word;
 //   * structure (rules 1-3): a byte must be a continuation exactly when one of the three
@@ -18,7 +18,7 @@
 //     D800-DFFF, four-byte in U+10000-10FFFF (tested on the high surrogate it produces);
 //   * output: one UTF-16 word per leading byte, two for a four-byte sequence; the word
 //     offsets are prefix sums of per-byte counts (bytes inside a word via a multiply by
-//     0x01010101, threads via a warp/CTA scan, tiles via the look-back scan);
+//     0x01010101, threads via a warp/CTA scan, tiles via the producer's look-back scan);
 //   * an all-ASCII warp takes a fast path that widens bytes directly (Section 4's ASCII path).
 // A thread whose 16 bytes break any check reports its chunk start; the first error lies in
 // [start - 3, start + 15], and the last CTA finds its exact offset and kind by decoding that
@@ -61,8 +61,9 @@ __device__ __forceinline__ uint32_t selE(int h) { return h ? 0x3322u : 0x1100u; 
 __device__ __forceinline__ uint32_t selO(int h) { return h ? 0x4433u : 0x2211u; }
 __device__ __forceinline__ uint32_t selM(int h) { return h ? 0xBBAAu : 0x9988u; }
 
-// Decodes [start, limit) in reading order, from a position known to start a character, and
-// returns the first ill-formed sequence (kind, offset).  Single thread; used only on error.
+// Decodes in reading order from a position at or before the first error (backed up to a
+// byte that starts a character) and returns the first ill-formed sequence (kind, offset).
+// Single thread; used only on error.
 __device__ void resolve_utf8_error(const uint8_t *s, uint64_t n, long long chunk, int32_t *kind,
                                    uint64_t *off) {
   long long q = chunk - 3;
@@ -115,266 +116,244 @@ __device__ __forceinline__ void stage16(uint16_t *st, uint32_t x, const uint32_t
   }
 }
 
+// UTF-16 words of one tile (length formula), counted by one warp.
+__device__ __forceinline__ uint32_t count_utf16_units_warp(const Params &p, uint32_t tile,
+                                                           const uint8_t *win) {
+  const int lane = threadIdx.x & 31;
+  uint32_t cnt = 0;
+#pragma unroll
+  for (int r = 0; r < NC / 32; ++r) {
+    const int chunk = r * 32 + lane;
+    const long long c = (long long)tile * TILE_BYTES + (long long)CHUNK * chunk;
+    const bool edge = c < (long long)p.off0 || c + (long long)CHUNK > (long long)p.vbytes;
+    const uint4 v = *reinterpret_cast<const uint4 *>(win + HALO + CHUNK * chunk);
+    const uint32_t W[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const Flags8 f = classify8(W[k]);
+      const uint32_t vm = edge ? byte_range_mask(c + 4 * k, p.off0, (long long)p.vbytes) : 0x80808080u;
+      cnt += __popc(~f.isC & vm) + __popc(f.geF0 & vm);
+    }
+  }
+#pragma unroll
+  for (int d = 16; d >= 1; d >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, d);
+  return cnt;
+}
+
+template <int MODE>
+struct Utf8Cfg {
+  static constexpr int NS = MODE == U8_CONVERT ? 4 : 8;  // input ring depth
+};
+
 template <int MODE>
 struct Utf8Smem {
-  LoopSmem loop;
-  uint8_t win[NSTAGE][WIN_BYTES];
+  PipeSmem<Utf8Cfg<MODE>::NS> pipe;
+  uint8_t win[Utf8Cfg<MODE>::NS][WIN_BYTES];
 };
 
 // Output staging: at most 2 words per input byte (F0-FF count 2 each), plus alignment slack.
 constexpr uint32_t STAGE8_UNITS = 2 * TILE_BYTES + 8;
 
 template <int MODE>
-__global__ void __launch_bounds__(NT) utf8_kernel(const Params p) {
+__global__ void __launch_bounds__(NTHREADS) utf8_kernel(const Params p) {
+  constexpr int NS = Utf8Cfg<MODE>::NS;
   extern __shared__ __align__(128) uint8_t smem_raw[];
   Utf8Smem<MODE> &sm = *reinterpret_cast<Utf8Smem<MODE> *>(smem_raw);
-  uint16_t *staging = reinterpret_cast<uint16_t *>(smem_raw + ((sizeof(Utf8Smem<MODE>) + 127) & ~size_t(127)));
-  LoopSmem &ls = sm.loop;
-  const int tid = threadIdx.x, lane = tid & 31;
+  uint16_t *staging =
+      reinterpret_cast<uint16_t *>(smem_raw + ((sizeof(Utf8Smem<MODE>) + 127) & ~size_t(127)));
+  PipeSmem<NS> &ps = sm.pipe;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const uint32_t epoch = p.ws->epoch;
+  pipe_init(ps, MODE == U8_CONVERT ? 1u : (uint32_t)NCW);
 
-  if (tid == 0) {
-    for (int s = 0; s < NSTAGE; ++s) mbar_init(&ls.bar[s], 1);
-    fence_mbar_init();
-    ls.tile_err[0] = ls.tile_err[1] = NT;
-    ls.cta_total = 0;
-  }
-  __syncthreads();
-  if (tid == 0) {
-    for (int s = 0; s < NSTAGE; ++s) {
-      const uint32_t t = blockIdx.x + (uint32_t)s * gridDim.x;
-      ls.ticket[s] = t;
-      if (t < p.ntiles) issue_window(p, t, sm.win[s], &ls.bar[s]);
-    }
-  }
-  __syncthreads();
+  unsigned long long err_pos = NO_ERROR;  // smallest erroring chunk start seen by this thread
+  unsigned long long total = 0;           // length / output units counted by this thread
 
-  unsigned long long my_total = 0;  // length kernel: per-thread sum
-  bool aborted = false;
-  uint32_t it = 0;
-  for (;; ++it) {
-    const int s = it % NSTAGE;
-    const uint32_t tile = ls.ticket[s];
-    if (tile >= p.ntiles) break;
-    if (!wait_stage(p, &ls.bar[s], (it / NSTAGE) & 1)) { aborted = true; break; }
-    if (window_has_edges(p, tile)) fill_window_edges(p, tile, sm.win[s]);
-
-    const uint8_t *my = sm.win[s] + HALO + CHUNK * tid;
-    const uint4 v = *reinterpret_cast<const uint4 *>(my);
-    uint32_t W[6];
-    W[0] = *reinterpret_cast<const uint32_t *>(my - 4);  // previous word
-    W[1] = v.x; W[2] = v.y; W[3] = v.z; W[4] = v.w;
-    W[5] = *reinterpret_cast<const uint32_t *>(my + 16);  // next word
-    const long long c = (long long)tile * TILE_BYTES + (long long)CHUNK * tid;  // virtual position of W[1]
-    const bool edge = c < (long long)p.off0 || c + (long long)CHUNK > (long long)p.vbytes;
-
-    Flags8 f[5];
-#pragma unroll
-    for (int k = 0; k < 5; ++k) f[k] = classify8(W[k]);
-
-    // counted (and, when converting, written) positions: not continuations, inside the data
-    uint32_t lead[4], four[4];
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      uint32_t vm = 0x80808080u;
-      if (edge) vm = byte_range_mask(c + 4 * k, p.off0, (long long)p.vbytes);
-      lead[k] = ~f[k + 1].isC & 0x80808080u & vm;
-      four[k] = f[k + 1].geF0 & vm;
-    }
-    uint32_t cnt = 0;
-    uint32_t excl_b[4];  // per byte: words before this byte inside its 32-bit word
-    uint32_t base_w[4];  // words before each 32-bit word inside the chunk
-    if (MODE != U8_VALIDATE) {
-      uint32_t acc = 0;
-#pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        const uint32_t u = (lead[k] >> 7) + (four[k] >> 7);
-        const uint32_t incl = u * 0x01010101u;
-        excl_b[k] = incl - u;
-        base_w[k] = acc;
-        acc += incl >> 24;
-      }
-      cnt = acc;
-    }
-
-    if (MODE == U8_LENGTH) {
-      my_total += cnt;
-      __syncthreads();  // every thread is done with this stage
-      if (tid == 0) {
-        const uint32_t t = blockIdx.x + (it + NSTAGE) * gridDim.x;
-        ls.ticket[s] = t;
-        if (t < p.ntiles) issue_window(p, t, sm.win[s], &ls.bar[s]);
-      }
-      continue;
-    }
-
-    // ---- validation ------------------------------------------------------------------
-    uint32_t err = 0;
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      const uint32_t req = __funnelshift_l(f[k].geC0, f[k + 1].geC0, 8) |
-                           __funnelshift_l(f[k].geE0, f[k + 1].geE0, 16) |
-                           __funnelshift_l(f[k].geF0, f[k + 1].geF0, 24);
-      err |= req ^ f[k + 1].isC;
-    }
-    const uint32_t nonascii = (W[1] | W[2] | W[3] | W[4]) & 0x80808080u;
-    const bool warp_ascii = __all_sync(0xffffffffu, nonascii == 0 && !edge);
-
-    uint32_t R[8], L4[8];  // decoded words per pair of positions (lanes), second words of 4-byte
-    uint32_t m4w[4];
-    if (!warp_ascii) {
-      uint32_t c2 = 0, c3 = 0, c4 = 0;
-#pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        c2 |= f[k + 1].geC0 & ~f[k + 1].geE0;
-        c3 |= f[k + 1].geE0 & ~f[k + 1].geF0;
-        c4 |= f[k + 1].geF0;
-      }
-      const bool has2 = __any_sync(0xffffffffu, c2 != 0);
-      const bool has3 = __any_sync(0xffffffffu, c3 != 0);
-      const bool has4 = __any_sync(0xffffffffu, c4 != 0);
-      // pair i covers positions 2i, 2i+1; E[i] = bytes (2i, 2i+1), O[i] = bytes (2i+1, 2i+2)
-      uint32_t E[9], O[9];
-#pragma unroll
-      for (int i = 0; i < 9; ++i) {
-        const int k = i >> 1, h = i & 1;
-        E[i] = __byte_perm(W[k + 1], W[k + 2 <= 5 ? k + 2 : 5], selE(h));
-        O[i] = __byte_perm(W[k + 1], W[k + 2 <= 5 ? k + 2 : 5], selO(h));
-      }
-      uint32_t bad = 0;
-#pragma unroll
-      for (int i = 0; i < 8; ++i) {
-        const int k = i >> 1, h = i & 1;
-        uint32_t r = E[i] & 0x00FF00FFu;
-        L4[i] = 0;
-        if (has2 || has3 || has4) {
-          const uint32_t U2 = ((E[i] << 6) & 0x07C007C0u) | (O[i] & 0x003F003Fu);
-          if (has2) {
-            const uint32_t M2 = prmt(f[k + 1].geC0 & ~f[k + 1].geE0, 0, selM(h));
-            const uint32_t t = E[i] & 0x001E001Eu;  // U2 < 0x80 exactly when the lead is C0/C1
-            bad |= ~(t + 0x7FFF7FFFu) & M2 & 0x80008000u;
-            r = (U2 & M2) | (r & ~M2);
-          }
-          if (has3) {
-            const uint32_t M3 = prmt(f[k + 1].geE0 & ~f[k + 1].geF0, 0, selM(h));
-            const uint32_t U3 = ((U2 << 6) & 0xFFC0FFC0u) | (E[i + 1] & 0x003F003Fu);
-            const uint32_t t = (U3 >> 11) & 0x001F001Fu;  // 0: below U+800; 0x1B: D800-DFFF
-            const uint32_t nz0 = t + 0x7FFF7FFFu;
-            const uint32_t nzS = (t ^ 0x001B001Bu) + 0x7FFF7FFFu;
-            bad |= ~(nz0 & nzS) & M3 & 0x80008000u;
-            r = (U3 & M3) | (r & ~M3);
-          }
-          if (has4) {
-            const uint32_t M4 = prmt(f[k + 1].geF0, 0, selM(h));
-            const uint32_t hi = (U2 << 2) + ((E[i + 1] >> 4) & 0x00030003u) + 0xC7C0C7C0u;
-            const uint32_t lo = ((E[i + 1] << 6) & 0x03C003C0u) | (O[i + 1] & 0x003F003Fu) | 0xDC00DC00u;
-            const uint32_t t = ((hi ^ 0xD800D800u) >> 10) & 0x003F003Fu;  // 0 iff U+10000-10FFFF
-            bad |= (t + 0x7FFF7FFFu) & M4 & 0x80008000u;
-            r = (hi & M4) | (r & ~M4);
-            L4[i] = lo;
-          }
-        }
-        R[i] = r;
-      }
-      err |= bad;
-#pragma unroll
-      for (int k = 0; k < 4; ++k) m4w[k] = four[k];
+  if (warp == PRODUCER_WARP) {
+    if (MODE == U8_CONVERT) {
+      run_producer<NS, true>(p, ps, sm.win, epoch, [&](uint32_t t, const uint8_t *w) {
+        return count_utf16_units_warp(p, t, w);
+      });
     } else {
+      run_producer<NS, false>(p, ps, sm.win, epoch, [](uint32_t, const uint8_t *) { return 0u; });
+    }
+  } else {
+    for (uint32_t it = 0;; ++it) {
+      const int s = it % NS;
+      mbar_wait(p, &ps.ready[s], (it / NS) & 1);
+      const TileInfo inf = ps.info[s];
+      if (inf.tile >= p.ntiles) break;
+      const uint32_t tile = inf.tile;
+
+      const uint8_t *my = sm.win[s] + HALO + CHUNK * tid;
+      const uint4 v = *reinterpret_cast<const uint4 *>(my);
+      uint32_t W[6];
+      W[0] = *reinterpret_cast<const uint32_t *>(my - 4);  // previous word
+      W[1] = v.x; W[2] = v.y; W[3] = v.z; W[4] = v.w;
+      W[5] = *reinterpret_cast<const uint32_t *>(my + 16);  // next word
+      const long long c = (long long)tile * TILE_BYTES + (long long)CHUNK * tid;  // virtual pos of W[1]
+      const bool edge = c < (long long)p.off0 || c + (long long)CHUNK > (long long)p.vbytes;
+
+      Flags8 f[5];
 #pragma unroll
-      for (int k = 0; k < 4; ++k) m4w[k] = 0;
-    }
+      for (int k = 0; k < 5; ++k) f[k] = classify8(W[k]);
 
-    uint32_t &tile_err = ls.tile_err[it & 1];
-    if (err) atomicMin(&tile_err, (uint32_t)tid);
-
-    if (MODE == U8_VALIDATE) {
-      __syncthreads();  // stage consumed; tile_err complete
-      if (tid == 0) {
-        if (tile_err != NT) {
-          atomicMin(&p.ws->errkey,
-                    (unsigned long long)((long long)tile * TILE_BYTES + (long long)CHUNK * tile_err));
-          tile_err = NT;
-        }
-        const uint32_t t = blockIdx.x + (it + NSTAGE) * gridDim.x;
-        ls.ticket[s] = t;
-        if (t < p.ntiles) issue_window(p, t, sm.win[s], &ls.bar[s]);
-      }
-      continue;
-    }
-
-    // ---- conversion: offsets ------------------------------------------------------------
-    uint32_t tile_total;
-    const uint32_t texcl = block_exclusive_scan(cnt, ls.warp_sums, &tile_total);
-    if (tid < 32) {
-      const uint64_t ex = lookback(p, tile, tile_total, epoch);
-      if (lane == 0) {
-        ls.excl = ex;
-        atomicAdd(&p.ws->total, (unsigned long long)tile_total);
-        if (tile_err != NT) {
-          atomicMin(&p.ws->errkey,
-                    (unsigned long long)((long long)tile * TILE_BYTES + (long long)CHUNK * tile_err));
-          tile_err = NT;
-        }
-        bulk_wait_read<1>();  // the staging buffer written below is free again
-      }
-    }
-    __syncthreads();
-    const uint64_t S = ls.excl;
-    uint16_t *st = staging + (it & 1) * STAGE8_UNITS;
-    const uint32_t h = (uint32_t)((p.dshift + S) & 7);
-    const uint32_t x0 = h + texcl;  // staging index of this thread's first word
-
-    if (warp_ascii) {
-      uint32_t u[8];
+      // counted (and, when converting, written) positions: not continuations, inside the data
+      uint32_t lead[4], four[4];
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
-        u[2 * k] = __byte_perm(W[k + 1], 0, 0x4140);
-        u[2 * k + 1] = __byte_perm(W[k + 1], 0, 0x4342);
+        uint32_t vm = 0x80808080u;
+        if (edge) vm = byte_range_mask(c + 4 * k, p.off0, (long long)p.vbytes);
+        lead[k] = ~f[k + 1].isC & 0x80808080u & vm;
+        four[k] = f[k + 1].geF0 & vm;
       }
-      stage16(st, x0, u);
-    } else {
+      uint32_t cnt = 0;
+      uint32_t excl_b[4];  // per byte: words before this byte inside its 32-bit word
+      uint32_t base_w[4];  // words before each 32-bit word inside the chunk
+      if (MODE != U8_VALIDATE) {
+        uint32_t acc = 0;
 #pragma unroll
-      for (int j = 0; j < 16; ++j) {
-        const int k = j >> 2, b = j & 3, i = j >> 1;
-        if (lead[k] & (0x80u << (8 * b))) {
-          const uint32_t o = x0 + base_w[k] + ((excl_b[k] >> (8 * b)) & 0xFF);
-          const uint32_t word = (j & 1) ? (R[i] >> 16) : (R[i] & 0xFFFF);
-          st[o] = (uint16_t)word;
-          if (m4w[k] & (0x80u << (8 * b))) st[o + 1] = (uint16_t)((j & 1) ? (L4[i] >> 16) : (L4[i] & 0xFFFF));
+        for (int k = 0; k < 4; ++k) {
+          const uint32_t u = (lead[k] >> 7) + (four[k] >> 7);
+          const uint32_t incl = u * 0x01010101u;
+          excl_b[k] = incl - u;
+          base_w[k] = acc;
+          acc += incl >> 24;
+        }
+        cnt = acc;
+      }
+
+      if (MODE == U8_LENGTH) {
+        total += cnt;
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&ps.empty[s]);
+        continue;
+      }
+
+      // ---- validation ----------------------------------------------------------------
+      uint32_t err = 0;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const uint32_t req = __funnelshift_l(f[k].geC0, f[k + 1].geC0, 8) |
+                             __funnelshift_l(f[k].geE0, f[k + 1].geE0, 16) |
+                             __funnelshift_l(f[k].geF0, f[k + 1].geF0, 24);
+        err |= req ^ f[k + 1].isC;
+      }
+      const uint32_t nonascii = (W[1] | W[2] | W[3] | W[4]) & 0x80808080u;
+      const bool warp_ascii = __all_sync(0xffffffffu, nonascii == 0 && !edge);
+
+      uint32_t R[8], L4[8];  // decoded words per pair of positions (lanes); second words of 4-byte
+      if (!warp_ascii) {
+        uint32_t c2 = 0, c3 = 0, c4 = 0;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          c2 |= f[k + 1].geC0 & ~f[k + 1].geE0;
+          c3 |= f[k + 1].geE0 & ~f[k + 1].geF0;
+          c4 |= f[k + 1].geF0;
+        }
+        const bool has2 = __any_sync(0xffffffffu, c2 != 0);
+        const bool has3 = __any_sync(0xffffffffu, c3 != 0);
+        const bool has4 = __any_sync(0xffffffffu, c4 != 0);
+        // pair i covers positions 2i, 2i+1; E[i] = bytes (2i, 2i+1), O[i] = bytes (2i+1, 2i+2)
+        uint32_t E[9], O[9];
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+          const int k = i >> 1, h = i & 1;
+          E[i] = __byte_perm(W[k + 1], W[k + 2 <= 5 ? k + 2 : 5], selE(h));
+          O[i] = __byte_perm(W[k + 1], W[k + 2 <= 5 ? k + 2 : 5], selO(h));
+        }
+        uint32_t bad = 0;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          const int k = i >> 1, h = i & 1;
+          uint32_t r = E[i] & 0x00FF00FFu;
+          L4[i] = 0;
+          if (has2 || has3 || has4) {
+            const uint32_t U2 = ((E[i] << 6) & 0x07C007C0u) | (O[i] & 0x003F003Fu);
+            if (has2) {
+              const uint32_t M2 = prmt(f[k + 1].geC0 & ~f[k + 1].geE0, 0, selM(h));
+              const uint32_t t = E[i] & 0x001E001Eu;  // U2 < 0x80 exactly when the lead is C0/C1
+              bad |= ~(t + 0x7FFF7FFFu) & M2 & 0x80008000u;
+              r = (U2 & M2) | (r & ~M2);
+            }
+            if (has3) {
+              const uint32_t M3 = prmt(f[k + 1].geE0 & ~f[k + 1].geF0, 0, selM(h));
+              const uint32_t U3 = ((U2 << 6) & 0xFFC0FFC0u) | (E[i + 1] & 0x003F003Fu);
+              const uint32_t t = (U3 >> 11) & 0x001F001Fu;  // 0: below U+800; 0x1B: D800-DFFF
+              const uint32_t nz0 = t + 0x7FFF7FFFu;
+              const uint32_t nzS = (t ^ 0x001B001Bu) + 0x7FFF7FFFu;
+              bad |= ~(nz0 & nzS) & M3 & 0x80008000u;
+              r = (U3 & M3) | (r & ~M3);
+            }
+            if (has4) {
+              const uint32_t M4 = prmt(f[k + 1].geF0, 0, selM(h));
+              const uint32_t hi = (U2 << 2) + ((E[i + 1] >> 4) & 0x00030003u) + 0xC7C0C7C0u;
+              const uint32_t lo =
+                  ((E[i + 1] << 6) & 0x03C003C0u) | (O[i + 1] & 0x003F003Fu) | 0xDC00DC00u;
+              const uint32_t t = ((hi ^ 0xD800D800u) >> 10) & 0x003F003Fu;  // 0 iff U+10000-10FFFF
+              bad |= (t + 0x7FFF7FFFu) & M4 & 0x80008000u;
+              r = (hi & M4) | (r & ~M4);
+              L4[i] = lo;
+            }
+          }
+          R[i] = r;
+        }
+        err |= bad;
+      }
+      if (err && (unsigned long long)c < err_pos) err_pos = (unsigned long long)c;
+
+      if (MODE == U8_VALIDATE) {
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&ps.empty[s]);
+        continue;
+      }
+
+      // ---- conversion: offsets, staging, write-back -------------------------------------
+      if (tid == 0) bulk_wait_read<1>();  // the staging buffer written below is free again
+      uint32_t tile_total;
+      const uint32_t texcl = consumer_exclusive_scan(cnt, ps.warp_sums, &tile_total);
+      const uint64_t S = inf.excl;
+      uint16_t *st = staging + (it & 1) * STAGE8_UNITS;
+      const uint32_t x0 = (uint32_t)((p.dshift + S) & 7) + texcl;  // this thread's first word
+
+      if (warp_ascii) {
+        uint32_t u[8];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          u[2 * k] = __byte_perm(W[k + 1], 0, 0x4140);
+          u[2 * k + 1] = __byte_perm(W[k + 1], 0, 0x4342);
+        }
+        stage16(st, x0, u);
+      } else {
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          const int k = j >> 2, b = j & 3, i = j >> 1;
+          if (lead[k] & (0x80u << (8 * b))) {
+            const uint32_t o = x0 + base_w[k] + ((excl_b[k] >> (8 * b)) & 0xFF);
+            st[o] = (uint16_t)((j & 1) ? (R[i] >> 16) : (R[i] & 0xFFFF));
+            if (four[k] & (0x80u << (8 * b)))
+              st[o + 1] = (uint16_t)((j & 1) ? (L4[i] >> 16) : (L4[i] & 0xFFFF));
+          }
         }
       }
+      fence_proxy_async_smem();  // staging writes -> visible to the bulk-copy engine
+      consumer_sync();           // staging complete; every consumer is done with stage s
+      if (tid == 0) mbar_arrive(&ps.empty[s]);
+      store_staged<uint16_t>(p, st, S, tile_total);
     }
-    fence_proxy_async_smem();  // staging writes -> visible to the bulk-copy engine
-    __syncthreads();           // staging complete; stage s consumed
-    store_staged<uint16_t>(p, st, S, tile_total);
-    if (tid == 0) {
-      const uint32_t t = blockIdx.x + (it + NSTAGE) * gridDim.x;
-      ls.ticket[s] = t;
-      if (t < p.ntiles) issue_window(p, t, sm.win[s], &ls.bar[s]);
-    }
+    if (MODE == U8_CONVERT && tid == 0) bulk_wait_all<0>();
   }
 
-  // input copies still in flight after an aborted loop must land before the CTA exits
-  if (aborted && tid == 0) drain_stages(p, ls, it);
-  if (MODE == U8_CONVERT && tid == 0) bulk_wait_all<0>();
-  if (MODE == U8_LENGTH) {
-    // CTA sum of the per-thread counts
-    unsigned long long v = my_total;
-#pragma unroll
-    for (int d = 16; d >= 1; d >>= 1) v += __shfl_xor_sync(0xffffffffu, v, d);
-    if (lane == 0 && v) atomicAdd(&ls.cta_total, v);
-    __syncthreads();
-    if (tid == 0 && ls.cta_total) atomicAdd(&p.ws->total, ls.cta_total);
-  }
+  cta_fold(p, ps, err_pos, total, MODE != U8_LENGTH, MODE == U8_LENGTH);
 
-  if (finish_cta(p, ls)) {
+  if (finish_cta(p, ps)) {
     if (tid == 0) {
       WsHeader *ws = p.ws;
       const uint32_t status = *(volatile uint32_t *)&ws->status;
       const unsigned long long key = *(volatile unsigned long long *)&ws->errkey;
-      const unsigned long long total = *(volatile unsigned long long *)&ws->total;
+      const unsigned long long tot = *(volatile unsigned long long *)&ws->total;
       if (MODE == U8_LENGTH) {
-        *p.len_out = total;
+        *p.len_out = tot;
       } else if (status) {
         write_result(p.result, GBU_TIMEOUT, 0);
       } else if (key != NO_ERROR) {
@@ -384,7 +363,7 @@ __global__ void __launch_bounds__(NT) utf8_kernel(const Params p) {
         resolve_utf8_error(src, p.n, (long long)key - (long long)p.off0, &kind, &off);
         write_result(p.result, kind, off);
       } else if (MODE == U8_CONVERT) {
-        write_result(p.result, total > p.cap ? GBU_OUTPUT_TOO_SMALL : GBU_OK, total);
+        write_result(p.result, tot > p.cap ? GBU_OUTPUT_TOO_SMALL : GBU_OK, tot);
       } else {
         write_result(p.result, GBU_OK, p.n);
       }

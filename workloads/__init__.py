@@ -25,7 +25,7 @@ import os
 
 import numpy as np
 
-VERSION = "1"  # bump when any generator's output changes (invalidates the on-disk cache)
+VERSION = "2"  # bump when any generator's output changes (invalidates the on-disk cache)
 
 PROFILE_ORDER = ("ascii", "latin", "cyrillic", "cjk", "emoji")
 PROFILE_SEEDS = {"ascii": 1, "latin": 2, "cyrillic": 3, "cjk": 4, "emoji": 5}
@@ -55,30 +55,31 @@ PLACEHOLDER_8 = 0xF0000   # plane-15 private use: its UTF-8 form starts with byt
 PLACEHOLDER_16 = 0xE000   # BMP private use: one UTF-16 word E000
 
 
+def _draw_component(comp, m, rng):
+    _w, kind, lo, hi = comp
+    if kind == "range":
+        return rng.integers(lo, hi, size=m, dtype=np.uint32)
+    if kind == "bmp_nosurr":
+        v = rng.integers(0x800, 0x10000 - 0x800, size=m, dtype=np.uint32)
+        return np.where(v >= 0xD800, v + 0x800, v).astype(np.uint32)
+    half = rng.random(m) < 0.5  # space_punct
+    return np.where(half, np.uint32(0x20), _PUNCT[rng.integers(0, 32, size=m)]).astype(np.uint32)
+
+
 def draw_codepoints(profile: str, count: int, rng: np.random.Generator) -> np.ndarray:
-    """`count` code points of `profile`, as uint32."""
+    """`count` code points of `profile`, as uint32.  A uniform draw u per position picks the
+    component whose cumulative-weight interval holds u; every component is drawn for every
+    position and the picks are merged (vectorised, and independent of the order of the
+    components' values)."""
     mix = _MIX[profile]
-    out = np.empty(count, dtype=np.uint32)
     if len(mix) == 1:
-        comps = [(slice(None), count, mix[0])]
-    else:
-        cum = np.cumsum([w for w, *_ in mix])
-        comp = np.searchsorted(cum, rng.random(count) * cum[-1], side="right")
-        comp = np.minimum(comp, len(mix) - 1)
-        comps = []
-        for k, m in enumerate(mix):
-            idx = np.flatnonzero(comp == k)
-            comps.append((idx, idx.size, m))
-    for idx, m, (_w, kind, lo, hi) in comps:
-        if kind == "range":
-            v = rng.integers(lo, hi, size=m, dtype=np.uint32)
-        elif kind == "bmp_nosurr":
-            v = rng.integers(0x800, 0x10000 - 0x800, size=m, dtype=np.uint32)
-            v = np.where(v >= 0xD800, v + 0x800, v).astype(np.uint32)
-        else:  # space_punct
-            half = rng.random(m) < 0.5
-            v = np.where(half, np.uint32(0x20), _PUNCT[rng.integers(0, 32, size=m)]).astype(np.uint32)
-        out[idx] = v
+        return _draw_component(mix[0], count, rng)
+    u = rng.random(count)
+    cum = np.cumsum([w for w, *_ in mix])
+    cum = cum / cum[-1]
+    out = _draw_component(mix[-1], count, rng)
+    for k in range(len(mix) - 2, -1, -1):
+        np.copyto(out, _draw_component(mix[k], count, rng), where=u < cum[k])
     return out
 
 
@@ -149,44 +150,81 @@ def cache_dir() -> str:
     return d
 
 
-def _cached(key: str, make):
-    """make() -> dict of numpy arrays; cached as one .npz per key."""
+def _cache_path(key: str) -> str:
     h = hashlib.sha1((VERSION + key).encode()).hexdigest()[:20]
-    path = os.path.join(cache_dir(), h + ".npz")
-    if os.path.exists(path):
+    return os.path.join(cache_dir(), h)
+
+
+def _cached(key: str, make, mmap: bool = False):
+    """make() -> dict of numpy arrays, cached as one directory of .npy files per key (loaded
+    memory-mapped when mmap is true)."""
+    path = _cache_path(key)
+    done = os.path.join(path, "DONE")
+    if os.path.exists(done):
         try:
-            with np.load(path) as z:
-                return {k: z[k] for k in z.files}
+            names = [f[:-4] for f in os.listdir(path) if f.endswith(".npy")]
+            return {k: np.load(os.path.join(path, k + ".npy"), mmap_mode="r" if mmap else None)
+                    for k in names}
         except Exception:
             pass
     out = make()
-    tmp = path + f".tmp{os.getpid()}.npz"
-    np.savez(tmp, **out)
-    os.replace(tmp, path)
+    tmp = path + f".tmp{os.getpid()}"
+    os.makedirs(tmp, exist_ok=True)
+    for k, v in out.items():
+        np.save(os.path.join(tmp, k + ".npy"), v)
+    open(os.path.join(tmp, "DONE"), "w").close()
+    try:
+        os.rename(tmp, path)
+    except OSError:  # another process made it first
+        pass
     return out
 
 
 # ---- single-buffer workloads -----------------------------------------------------------------
 
 def profile_buffers(profile: str, n_utf8_bytes: int, n_utf16_units: int, seed: int,
-                    cache: bool = True):
+                    cache: bool = True, mmap: bool = False):
     """One UTF-8 buffer of exactly n_utf8_bytes and one UTF-16LE buffer of exactly
     n_utf16_units, both prefixes of the same seeded character stream."""
     def make():
         u8, u16 = _fill_buffers(profile, n_utf8_bytes, n_utf16_units, np.random.default_rng(seed))
         return {"u8": u8, "u16": u16}
     if cache and n_utf8_bytes + 2 * n_utf16_units >= (1 << 24):
-        d = _cached(f"profile:{profile}:{n_utf8_bytes}:{n_utf16_units}:{seed}", make)
+        d = _cached(f"profile:{profile}:{n_utf8_bytes}:{n_utf16_units}:{seed}", make, mmap=mmap)
     else:
         d = make()
     assert d["u8"].size == n_utf8_bytes and d["u16"].size == n_utf16_units
     return d["u8"], d["u16"]
 
 
-def single_buffer_1gib(profile: str, scale: int = 1 << 30):
+def single_buffer_1gib(profile: str, scale: int = 1 << 30, mmap: bool = False):
     """The 1 GiB workload of one profile: 2^30 UTF-8 bytes and 2^29 UTF-16 words (scale sets
     the UTF-8 byte count; the UTF-16 buffer has scale/2 words, the same number of bytes)."""
-    return profile_buffers(profile, scale, scale // 2, PROFILE_SEEDS[profile])
+    return profile_buffers(profile, scale, scale // 2, PROFILE_SEEDS[profile], mmap=mmap)
+
+
+def _make_one(args):
+    profile, scale = args
+    single_buffer_1gib(profile, scale, mmap=True)
+    return profile
+
+
+def prepare_single_buffers(profiles=PROFILE_ORDER, scale: int = 1 << 30, workers: int | None = None):
+    """Generates (into the on-disk cache) the single-buffer workloads of several profiles in
+    parallel worker processes.  The pool uses the 'spawn' start method, so it is safe to call
+    from a process that already uses CUDA."""
+    import concurrent.futures as cf
+    import multiprocessing as mp
+    todo = [p for p in profiles
+            if not os.path.exists(os.path.join(_cache_path(
+                f"profile:{p}:{scale}:{scale // 2}:{PROFILE_SEEDS[p]}"), "DONE"))]
+    if len(todo) <= 1 or (workers or os.cpu_count() or 1) <= 1:
+        for p in todo:
+            _make_one((p, scale))
+        return
+    with cf.ProcessPoolExecutor(max_workers=min(len(todo), workers or os.cpu_count() or 1),
+                                mp_context=mp.get_context("spawn")) as ex:
+        list(ex.map(_make_one, [(p, scale) for p in todo]))
 
 
 def mixed_1mib(seed: int = 0, n: int = 1 << 20):
