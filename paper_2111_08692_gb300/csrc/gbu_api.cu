@@ -10,18 +10,26 @@
 #include "gbu_kernels.h"
 #include "gbutf.h"
 
-using gbu::NTHREADS;
-using gbu::TILE_BYTES;
-
 namespace {
 
+// The six kernels, in the order gbu_launch_config reports them.
 enum Kernel { K_V8 = 0, K_L8, K_C8, K_V16, K_L16, K_C16, K_COUNT };
 
 const void *kernel_ptr(int k) {
-  return k < K_V16 ? gbu::utf8_kernel_ptr(k) : gbu::utf16_kernel_ptr(k - K_V16);
+  switch (k) {
+    case K_V8: return gbu::stream_kernel_ptr(0);
+    case K_L8: return gbu::stream_kernel_ptr(1);
+    case K_V16: return gbu::stream_kernel_ptr(2);
+    case K_L16: return gbu::stream_kernel_ptr(3);
+    case K_C8: return gbu::utf8_to_utf16_kernel_ptr();
+    default: return gbu::utf16_to_utf8_kernel_ptr();
+  }
 }
-size_t kernel_smem(int k) {
-  return k < K_V16 ? gbu::utf8_smem_bytes(k) : gbu::utf16_smem_bytes(k - K_V16);
+bool is_transcoder(int k) { return k == K_C8 || k == K_C16; }
+size_t kernel_smem(int) { return 0; }
+int kernel_threads(int k) { return is_transcoder(k) ? gbu::XT : gbu::STREAM_THREADS; }
+uint32_t kernel_tile_bytes(int k) {
+  return is_transcoder(k) ? gbu::PART_BYTES : gbu::stream_tile_bytes();
 }
 
 // Restores the caller's current device on scope exit.
@@ -76,10 +84,9 @@ extern "C" gbu_ctx *gbu_create(int device, uint64_t max_units) {
     delete c;
     return nullptr;
   }
-  // the largest window count: UTF-16 input of max_units words (2 bytes each), plus the extra
-  // tile that UTF-8 kernels use past the end
-  const uint64_t bytes = 2 * max_units + 64;
-  const uint64_t tiles = bytes / TILE_BYTES + 4;
+  // scan states: one per transcoder partition of the largest input (UTF-16: 2 bytes per
+  // unit), plus the extra partition UTF-8 inputs may use past their end
+  const uint64_t tiles = (2 * max_units + 64) / gbu::PART_BYTES + 4;
   if (tiles > 0xFFFFFFF0ull) {
     delete c;
     return nullptr;
@@ -98,8 +105,9 @@ extern "C" gbu_ctx *gbu_create(int device, uint64_t max_units) {
     const void *f = kernel_ptr(k);
     const size_t smem = kernel_smem(k);
     int bps = 0;
-    if (cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, f, NTHREADS, smem) != cudaSuccess || bps < 1) {
+    if ((smem && cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, f, kernel_threads(k), smem) != cudaSuccess ||
+        bps < 1) {
       cudaFree(c->states);
       cudaFree(c->ws);
       delete c;
@@ -142,18 +150,19 @@ extern "C" uint64_t gbu_launch_count(const gbu_ctx *c) { return c ? c->launches.
 
 extern "C" int gbu_launch_config(const gbu_ctx *c, int32_t *out, int n) {
   if (!c || !out) return 0;
-  int32_t v[K_COUNT + 2];
+  int32_t v[K_COUNT + 3];
   v[0] = c->num_sms;
   for (int k = 0; k < K_COUNT; ++k) v[1 + k] = c->blocks_per_sm[k];
-  v[K_COUNT + 1] = NTHREADS;
-  int m = n < K_COUNT + 2 ? n : K_COUNT + 2;
+  v[K_COUNT + 1] = gbu::STREAM_THREADS;
+  v[K_COUNT + 2] = gbu::XT;
+  const int m = n < K_COUNT + 3 ? n : K_COUNT + 3;
   for (int i = 0; i < m; ++i) out[i] = v[i];
   return m;
 }
 
-// Builds the launch parameters for an input of n code units of unit_bytes bytes each.
-static int make_params(gbu_ctx *c, const void *src, uint64_t n, uint32_t unit_bytes, bool extra_tile,
-                       gbu::Params *p) {
+// Builds the launch parameters of kernel k for an input of n code units.
+static int make_params(gbu_ctx *c, int k, const void *src, uint64_t n, uint32_t unit_bytes,
+                       bool extra_tail, gbu::Params *p) {
   if (!c) return GBU_BAD_ARGUMENT;
   if (n > c->max_units) return GBU_BAD_ARGUMENT;
   if (n > 0 && !src) return GBU_BAD_ARGUMENT;
@@ -164,9 +173,11 @@ static int make_params(gbu_ctx *c, const void *src, uint64_t n, uint32_t unit_by
   p->off0 = (uint32_t)(a & 15);
   p->n = n;
   p->vbytes = p->off0 + n * unit_bytes;
-  const uint64_t span = n == 0 ? 0 : p->vbytes + (extra_tile ? 3 : 0);
-  const uint64_t ntiles = (span + TILE_BYTES - 1) / TILE_BYTES;
-  if (ntiles > c->max_states) return GBU_BAD_ARGUMENT;
+  // UTF-8 validation looks at the three positions past the end (a cut sequence fails there)
+  const uint64_t span = n == 0 ? 0 : p->vbytes + (extra_tail ? 3 : 0);
+  const uint64_t tb = kernel_tile_bytes(k);
+  const uint64_t ntiles = (span + tb - 1) / tb;
+  if (ntiles > 0xFFFFFF00ull || (is_transcoder(k) && ntiles > c->max_states)) return GBU_BAD_ARGUMENT;
   p->ntiles = (uint32_t)ntiles;
   p->ws = c->ws;
   p->states = c->states;
@@ -176,17 +187,19 @@ static int make_params(gbu_ctx *c, const void *src, uint64_t n, uint32_t unit_by
   return GBU_OK;
 }
 
-// Read-only kernels deal tiles to CTAs round-robin and never wait on another CTA;
-// transcoders claim tiles from a ticket counter, so a tile only waits (in the look-back) on
-// tiles that running CTAs already hold.  Neither needs the grid to be co-resident; the grid
-// is sized to what fits on the device at once.
+// Read-only kernels deal warp tiles round-robin and never wait on another CTA; transcoders
+// claim tiles from a ticket counter, so a tile only waits (in the look-back) on tiles that
+// running CTAs already hold.  Neither needs the grid to be co-resident; the grid is sized to
+// what fits on the device at once.
 static int launch(gbu_ctx *c, int k, const gbu::Params &p, gbu_stream stream) {
   DeviceGuard g(c->device);
   uint64_t grid = (uint64_t)c->num_sms * (uint64_t)c->blocks_per_sm[k];
-  if (p.ntiles < grid) grid = p.ntiles;
+  const uint64_t useful = is_transcoder(k) ? p.ntiles
+                                           : (p.ntiles + gbu::STREAM_THREADS / 32 - 1) / (gbu::STREAM_THREADS / 32);
+  if (useful < grid) grid = useful;
   if (grid < 1) grid = 1;
   void *args[] = {(void *)&p};
-  cudaError_t e = cudaLaunchKernel(kernel_ptr(k), dim3((unsigned)grid), dim3(NTHREADS), args,
+  cudaError_t e = cudaLaunchKernel(kernel_ptr(k), dim3((unsigned)grid), dim3(kernel_threads(k)), args,
                                    kernel_smem(k), (cudaStream_t)stream);
   if (e != cudaSuccess) {
     cudaGetLastError();
@@ -206,7 +219,7 @@ static void set_dst(gbu::Params *p, void *dst, uint64_t cap, uint32_t out_unit_b
 extern "C" int gbu_validate_utf8(gbu_ctx *c, const uint8_t *src, uint64_t n, gbu_result *result,
                                  gbu_stream stream) {
   gbu::Params p;
-  int rc = make_params(c, src, n, 1, true, &p);
+  int rc = make_params(c, K_V8, src, n, 1, true, &p);
   if (rc != GBU_OK) return rc;
   if (!result) return GBU_BAD_ARGUMENT;
   p.result = result;
@@ -216,7 +229,7 @@ extern "C" int gbu_validate_utf8(gbu_ctx *c, const uint8_t *src, uint64_t n, gbu
 extern "C" int gbu_validate_utf16le(gbu_ctx *c, const uint16_t *src, uint64_t n, gbu_result *result,
                                     gbu_stream stream) {
   gbu::Params p;
-  int rc = make_params(c, src, n, 2, false, &p);
+  int rc = make_params(c, K_V16, src, n, 2, false, &p);
   if (rc != GBU_OK) return rc;
   if (!result) return GBU_BAD_ARGUMENT;
   p.result = result;
@@ -226,7 +239,7 @@ extern "C" int gbu_validate_utf16le(gbu_ctx *c, const uint16_t *src, uint64_t n,
 extern "C" int gbu_utf16_length_from_utf8(gbu_ctx *c, const uint8_t *src, uint64_t n, uint64_t *len,
                                           gbu_stream stream) {
   gbu::Params p;
-  int rc = make_params(c, src, n, 1, false, &p);
+  int rc = make_params(c, K_L8, src, n, 1, false, &p);
   if (rc != GBU_OK) return rc;
   if (!len) return GBU_BAD_ARGUMENT;
   p.len_out = len;
@@ -236,7 +249,7 @@ extern "C" int gbu_utf16_length_from_utf8(gbu_ctx *c, const uint8_t *src, uint64
 extern "C" int gbu_utf8_length_from_utf16le(gbu_ctx *c, const uint16_t *src, uint64_t n, uint64_t *len,
                                             gbu_stream stream) {
   gbu::Params p;
-  int rc = make_params(c, src, n, 2, false, &p);
+  int rc = make_params(c, K_L16, src, n, 2, false, &p);
   if (rc != GBU_OK) return rc;
   if (!len) return GBU_BAD_ARGUMENT;
   p.len_out = len;
@@ -246,7 +259,7 @@ extern "C" int gbu_utf8_length_from_utf16le(gbu_ctx *c, const uint16_t *src, uin
 extern "C" int gbu_convert_utf8_to_utf16le(gbu_ctx *c, const uint8_t *src, uint64_t n, uint16_t *dst,
                                            uint64_t cap, gbu_result *result, gbu_stream stream) {
   gbu::Params p;
-  int rc = make_params(c, src, n, 1, true, &p);
+  int rc = make_params(c, K_C8, src, n, 1, true, &p);
   if (rc != GBU_OK) return rc;
   if (!result || (cap > 0 && !dst) || ((uintptr_t)dst & 1)) return GBU_BAD_ARGUMENT;
   p.result = result;
@@ -257,7 +270,7 @@ extern "C" int gbu_convert_utf8_to_utf16le(gbu_ctx *c, const uint8_t *src, uint6
 extern "C" int gbu_convert_utf16le_to_utf8(gbu_ctx *c, const uint16_t *src, uint64_t n, uint8_t *dst,
                                            uint64_t cap, gbu_result *result, gbu_stream stream) {
   gbu::Params p;
-  int rc = make_params(c, src, n, 2, false, &p);
+  int rc = make_params(c, K_C16, src, n, 2, false, &p);
   if (rc != GBU_OK) return rc;
   if (!result || (cap > 0 && !dst)) return GBU_BAD_ARGUMENT;
   p.result = result;

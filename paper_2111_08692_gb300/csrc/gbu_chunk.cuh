@@ -1,0 +1,242 @@
+// gbu_chunk.cuh -- per-thread analysis of one 16-byte chunk (4 x 32-bit words), shared by
+// the streaming kernels (validation, lengths) and the transcoders.
+//
+// UTF-8 (paper Section 3): a leading byte's top bits give the sequence length (0xxxxxxx,
+// 110xxxxx, 1110xxxx, 11110xxx); continuation bytes are 10xxxxxx; rules 1-6 make a byte
+// sequence valid.  All tests run on 32-bit words (SWAR):
+//   * classification: per byte, flags "continuation", ">= C0", ">= E0", ">= F0" as the
+//     most significant bit of each byte;
+//   * structure (rules 1-3): a byte must be a continuation exactly when one of the three
+//     bytes before it is a leading byte that needs it (>= C0 one back, >= E0 two back, >= F0
+//     three back): the three flag words are funnel-shifted by 1, 2 and 3 bytes and compared
+//     with the continuation flags (bytes past the end of the input read as zero, so a cut
+//     sequence fails there);
+//   * values (rules 4-6, and rule 1 for F8-FF): each position is decoded as if it were a
+//     leading byte, two positions per 32-bit register (16-bit lanes), and the decoded value
+//     is range-checked for its class: two-byte >= U+80, three-byte >= U+800 and outside
+//     D800-DFFF, four-byte in U+10000-10FFFF (tested on the high surrogate it produces).
+// UTF-16 (Section 3): a word in D800-DBFF must be followed by one in DC00-DFFF and a word
+// in DC00-DFFF must follow one in D800-DBFF.
+#pragma once
+
+#include <stdint.h>
+
+#include "gbu_device.cuh"
+
+namespace gbu {
+
+struct Flags8 {
+  uint32_t isC, geC0, geE0, geF0;
+};
+
+// Per byte (as bit 7 of each byte): continuation 10xxxxxx, >= C0, >= E0, >= F0.
+__device__ __forceinline__ Flags8 classify8(uint32_t w) {
+  Flags8 f;
+  const uint32_t s1 = w << 1;
+  f.geC0 = w & s1 & 0x80808080u;
+  f.isC = w & ~s1 & 0x80808080u;
+  f.geE0 = f.geC0 & (w << 2);
+  f.geF0 = f.geE0 & (w << 3);
+  return f;
+}
+
+// Bytes of word [c, c+4) whose virtual position lies in [lo, hi), as bit 7 of each byte.
+__device__ __forceinline__ uint32_t byte_range_mask(long long c, long long lo, long long hi) {
+  uint32_t m = 0;
+#pragma unroll
+  for (int j = 0; j < 4; ++j)
+    if (c + j >= lo && c + j < hi) m |= 0x80u << (8 * j);
+  return m;
+}
+
+// Byte selectors for a pair of positions (q, q+1), q = 0 or 2, inside W[k]:W[k+1].
+__device__ __forceinline__ uint32_t selE(int h) { return h ? 0x3322u : 0x1100u; }
+__device__ __forceinline__ uint32_t selO(int h) { return h ? 0x4433u : 0x2211u; }
+__device__ __forceinline__ uint32_t selM(int h) { return h ? 0xBBAAu : 0x9988u; }
+
+// Rules 1-3 for the 16 bytes W[1..4], given the word before (W[0]).  Nonzero = error.
+__device__ __forceinline__ uint32_t utf8_structure_errors(const Flags8 f[5]) {
+  uint32_t err = 0;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const uint32_t req = __funnelshift_l(f[k].geC0, f[k + 1].geC0, 8) |
+                         __funnelshift_l(f[k].geE0, f[k + 1].geE0, 16) |
+                         __funnelshift_l(f[k].geF0, f[k + 1].geF0, 24);
+    err |= req ^ f[k + 1].isC;
+  }
+  return err;
+}
+
+// Rules 4-6 (and rule 1 for F8-FF) on the values the 16 positions of W[1..4] would decode
+// to, with W[5] the word after.  Must be called by all 32 lanes of a warp (the classes that
+// occur are agreed warp-wide so that absent classes cost nothing).  Nonzero = error.  When
+// UNITS, R[i] receives the UTF-16 word of positions 2i, 2i+1 (low, high lane: the byte
+// itself for ASCII, the decoded value for 2- and 3-byte leads, the high surrogate for
+// 4-byte leads) and L4[i] the low surrogate of 4-byte leads.
+template <bool UNITS>
+__device__ __forceinline__ uint32_t utf8_value_errors(const uint32_t W[6], const Flags8 f[5],
+                                                      uint32_t R[8], uint32_t L4[8]) {
+  uint32_t c2 = 0, c3 = 0, c4 = 0;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    c2 |= f[k + 1].geC0 & ~f[k + 1].geE0;
+    c3 |= f[k + 1].geE0 & ~f[k + 1].geF0;
+    c4 |= f[k + 1].geF0;
+  }
+  const bool has2 = __any_sync(0xffffffffu, c2 != 0);
+  const bool has3 = __any_sync(0xffffffffu, c3 != 0);
+  const bool has4 = __any_sync(0xffffffffu, c4 != 0);
+  if (!UNITS && !(has2 || has3 || has4)) return 0;
+  // pair i covers positions 2i, 2i+1; E[i] = bytes (2i, 2i+1), O[i] = bytes (2i+1, 2i+2)
+  uint32_t E[9], O[9];
+#pragma unroll
+  for (int i = 0; i < 9; ++i) {
+    const int k = i >> 1, h = i & 1;
+    E[i] = __byte_perm(W[k + 1], W[k + 2 <= 5 ? k + 2 : 5], selE(h));
+    O[i] = __byte_perm(W[k + 1], W[k + 2 <= 5 ? k + 2 : 5], selO(h));
+  }
+  uint32_t bad = 0;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const int k = i >> 1, h = i & 1;
+    uint32_t r = E[i] & 0x00FF00FFu;
+    if (UNITS) L4[i] = 0;
+    if (has2 || has3 || has4) {
+      const uint32_t U2 = ((E[i] << 6) & 0x07C007C0u) | (O[i] & 0x003F003Fu);
+      if (has2) {
+        const uint32_t M2 = prmt(f[k + 1].geC0 & ~f[k + 1].geE0, 0, selM(h));
+        const uint32_t t = E[i] & 0x001E001Eu;  // U2 < 0x80 exactly when the lead is C0/C1
+        bad |= ~(t + 0x7FFF7FFFu) & M2 & 0x80008000u;
+        if (UNITS) r = (U2 & M2) | (r & ~M2);
+      }
+      if (has3) {
+        const uint32_t M3 = prmt(f[k + 1].geE0 & ~f[k + 1].geF0, 0, selM(h));
+        const uint32_t U3 = ((U2 << 6) & 0xFFC0FFC0u) | (E[i + 1] & 0x003F003Fu);
+        const uint32_t t = (U3 >> 11) & 0x001F001Fu;  // 0: below U+800; 0x1B: D800-DFFF
+        const uint32_t nz0 = t + 0x7FFF7FFFu;
+        const uint32_t nzS = (t ^ 0x001B001Bu) + 0x7FFF7FFFu;
+        bad |= ~(nz0 & nzS) & M3 & 0x80008000u;
+        if (UNITS) r = (U3 & M3) | (r & ~M3);
+      }
+      if (has4) {
+        const uint32_t M4 = prmt(f[k + 1].geF0, 0, selM(h));
+        const uint32_t hi = (U2 << 2) + ((E[i + 1] >> 4) & 0x00030003u) + 0xC7C0C7C0u;
+        const uint32_t t = ((hi ^ 0xD800D800u) >> 10) & 0x003F003Fu;  // 0 iff U+10000-10FFFF
+        bad |= (t + 0x7FFF7FFFu) & M4 & 0x80008000u;
+        if (UNITS) {
+          r = (hi & M4) | (r & ~M4);
+          L4[i] = ((E[i + 1] << 6) & 0x03C003C0u) | (O[i + 1] & 0x003F003Fu) | 0xDC00DC00u;
+        }
+      }
+    }
+    if (UNITS) R[i] = r;
+  }
+  return bad;
+}
+
+// UTF-16 words of the chunk's positions inside [lo, hi) (length formula: one per byte that is
+// not a continuation byte, one more per byte F0-FF).
+__device__ __forceinline__ uint32_t utf8_count_units(const Flags8 f[5], long long c, bool edge,
+                                                     long long lo, long long hi) {
+  uint32_t cnt = 0;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const uint32_t vm = edge ? byte_range_mask(c + 4 * k, lo, hi) : 0x80808080u;
+    cnt += __popc(~f[k + 1].isC & vm) + __popc(f[k + 1].geF0 & vm);
+  }
+  return cnt;
+}
+
+__device__ __forceinline__ bool is_high16(uint32_t w) { return (w & 0xFC00u) == 0xD800u; }
+__device__ __forceinline__ bool is_low16(uint32_t w) { return (w & 0xFC00u) == 0xDC00u; }
+
+// UTF-8 bytes of one word for the length function (2 per surrogate word).
+__device__ __forceinline__ uint32_t len8_of_word(uint32_t w) {
+  return w < 0x80u ? 1u : (w < 0x800u ? 2u : ((w & 0xF800u) == 0xD800u ? 2u : 3u));
+}
+
+// Unpaired surrogates among the 8 words of a chunk, given the word before (prevw's high
+// half) and after (nextw's low half); words outside [lo, hi) are not judged.
+__device__ __forceinline__ bool utf16_chunk_errors(const uint32_t W[4], uint32_t prevw,
+                                                   uint32_t nextw, long long c, bool edge,
+                                                   long long lo, long long hi) {
+  // fast exit: no surrogate word in the chunk, and the word before is not a first surrogate
+  // followed by our first word (that one is judged by the chunk that owns it)
+  const uint32_t any = (W[0] | W[1] | W[2] | W[3]);
+  uint32_t u[10];
+  u[0] = prevw >> 16;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    u[1 + 2 * k] = W[k] & 0xFFFFu;
+    u[2 + 2 * k] = W[k] >> 16;
+  }
+  u[9] = nextw & 0xFFFFu;
+  if ((any & 0x80008000u) == 0) return false;  // all words below 0x8000: no surrogates
+  bool err = false;
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    const uint32_t w = u[j + 1];
+    const bool valid = !edge || (c + 2 * j >= lo && c + 2 * j < hi);
+    err |= valid && ((is_high16(w) && !is_low16(u[j + 2])) || (is_low16(w) && !is_high16(u[j])));
+  }
+  return err;
+}
+
+// ---- exact first error (single thread, only when an error was flagged) --------------------
+
+// `chunk` is the smallest start (in code units of src) of a 16-byte chunk that failed a
+// check.  Every check flags a position at most 3 bytes after the start of the ill-formed
+// sequence it belongs to, and nothing before the first error is flagged, so the first error
+// starts in [chunk - 3, chunk + 15].  Decoding in reading order from a character start at or
+// before chunk - 3 finds it; the kind is the first rule the bytes read so far break.
+static __device__ __noinline__ void resolve_utf8_error(const uint8_t *s, uint64_t n, long long chunk,
+                                                       int32_t *kind, uint64_t *off) {
+  long long q = chunk - 3;
+  if (q < 0) q = 0;
+  if (q > (long long)n) q = (long long)n;
+  for (int k = 0; k < 4 && q > 0 && (q >= (long long)n || (s[q] & 0xC0) == 0x80); ++k) --q;
+  uint64_t i = (uint64_t)q;
+  const uint64_t stop = (uint64_t)(chunk + 64) < n ? (uint64_t)(chunk + 64) : n;
+  while (i < stop) {
+    const uint32_t b = s[i];
+    if (b < 0x80) { ++i; continue; }
+    int32_t k = GBU_OK;
+    if (b < 0xC0) k = GBU_TOO_LONG;
+    else if (b >= 0xF8) k = GBU_HEADER_BITS;
+    else if (b < 0xC2) k = GBU_OVERLONG;
+    else if (b >= 0xF5) k = GBU_TOO_LARGE;
+    if (k != GBU_OK) { *kind = k; *off = i; return; }
+    const int len = b >= 0xF0 ? 4 : (b >= 0xE0 ? 3 : 2);
+    if (i + 1 >= n || (s[i + 1] & 0xC0) != 0x80) { *kind = GBU_TOO_SHORT; *off = i; return; }
+    const uint32_t c1 = s[i + 1];
+    if ((b == 0xE0 && c1 < 0xA0) || (b == 0xF0 && c1 < 0x90)) k = GBU_OVERLONG;
+    else if (b == 0xED && c1 >= 0xA0) k = GBU_SURROGATE;
+    else if (b == 0xF4 && c1 >= 0x90) k = GBU_TOO_LARGE;
+    if (k != GBU_OK) { *kind = k; *off = i; return; }
+    for (int j = 2; j < len; ++j)
+      if (i + j >= n || (s[i + j] & 0xC0) != 0x80) { *kind = GBU_TOO_SHORT; *off = i; return; }
+    i += len;
+  }
+  // Not reached for a real error (the flagged chunk always holds or follows the first error).
+  *kind = GBU_TOO_SHORT;
+  *off = chunk < 0 ? 0 : (uint64_t)chunk;
+}
+
+// UTF-16: a word is flagged exactly when it is the first word of an ill-formed sequence, so
+// the first error lies in the flagged chunk [chunk, chunk + 8).
+static __device__ __noinline__ void resolve_utf16_error(const uint16_t *s, uint64_t n, long long chunk,
+                                                        uint64_t *off) {
+  long long i = chunk < 0 ? 0 : chunk;
+  if (i > 0 && i < (long long)n && is_low16(s[i]) && is_high16(s[i - 1])) --i;
+  const long long stop = (chunk + 64) < (long long)n ? chunk + 64 : (long long)n;
+  while (i < stop) {
+    const uint32_t w = s[i];
+    if ((w & 0xF800u) != 0xD800u) { ++i; continue; }
+    if (is_high16(w) && i + 1 < (long long)n && is_low16(s[i + 1])) { i += 2; continue; }
+    *off = (uint64_t)i;
+    return;
+  }
+  *off = chunk < 0 ? 0 : (uint64_t)chunk;  // not reached for a real error
+}
+
+}  // namespace gbu

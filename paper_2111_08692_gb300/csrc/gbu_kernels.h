@@ -2,13 +2,17 @@
 #pragma once
 
 #include <stddef.h>
+#include <stdint.h>
 
 namespace gbu {
 
-// mode: 0 validate, 1 length, 2 convert
-size_t utf8_smem_bytes(int mode);
-const void *utf8_kernel_ptr(int mode);
-size_t utf16_smem_bytes(int mode);
-const void *utf16_kernel_ptr(int mode);
+// read-only streaming kernels; mode: 0 validate_utf8, 1 utf16_length_from_utf8,
+// 2 validate_utf16le, 3 utf8_length_from_utf16le
+const void *stream_kernel_ptr(int mode);
+uint32_t stream_tile_bytes();
+
+// transcoders (static shared memory only)
+const void *utf8_to_utf16_kernel_ptr();
+const void *utf16_to_utf8_kernel_ptr();
 
 }  // namespace gbu

@@ -1,0 +1,128 @@
+// gbu_stream.cu -- read-only kernels: validate_utf8, utf16_length_from_utf8,
+// validate_utf16le, utf8_length_from_utf16le.
+//
+// These never wait on another CTA, so they stream straight from global memory: each warp
+// owns 4 KB warp tiles (round-robin over all warps of the grid), issues all eight 16-byte
+// loads of a lane before using any (ld.global.nc, no L1 allocation), and takes each chunk's
+// neighbouring words from the adjacent lanes with shuffles (the warp tile's outer
+// neighbours with two extra 4-byte loads).  Only the warp tiles that straddle the ends of
+// the buffer read byte by byte with bounds checks.  Per-thread results (smallest erroring
+// chunk start, or unit count) are folded over the CTA and into the workspace; the last CTA
+// writes the result.
+#include <stdint.h>
+
+#include "gbu_chunk.cuh"
+#include "gbu_device.cuh"
+#include "gbu_kernels.h"
+
+namespace gbu {
+
+enum StreamMode { S_V8 = 0, S_L16 = 1, S_V16 = 2, S_L8 = 3 };
+
+constexpr int ST_WARPS = STREAM_THREADS / 32;
+constexpr int ST_ROUNDS = 8;                              // 16-byte chunks per lane per tile
+constexpr uint32_t WT_BYTES = 32u * 16u * ST_ROUNDS;      // 4096 bytes per warp tile
+
+template <int MODE>
+__global__ void __launch_bounds__(STREAM_THREADS) stream_kernel(const Params p) {
+  __shared__ unsigned long long red[ST_WARPS];
+  __shared__ int is_last;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const long long gw = (long long)blockIdx.x * ST_WARPS + warp;
+  const long long nw = (long long)gridDim.x * ST_WARPS;
+  const long long lo = p.off0, hi = (long long)p.vbytes;
+  unsigned long long err_pos = NO_ERROR, total = 0;
+
+  for (long long wt = gw; wt < (long long)p.ntiles; wt += nw) {
+    const long long t0 = wt * WT_BYTES;
+    const bool fast = t0 - 4 >= lo && t0 + (long long)WT_BYTES + 4 <= hi;
+    uint4 v[ST_ROUNDS];
+    uint32_t pre, post;
+#pragma unroll
+    for (int r = 0; r < ST_ROUNDS; ++r) v[r] = load_chunk(p, t0 + 512 * r + 16 * lane, fast);
+    if (fast) {
+      pre = ldg_word(p.base + t0 - 4);
+      post = ldg_word(p.base + t0 + WT_BYTES);
+    } else {
+      pre = load_word_checked(p, t0 - 4);
+      post = load_word_checked(p, t0 + WT_BYTES);
+    }
+#pragma unroll
+    for (int r = 0; r < ST_ROUNDS; ++r) {
+      const long long c = t0 + 512 * r + 16 * lane;
+      const bool edge = !fast && (c < lo || c + 16 > hi);
+      uint32_t W[6];
+      W[1] = v[r].x; W[2] = v[r].y; W[3] = v[r].z; W[4] = v[r].w;
+      const uint32_t up = __shfl_up_sync(0xffffffffu, v[r].w, 1);
+      const uint32_t down = __shfl_down_sync(0xffffffffu, v[r].x, 1);
+      const uint32_t before = r == 0 ? pre : __shfl_sync(0xffffffffu, v[r > 0 ? r - 1 : 0].w, 31);
+      const uint32_t after =
+          r == ST_ROUNDS - 1 ? post : __shfl_sync(0xffffffffu, v[r < ST_ROUNDS - 1 ? r + 1 : r].x, 0);
+      W[0] = lane == 0 ? before : up;
+      W[5] = lane == 31 ? after : down;
+
+      if (MODE == S_V8 || MODE == S_L16) {
+        Flags8 f[5];
+#pragma unroll
+        for (int k = 0; k < 5; ++k) f[k] = classify8(W[k]);
+        if (MODE == S_L16) {
+          total += utf8_count_units(f, c, edge, lo, hi);
+        } else {
+          uint32_t err = utf8_structure_errors(f);
+          err |= utf8_value_errors<false>(W, f, nullptr, nullptr);
+          if (err && (unsigned long long)c < err_pos) err_pos = (unsigned long long)c;
+        }
+      } else {
+        const uint32_t Wd[4] = {W[1], W[2], W[3], W[4]};
+        if (MODE == S_L8) {
+          uint32_t cnt = 0;
+#pragma unroll
+          for (int j = 0; j < 8; ++j) {
+            const uint32_t w = (Wd[j >> 1] >> (16 * (j & 1))) & 0xFFFFu;
+            const bool valid = !edge || (c + 2 * j >= lo && c + 2 * j < hi);
+            cnt += valid ? len8_of_word(w) : 0u;
+          }
+          total += cnt;
+        } else if (utf16_chunk_errors(Wd, W[0], W[5], c, edge, lo, hi)) {
+          if ((unsigned long long)c < err_pos) err_pos = (unsigned long long)c;
+        }
+      }
+    }
+  }
+
+  const bool want_err = MODE == S_V8 || MODE == S_V16;
+  if (!fold_and_finish<STREAM_THREADS>(p, want_err ? err_pos : total, want_err, red, &is_last)) return;
+  if (threadIdx.x == 0) {
+    const unsigned long long key = *(volatile unsigned long long *)&p.ws->errkey;
+    const unsigned long long tot = *(volatile unsigned long long *)&p.ws->total;
+    if (MODE == S_L16 || MODE == S_L8) {
+      *p.len_out = tot;
+    } else if (key == NO_ERROR) {
+      write_result(p.result, GBU_OK, p.n);
+    } else if (MODE == S_V8) {
+      int32_t kind;
+      uint64_t off;
+      resolve_utf8_error(p.base + p.off0, p.n, (long long)key - (long long)p.off0, &kind, &off);
+      write_result(p.result, kind, off);
+    } else {
+      uint64_t off;
+      resolve_utf16_error(reinterpret_cast<const uint16_t *>(p.base + p.off0), p.n,
+                          ((long long)key - (long long)p.off0) / 2, &off);
+      write_result(p.result, GBU_SURROGATE, off);
+    }
+  }
+  reset_workspace(p);
+}
+
+const void *stream_kernel_ptr(int mode) {
+  switch (mode) {
+    case S_V8: return (const void *)stream_kernel<S_V8>;
+    case S_L16: return (const void *)stream_kernel<S_L16>;
+    case S_V16: return (const void *)stream_kernel<S_V16>;
+    default: return (const void *)stream_kernel<S_L8>;
+  }
+}
+
+uint32_t stream_tile_bytes() { return WT_BYTES; }
+
+}  // namespace gbu

@@ -1,0 +1,257 @@
+// gbu_xcode.cuh -- the partition loop shared by both transcoders.
+//
+// A CTA of XT threads (XWARPS warps) claims 64 KB partitions from a ticket counter.  Warp w
+// owns the partition's w-th 4 KB slice and walks it in eight 512-byte regions (one 16-byte
+// chunk per lane per region), so a chunk's neighbouring words come from the adjacent lane,
+// or from the previous / next region's registers.  For every partition the CTA
+//   1. counts the output units of each region of the NEXT partition (a read from HBM), turns
+//      the 128 region counts into region offsets inside that partition, and publishes the
+//      partition total as its aggregate -- a whole partition before any look-back needs it;
+//   2. gets the CURRENT partition's output offset from a CTA-wide decoupled look-back;
+//   3. transcodes the current partition (a re-read, normally from L2): every warp handles its
+//      regions on its own -- a warp-level scan orders the lanes' output, the region's output
+//      is staged in the warp's shared-memory buffer and leaves with one bulk store (whole
+//      16-byte chunks) plus plain stores for the ragged ends.  No CTA-wide barrier is needed
+//      inside the region loop.
+// The direction-specific parts are a Codec class:
+//   struct Codec {
+//     using Out = uint8_t or uint16_t;                 // output code unit
+//     static constexpr uint32_t STAGE;                 // staged units per warp buffer
+//     __device__ static uint32_t count(const Params&, uint4 v, long long c, bool edge);
+//     __device__ static Region convert(const Params&, uint4 v, uint32_t prev, uint32_t next,
+//                                      long long c, bool edge, Out* st, uint32_t base,
+//                                      unsigned long long& err_pos);
+//   };
+// count() returns the units one chunk contributes to its region (the total that converting
+// the region stages); convert() stages the chunk's units at base + (the lane's exclusive
+// prefix inside the warp) and returns the region's unit count and the units it writes past
+// its end or leaves to its predecessor at its start.
+#pragma once
+
+#include <stdint.h>
+
+#include "gbu_device.cuh"
+
+namespace gbu {
+
+constexpr uint32_t SLICE_BYTES = PART_BYTES / XWARPS;  // 4 KB per warp
+constexpr uint32_t REGION_BYTES = 32 * CHUNK;          // 512 bytes per warp per round
+static_assert(SLICE_BYTES == REGION_BYTES * PART_ROUNDS, "a slice is PART_ROUNDS regions");
+
+struct Region {
+  uint32_t total;  // units counted for the region
+  uint32_t skip;   // leading units written by the previous region (not to be stored here)
+  uint32_t extra;  // units this region writes past its end (a pair cut by the region end)
+};
+
+struct __align__(16) PartCounts {
+  uint32_t off[PART_ROUNDS * XWARPS];  // region offsets inside the partition, in byte order
+  uint32_t total;
+};
+
+template <class Codec>
+struct __align__(128) XSmem {
+  typename Codec::Out staging[XWARPS][2][Codec::STAGE];
+  PartCounts counts[2];
+  uint32_t scratch[2 * XWARPS + 2];
+  unsigned long long sums[XWARPS];
+  unsigned long long red[XWARPS];
+  uint32_t ticket;
+  int is_last;
+};
+
+// Virtual position of lane `lane`'s chunk in region r of warp w's slice of partition part.
+__device__ __forceinline__ long long chunk_pos(uint32_t part, int w, int r, int lane) {
+  return (long long)part * PART_BYTES + (long long)w * SLICE_BYTES + (long long)r * REGION_BYTES +
+         (long long)lane * CHUNK;
+}
+
+// Counts partition `part` into pc (all threads).  Region (w, r)'s units are summed by warp w
+// (two regions packed per register), then warp 0 turns the 128 counts into offsets.
+template <class Codec>
+__device__ __forceinline__ void count_partition(const Params &p, uint32_t part, PartCounts &pc) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const long long p0 = (long long)part * PART_BYTES;
+  const long long lo = p.off0, hi = (long long)p.vbytes;
+  const bool inside = p0 >= lo && p0 + (long long)PART_BYTES <= hi;
+  uint4 v[PART_ROUNDS];
+#pragma unroll
+  for (int r = 0; r < PART_ROUNDS; ++r) v[r] = load_chunk(p, chunk_pos(part, warp, r, lane), inside);
+  uint32_t packed[PART_ROUNDS / 2];
+#pragma unroll
+  for (int r = 0; r < PART_ROUNDS; r += 2) {
+    uint32_t a[2];
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      const long long c = chunk_pos(part, warp, r + q, lane);
+      const bool edge = !inside && (c < lo || c + 16 > hi);
+      a[q] = Codec::count(p, v[r + q], c, edge);
+    }
+    packed[r / 2] = a[0] | (a[1] << 16);  // a region has at most 32 x 48 units
+  }
+#pragma unroll
+  for (int i = 0; i < PART_ROUNDS / 2; ++i) {
+#pragma unroll
+    for (int d = 16; d >= 1; d >>= 1) packed[i] += __shfl_xor_sync(0xffffffffu, packed[i], d);
+  }
+  if (lane == 0) {
+#pragma unroll
+    for (int r = 0; r < PART_ROUNDS; ++r)
+      pc.off[warp * PART_ROUNDS + r] = (packed[r / 2] >> (16 * (r & 1))) & 0xFFFFu;
+  }
+  __syncthreads();
+  if (warp == 0) {
+    constexpr int PER = PART_ROUNDS * XWARPS / 32;  // consecutive values per lane
+    uint32_t vals[PER], s = 0;
+#pragma unroll
+    for (int i = 0; i < PER; ++i) {
+      vals[i] = pc.off[lane * PER + i];
+      s += vals[i];
+    }
+    uint32_t incl = s;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, incl, d);
+      if (lane >= d) incl += y;
+    }
+    uint32_t run = incl - s;
+#pragma unroll
+    for (int i = 0; i < PER; ++i) {
+      pc.off[lane * PER + i] = run;
+      run += vals[i];
+    }
+    if (lane == 31) pc.total = incl;
+  }
+  __syncthreads();
+}
+
+// Writes the region's staged units [skip, cnt + extra), which start at global unit S (one
+// warp).  Staged index h + k holds global unit S + k with h = (dshift + S) & (V - 1), so
+// staged chunk boundaries fall on 16-byte destination boundaries; units at or past cap are
+// not written.  Lane 0 issues the bulk store of the whole 16-byte chunks and commits it as
+// one bulk group; the lanes write the ragged ends.  Every lane that wrote the staging
+// buffer must have run fence_proxy_async_smem() before the __syncwarp preceding this call.
+template <typename U>
+__device__ __forceinline__ void store_region(const Params &p, const U *staging, uint64_t S,
+                                             uint32_t skip, uint32_t cnt, uint32_t extra) {
+  constexpr uint32_t V = 16 / sizeof(U);
+  const int lane = threadIdx.x & 31;
+  const uint32_t h = (uint32_t)((p.dshift + S) & (V - 1));
+  uint64_t lim = (uint64_t)cnt + extra;
+  if (S >= p.cap) lim = 0;
+  else if (p.cap - S < lim) lim = p.cap - S;
+  const uint64_t A0 = (p.dshift + S) - h;
+  U *gdst = reinterpret_cast<U *>(p.dbase) + A0;
+  const uint32_t beg = h + (skip < lim ? skip : (uint32_t)lim);
+  const uint32_t end = h + (uint32_t)lim;
+  const uint32_t first_full = (beg + V - 1) / V;
+  const uint32_t last_full = end / V;
+  if (first_full < last_full) {
+    if (lane == 0)
+      bulk_store(gdst + first_full * V, staging + first_full * V, (last_full - first_full) * 16u);
+    for (uint32_t i = beg + lane; i < first_full * V; i += 32) gdst[i] = staging[i];
+    for (uint32_t i = last_full * V + lane; i < end; i += 32) gdst[i] = staging[i];
+  } else {
+    for (uint32_t i = beg + lane; i < end; i += 32) gdst[i] = staging[i];
+  }
+  if (lane == 0) bulk_commit();
+}
+
+// Warp-level exclusive scan of per-lane counts; *total receives the warp sum.
+__device__ __forceinline__ uint32_t warp_exclusive_scan(uint32_t x, uint32_t *total) {
+  const int lane = threadIdx.x & 31;
+  uint32_t incl = x;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, incl, d);
+    if (lane >= d) incl += y;
+  }
+  *total = __shfl_sync(0xffffffffu, incl, 31);
+  return incl - x;
+}
+
+// The whole transcoder kernel body.  finalize(status, key, total) runs in thread 0 of the
+// last CTA and writes the result.
+template <class Codec, class Final>
+__device__ __forceinline__ void transcode(const Params &p, XSmem<Codec> &sm, Final finalize) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const uint32_t epoch = p.ws->epoch;
+  const long long lo = p.off0, hi = (long long)p.vbytes;
+  unsigned long long err_pos = NO_ERROR;
+  uint32_t use = 0;  // regions staged by this warp (picks the staging buffer)
+  int cb = 0;        // which counts[] holds the current partition
+
+  if (tid == 0) sm.ticket = atomicAdd(&p.ws->ticket, 1u);
+  __syncthreads();
+  uint32_t cur = sm.ticket;
+  if (cur < p.ntiles) {
+    count_partition<Codec>(p, cur, sm.counts[cb]);
+    if (tid == 0) {
+      publish_aggregate(p, cur, sm.counts[cb].total, epoch);
+      atomicAdd(&p.ws->total, (unsigned long long)sm.counts[cb].total);
+    }
+  }
+  while (cur < p.ntiles) {
+    // claim and count the next partition, so that its aggregate is out a partition early
+    if (tid == 0) sm.ticket = atomicAdd(&p.ws->ticket, 1u);
+    __syncthreads();
+    const uint32_t nxt = sm.ticket;
+    if (nxt < p.ntiles) {
+      count_partition<Codec>(p, nxt, sm.counts[cb ^ 1]);
+      if (tid == 0) {
+        publish_aggregate(p, nxt, sm.counts[cb ^ 1].total, epoch);
+        atomicAdd(&p.ws->total, (unsigned long long)sm.counts[cb ^ 1].total);
+      }
+    }
+    const uint64_t S0 = lookback_cta<XT>(p, cur, sm.counts[cb].total, epoch, sm.scratch, sm.sums);
+
+    // this warp's slice: the words just before and after it, and its first chunk
+    const long long s0 = chunk_pos(cur, warp, 0, 0);
+    const bool slice_inside = s0 - 4 >= lo && s0 + (long long)SLICE_BYTES + 4 <= hi;
+    const uint32_t before = slice_inside ? ldg_word(p.base + s0 - 4) : load_word_checked(p, s0 - 4);
+    const uint32_t after =
+        slice_inside ? ldg_word(p.base + s0 + SLICE_BYTES) : load_word_checked(p, s0 + SLICE_BYTES);
+    uint4 v_next = load_chunk(p, s0 + CHUNK * lane, slice_inside);
+    uint32_t prev_last = before;  // last word of the previous region (lane 31's), for lane 0
+#pragma unroll 1
+    for (int r = 0; r < PART_ROUNDS; ++r, ++use) {
+      const long long c = s0 + (long long)r * REGION_BYTES + CHUNK * lane;
+      const bool edge = c < lo || c + 16 > hi;
+      const uint4 v = v_next;
+      if (r + 1 < PART_ROUNDS) v_next = load_chunk(p, c + REGION_BYTES, slice_inside);
+      uint32_t prev = __shfl_up_sync(0xffffffffu, v.w, 1);
+      uint32_t next = __shfl_down_sync(0xffffffffu, v.x, 1);
+      const uint32_t next_first = __shfl_sync(0xffffffffu, v_next.x, 0);  // next region's first word
+      if (lane == 0) prev = prev_last;
+      if (lane == 31) next = r + 1 < PART_ROUNDS ? next_first : after;
+      prev_last = __shfl_sync(0xffffffffu, v.w, 31);
+
+      typename Codec::Out *st = sm.staging[warp][use & 1];
+      const uint64_t S = S0 + sm.counts[cb].off[warp * PART_ROUNDS + r];
+      constexpr uint32_t V = 16 / sizeof(typename Codec::Out);
+      const uint32_t h = (uint32_t)((p.dshift + S) & (V - 1));
+      if (lane == 0) bulk_wait_read<1>();  // the store of two regions ago has read this buffer
+      __syncwarp();
+      const Region g = Codec::convert(p, v, prev, next, c, edge, st, h, err_pos);
+      fence_proxy_async_smem();
+      __syncwarp();
+      store_region(p, st, S, g.skip, g.total, g.extra);
+    }
+    cur = nxt;
+    cb ^= 1;
+    __syncthreads();  // counts[cb ^ 1] is rewritten by the next count pass
+  }
+  if (lane == 0) bulk_wait_all<0>();
+
+  if (!fold_and_finish<XT>(p, err_pos, true, sm.red, &sm.is_last)) return;
+  if (tid == 0) {
+    WsHeader *ws = p.ws;
+    const uint32_t status = *(volatile uint32_t *)&ws->status;
+    const unsigned long long key = *(volatile unsigned long long *)&ws->errkey;
+    const unsigned long long tot = *(volatile unsigned long long *)&ws->total;
+    finalize(status, key, tot);
+  }
+  reset_workspace(p);
+}
+
+}  // namespace gbu

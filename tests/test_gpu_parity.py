@@ -13,7 +13,9 @@ from gpu_helpers import char_starts_utf8, check_utf16_input, check_utf8_input
 
 pytestmark = pytest.mark.gpu
 
-TILE = 4096  # input bytes per tile in the library
+TILE = 4096    # bytes per streaming warp tile
+TTILE = 8192   # bytes per transcoder round (512-byte regions per warp)
+PART = 65536   # bytes per transcoder partition (the unit of the look-back)
 
 
 @pytest.fixture(scope="module")
@@ -102,10 +104,11 @@ INVALID_UTF8 = [bytes.fromhex(h) for h in (
 
 
 def test_errors_near_tile_and_warp_boundaries(codec, torch):
-    base = _mixed(6 * TILE, 3)
+    base = _mixed(PART + 2 * TILE, 3)
     starts = char_starts_utf8(base)
     targets = []
-    for b in (TILE, 2 * TILE, 3 * TILE, 512, 1024 + 512, 5 * TILE):
+    for b in (TILE, 2 * TILE, 3 * TILE, 512, 1024 + 512, 5 * TILE, TTILE + 16, 2 * TTILE - 16,
+              PART, PART + 512):
         targets += [b - 5, b - 4, b - 3, b - 2, b - 1, b, b + 1, b + 2, b + 3]
     targets += [0, 1, 2, 15, 16, 17]
     for t in targets:
@@ -221,12 +224,12 @@ def test_wait_timeout_is_reported_and_recovered(codec, torch):
     """A tile that never publishes its scan state: the waits give up, the call reports
     GBU_TIMEOUT, and the next call on the same context is correct again."""
     from paper_2111_08692_gb300 import result_tuple
-    data = _mixed(8 * TILE, 17)
+    data = _mixed(6 * PART, 17)
     src = torch.from_numpy(data).to("cuda")
     cap = oracle.utf16_length_from_utf8(data)
     dst = torch.empty(cap, dtype=torch.int16, device="cuda")
     codec.set_wait_limit(2000)
-    codec.debug_skip_publish(2)
+    codec.debug_skip_publish(2)  # partition 3 must look back past it
     try:
         r = result_tuple(codec.convert_utf8_to_utf16le(src, dst))
     finally:
