@@ -1,0 +1,164 @@
+// gbu_codec_utf16.cuh -- the UTF-16LE -> UTF-8 codec (validating), used by the single-buffer
+// transcoder (gbu_utf16.cu) and the batched kernels (gbu_batch.cu).
+//
+// Paper Section 3: words 0000-D7FF and E000-FFFF are characters by themselves; a word in
+// D800-DBFF must be followed by one in DC00-DFFF and the pair encodes
+// ((first & 0x3FF) << 10 | (second & 0x3FF)) + 0x10000.  Section 4 routes whole registers
+// by range (all ASCII, all below 0x800, no surrogates, else a scalar fallback); here a warp
+// handles a 512-byte region, 8 words (16 bytes) per lane:
+//   * a word is in error when it is a first surrogate not followed by a second one, or a
+//     second surrogate not preceded by a first one (neighbours come from adjacent lanes);
+//   * UTF-8 sizes: 1 byte below 0x80, 2 below 0x800, 3 otherwise, and 2 per surrogate word:
+//     the first word of a pair writes all 4 bytes of the character, over its own 2 slots and
+//     its partner's, and the second word writes nothing.  A pair cut by a region boundary is
+//     written by the region holding its first word (2 bytes past its end), and the next
+//     region leaves its first 2 slots alone;
+//   * an all-ASCII warp narrows words to bytes directly (Section 4's ASCII route);
+//   * other words are encoded one at a time into the warp's staging buffer.
+#pragma once
+
+#include <stdint.h>
+
+#include "gbu_chunk.cuh"
+#include "gbu_device.cuh"
+#include "gbu_xcode.cuh"
+
+namespace gbu {
+
+struct Utf16ToUtf8 {
+  using Out = uint8_t;
+  // a region of 256 words yields at most 768 bytes, +2 for a pair cut at its end, plus 15
+  // bytes of alignment slack
+  static constexpr uint32_t STAGE = 3 * 256 + 32;
+
+  __device__ __forceinline__ static uint32_t count(const Params &p, uint4 v, long long c, bool edge) {
+    const uint32_t W[4] = {v.x, v.y, v.z, v.w};
+    if (!edge && ((W[0] | W[1] | W[2] | W[3]) & 0xFF80FF80u) == 0) return 8;  // all ASCII
+    uint32_t cnt = 0;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const uint32_t w = (W[j >> 1] >> (16 * (j & 1))) & 0xFFFFu;
+      const bool valid = !edge || (c + 2 * j >= (long long)p.off0 && c + 2 * j < (long long)p.vbytes);
+      cnt += valid ? len8_of_word(w) : 0u;
+    }
+    return cnt;
+  }
+
+  __device__ __forceinline__ static Region convert(const Params &p, uint4 v, uint32_t prev,
+                                                   uint32_t next, long long c, bool edge,
+                                                   uint8_t *st, uint32_t base,
+                                                   unsigned long long &err_pos) {
+    const int lane = threadIdx.x & 31;
+    if (__all_sync(0xffffffffu, ((v.x | v.y | v.z | v.w) & 0xFF80FF80u) == 0 && !edge)) {
+      // an all-ASCII region: one byte per word, no surrogate among its words (a first
+      // surrogate just before the region is judged by the region that owns it)
+      const uint32_t x0 = base + 8 * lane;
+      const uint32_t lo8 = __byte_perm(v.x, v.y, 0x6420);
+      const uint32_t hi8 = __byte_perm(v.z, v.w, 0x6420);
+      if ((x0 & 7) == 0) {
+        *reinterpret_cast<uint2 *>(st + x0) = make_uint2(lo8, hi8);
+      } else if ((x0 & 3) == 0) {
+        reinterpret_cast<uint32_t *>(st + x0)[0] = lo8;
+        reinterpret_cast<uint32_t *>(st + x0)[1] = hi8;
+      } else {
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+          st[x0 + b] = (uint8_t)(lo8 >> (8 * b));
+          st[x0 + 4 + b] = (uint8_t)(hi8 >> (8 * b));
+        }
+      }
+      return Region{256u, 0u, 0u, 256u};
+    }
+    const uint32_t W[4] = {v.x, v.y, v.z, v.w};
+    uint32_t u[10];  // u[0] = word before the chunk, u[1..8] own words, u[9] = word after
+    u[0] = prev >> 16;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      u[1 + 2 * k] = W[k] & 0xFFFFu;
+      u[2 + 2 * k] = W[k] >> 16;
+    }
+    u[9] = next & 0xFFFFu;
+    bool valid[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j)
+      valid[j] = !edge || (c + 2 * j >= (long long)p.off0 && c + 2 * j < (long long)p.vbytes);
+
+    const uint32_t nonascii = (W[0] | W[1] | W[2] | W[3]) & 0xFF80FF80u;
+    const bool warp_ascii = __all_sync(0xffffffffu, nonascii == 0 && !edge);
+    uint32_t cnt = 0;
+    uint32_t sz[8];
+    bool err = false;
+    if (warp_ascii) {
+      cnt = 8;
+    } else {
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const uint32_t w = u[j + 1];
+        sz[j] = valid[j] ? len8_of_word(w) : 0u;
+        cnt += sz[j];
+        const bool hw = is_high16(w), lw = is_low16(w);
+        err |= valid[j] && ((hw && !is_low16(u[j + 2])) || (lw && !is_high16(u[j])));
+      }
+    }
+    if (err && (unsigned long long)c < err_pos) err_pos = (unsigned long long)c;
+
+    Region g;
+    const uint32_t x0 = base + warp_exclusive_scan(cnt, &g.total);
+    g.units = g.total;
+    // a pair cut by the region's start or end (lane 0's first word, lane 31's last word)
+    const bool cut_start = valid[0] && is_low16(u[1]) && is_high16(u[0]);
+    const bool cut_end = valid[7] && is_high16(u[8]) && is_low16(u[9]);
+    g.skip = __shfl_sync(0xffffffffu, cut_start ? 2u : 0u, 0);
+    g.extra = __shfl_sync(0xffffffffu, cut_end ? 2u : 0u, 31);
+    if (warp_ascii) {
+      const uint32_t lo8 = __byte_perm(W[0], W[1], 0x6420);
+      const uint32_t hi8 = __byte_perm(W[2], W[3], 0x6420);
+      if ((x0 & 7) == 0) {
+        *reinterpret_cast<uint2 *>(st + x0) = make_uint2(lo8, hi8);
+      } else if ((x0 & 3) == 0) {
+        reinterpret_cast<uint32_t *>(st + x0)[0] = lo8;
+        reinterpret_cast<uint32_t *>(st + x0)[1] = hi8;
+      } else {
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+          st[x0 + b] = (uint8_t)(lo8 >> (8 * b));
+          st[x0 + 4 + b] = (uint8_t)(hi8 >> (8 * b));
+        }
+      }
+    } else if (x0 + cnt + 2 <= STAGE) {  // else: after the first error, nothing to store
+      const bool has_sur = __any_sync(0xffffffffu, ((W[0] | W[1] | W[2] | W[3]) & 0x80008000u) != 0);
+      uint32_t o = x0;
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const uint32_t w = u[j + 1];
+        uint32_t nb = sz[j];  // bytes written by this word
+        // the one-, two- and three-byte forms (a lone surrogate takes the two-byte form's
+        // slots with unspecified bytes: it only occurs after the first error)
+        const uint32_t b2 = 0x80C0u | (w >> 6) | ((w & 0x3Fu) << 8);
+        const uint32_t b3 = 0x8080E0u | (w >> 12) | (((w >> 6) & 0x3Fu) << 8) | ((w & 0x3Fu) << 16);
+        uint32_t bytes = nb == 1 ? w : (nb == 2 ? b2 : b3);
+        if (has_sur) {
+          if (is_high16(w) && is_low16(u[j + 2])) {
+            const uint32_t cp = (((w & 0x3FFu) << 10) | (u[j + 2] & 0x3FFu)) + 0x10000u;
+            bytes = (0xF0u | (cp >> 18)) | ((0x80u | ((cp >> 12) & 0x3Fu)) << 8) |
+                    ((0x80u | ((cp >> 6) & 0x3Fu)) << 16) | ((0x80u | (cp & 0x3Fu)) << 24);
+            nb = valid[j] ? 4u : 0u;
+          } else if (is_low16(w) && is_high16(u[j])) {
+            nb = 0;  // written with its first word
+          }
+        }
+#pragma unroll
+        for (uint32_t q = 0; q < 4; ++q)
+          if (q < nb) st[o + q] = (uint8_t)(bytes >> (8 * q));
+        o += sz[j];
+      }
+    }
+    if (g.total + g.extra > STAGE - base) {  // only after the first error
+      g.extra = 0;
+      if (g.total > STAGE - base) g.total = STAGE - base;
+    }
+    return g;
+  }
+};
+
+}  // namespace gbu

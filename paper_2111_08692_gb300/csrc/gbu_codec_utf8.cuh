@@ -1,0 +1,190 @@
+// gbu_codec_utf8.cuh -- the UTF-8 -> UTF-16LE codec (validating), used by the single-buffer
+// transcoder (gbu_utf8.cu) and the batched kernels (gbu_batch.cu).
+//
+// Paper Section 3 defines both formats; Section 5 states that transcoding validates.
+// Section 4's design (64-byte blocks, a 12-byte shuffle-table routine) is a 128-bit-register
+// idiom; here a warp handles a 512-byte region, one 16-byte chunk per lane:
+//   * the chunk is classified and validated as in gbu_chunk.cuh;
+//   * output: one UTF-16 word per leading byte, two for a four-byte sequence, counted on the
+//     leading byte; word offsets are prefix sums of per-byte counts (bytes inside a word via
+//     a multiply by 0x01010101, lanes via a warp scan, regions via the partition count, and
+//     partitions via the look-back);
+//   * an all-ASCII warp widens its bytes directly (Section 4's ASCII path).
+// A lane whose chunk breaks any check reports the chunk start; the last CTA turns the
+// smallest one into the exact offset and kind (resolve_utf8_error).
+#pragma once
+
+#include <stdint.h>
+
+#include "gbu_chunk.cuh"
+#include "gbu_device.cuh"
+#include "gbu_xcode.cuh"
+
+namespace gbu {
+
+// Stores 16 UTF-16 words (8 packed words) at staging index x.
+__device__ __forceinline__ void stage16(uint16_t *st, uint32_t x, const uint32_t u[8]) {
+  if ((x & 7) == 0) {
+    uint4 *d = reinterpret_cast<uint4 *>(st + x);
+    d[0] = make_uint4(u[0], u[1], u[2], u[3]);
+    d[1] = make_uint4(u[4], u[5], u[6], u[7]);
+  } else if ((x & 1) == 0) {
+    uint32_t *d = reinterpret_cast<uint32_t *>(st + x);
+#pragma unroll
+    for (int j = 0; j < 8; ++j) d[j] = u[j];
+  } else {
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      st[x + 2 * j] = (uint16_t)(u[j] & 0xFFFF);
+      st[x + 2 * j + 1] = (uint16_t)(u[j] >> 16);
+    }
+  }
+}
+
+struct Utf8ToUtf16 {
+  using Out = uint16_t;
+  // a valid 512-byte region yields at most 512 words (+1 for a four-byte lead in its last
+  // byte), plus 7 words of alignment slack; words past this can only come from bytes after
+  // the first error and are dropped
+  static constexpr uint32_t STAGE = 512 + 16 + 16;
+
+  __device__ __forceinline__ static uint32_t count(const Params &p, uint4 v, long long c, bool edge) {
+    const uint32_t W[4] = {v.x, v.y, v.z, v.w};
+    if (!edge && ((W[0] | W[1] | W[2] | W[3]) & 0x80808080u) == 0) return 16;  // all ASCII
+    uint32_t cnt = 0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const Flags8 f = classify8(W[k]);
+      const uint32_t vm = edge ? byte_range_mask(c + 4 * k, p.off0, (long long)p.vbytes) : 0x80808080u;
+      cnt += __popc(~f.isC & vm) + __popc(f.geF0 & vm);
+    }
+    return cnt;
+  }
+
+  // Validates the chunk and stages its UTF-16 words.  Offsets come first (per-byte counts,
+  // then a warp scan), so each pair of positions is decoded and stored in one pass without
+  // keeping decoded words in registers.
+  __device__ __forceinline__ static Region convert(const Params &p, uint4 v, uint32_t prev,
+                                                   uint32_t next, long long c, bool edge,
+                                                   uint16_t *st, uint32_t base,
+                                                   unsigned long long &err_pos) {
+    const int lane = threadIdx.x & 31;
+    if (__all_sync(0xffffffffu, ((v.x | v.y | v.z | v.w) & 0x80808080u) == 0 && !edge)) {
+      // an all-ASCII region: one word per byte; the only possible error is a leading byte
+      // just before the region that wants continuation bytes inside it (lane 0's chunk)
+      if (lane == 0) {
+        const Flags8 fp = classify8(prev);
+        const uint32_t req = __funnelshift_l(fp.geC0, 0u, 8) | __funnelshift_l(fp.geE0, 0u, 16) |
+                             __funnelshift_l(fp.geF0, 0u, 24);
+        if (req && (unsigned long long)c < err_pos) err_pos = (unsigned long long)c;
+      }
+      uint32_t u[8];
+      u[0] = __byte_perm(v.x, 0, 0x4140); u[1] = __byte_perm(v.x, 0, 0x4342);
+      u[2] = __byte_perm(v.y, 0, 0x4140); u[3] = __byte_perm(v.y, 0, 0x4342);
+      u[4] = __byte_perm(v.z, 0, 0x4140); u[5] = __byte_perm(v.z, 0, 0x4342);
+      u[6] = __byte_perm(v.w, 0, 0x4140); u[7] = __byte_perm(v.w, 0, 0x4342);
+      stage16(st, base + 16 * lane, u);
+      return Region{512u, 0u, 0u, 512u};
+    }
+    uint32_t W[6];
+    W[0] = prev;
+    W[1] = v.x; W[2] = v.y; W[3] = v.z; W[4] = v.w;
+    W[5] = next;
+    Flags8 f[5];
+#pragma unroll
+    for (int k = 0; k < 5; ++k) f[k] = classify8(W[k]);
+    uint32_t uw[4];  // per byte: UTF-16 words produced at that position (0, 1 or 2)
+    uint32_t cnt = 0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      uint32_t vm = 0x80808080u;
+      if (edge) vm = byte_range_mask(c + 4 * k, p.off0, (long long)p.vbytes);
+      uw[k] = ((~f[k + 1].isC & vm) >> 7) + ((f[k + 1].geF0 & vm) >> 7);
+      cnt = __dp4a(uw[k], 0x01010101u, cnt);
+    }
+    uint32_t err = utf8_structure_errors(f);
+    const uint32_t nonascii = (W[1] | W[2] | W[3] | W[4]) & 0x80808080u;
+    const bool warp_ascii = __all_sync(0xffffffffu, nonascii == 0 && !edge);
+
+    Region g;
+    const uint32_t x0 = base + warp_exclusive_scan(cnt, &g.total);
+    g.skip = 0;
+    g.extra = 0;
+    // a chunk that would overflow the staging buffer lies after the first error: it stores
+    // nothing (its validation still runs)
+    const bool store = x0 + cnt <= STAGE;
+    if (warp_ascii) {
+      uint32_t u[8];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        u[2 * k] = __byte_perm(W[k + 1], 0, 0x4140);
+        u[2 * k + 1] = __byte_perm(W[k + 1], 0, 0x4342);
+      }
+      stage16(st, x0, u);  // an all-ASCII region fits: x0 + 16 <= 7 + 512
+    } else {
+      uint32_t c2 = 0, c3 = 0, c4 = 0;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        c2 |= f[k + 1].geC0 & ~f[k + 1].geE0;
+        c3 |= f[k + 1].geE0 & ~f[k + 1].geF0;
+        c4 |= f[k + 1].geF0;
+      }
+      const bool has2 = __any_sync(0xffffffffu, c2 != 0);
+      const bool has3 = __any_sync(0xffffffffu, c3 != 0);
+      const bool has4 = __any_sync(0xffffffffu, c4 != 0);
+      uint32_t bad = 0;
+      uint32_t addr = x0;
+      // pair i covers positions 2i, 2i+1: E = bytes (2i, 2i+1), O = bytes (2i+1, 2i+2); the
+      // next pair's E and O supply the third and fourth bytes of a sequence
+      uint32_t E = __byte_perm(W[1], W[2], selE(0));
+      uint32_t O = __byte_perm(W[1], W[2], selO(0));
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const int k = i >> 1, h = i & 1;
+        const int kn = (i + 1) >> 1, hn = (i + 1) & 1;
+        const uint32_t En = __byte_perm(W[kn + 1], W[kn + 2 <= 5 ? kn + 2 : 5], selE(hn));
+        const uint32_t On = __byte_perm(W[kn + 1], W[kn + 2 <= 5 ? kn + 2 : 5], selO(hn));
+        uint32_t r = E & 0x00FF00FFu;
+        uint32_t lo4 = 0;
+        const uint32_t U2 = ((E << 6) & 0x07C007C0u) | (O & 0x003F003Fu);
+        if (has2) {
+          const uint32_t M2 = prmt(f[k + 1].geC0 & ~f[k + 1].geE0, 0, selM(h));
+          const uint32_t t = E & 0x001E001Eu;  // U2 < 0x80 exactly when the lead is C0/C1
+          bad |= ~(t + 0x7FFF7FFFu) & M2 & 0x80008000u;
+          r = (U2 & M2) | (r & ~M2);
+        }
+        if (has3) {
+          const uint32_t M3 = prmt(f[k + 1].geE0 & ~f[k + 1].geF0, 0, selM(h));
+          const uint32_t U3 = ((U2 << 6) & 0xFFC0FFC0u) | (En & 0x003F003Fu);
+          const uint32_t t = (U3 >> 11) & 0x001F001Fu;  // 0: below U+800; 0x1B: D800-DFFF
+          bad |= ~((t + 0x7FFF7FFFu) & ((t ^ 0x001B001Bu) + 0x7FFF7FFFu)) & M3 & 0x80008000u;
+          r = (U3 & M3) | (r & ~M3);
+        }
+        if (has4) {
+          const uint32_t M4 = prmt(f[k + 1].geF0, 0, selM(h));
+          const uint32_t hi = (U2 << 2) + ((En >> 4) & 0x00030003u) + 0xC7C0C7C0u;
+          const uint32_t t = ((hi ^ 0xD800D800u) >> 10) & 0x003F003Fu;  // 0 iff U+10000-10FFFF
+          bad |= (t + 0x7FFF7FFFu) & M4 & 0x80008000u;
+          r = (hi & M4) | (r & ~M4);
+          lo4 = ((En << 6) & 0x03C003C0u) | (On & 0x003F003Fu) | 0xDC00DC00u;
+        }
+        const uint32_t ua = (uw[k] >> (16 * h)) & 3u, ub = (uw[k] >> (16 * h + 8)) & 3u;
+        if (store && ua) st[addr] = (uint16_t)r;
+        if (has4 && store && ua == 2) st[addr + 1] = (uint16_t)lo4;
+        addr += ua;
+        if (store && ub) st[addr] = (uint16_t)(r >> 16);
+        if (has4 && store && ub == 2) st[addr + 1] = (uint16_t)(lo4 >> 16);
+        addr += ub;
+        E = En;
+        O = On;
+      }
+      err |= bad;
+    }
+    if (err && (unsigned long long)c < err_pos) err_pos = (unsigned long long)c;
+    g.units = g.total;
+    if (g.total > STAGE - base) g.total = STAGE - base;  // only after the first error
+    return g;
+  }
+};
+
+}  // namespace gbu

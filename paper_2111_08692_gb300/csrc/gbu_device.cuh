@@ -136,6 +136,28 @@ __device__ __forceinline__ uint32_t ldg_word(const uint8_t *p) {
   return __ldg(reinterpret_cast<const unsigned int *>(p));
 }
 
+// L2 cache policies: keep a line resident (it will be read again soon), or mark it as the
+// line's last use.
+__device__ __forceinline__ uint64_t l2_policy_keep() {
+  uint64_t pol;
+  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+  return pol;
+}
+__device__ __forceinline__ uint64_t l2_policy_last_use() {
+  uint64_t pol;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+  return pol;
+}
+
+// 16-byte streaming load with an L2 cache policy
+__device__ __forceinline__ uint4 ldg_stream_hint(const uint8_t *p, uint64_t pol) {
+  uint4 v;
+  asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.v4.u32 {%0, %1, %2, %3}, [%4], %5;"
+               : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+               : "l"(p), "l"(pol));
+  return v;
+}
+
 // PRMT with the full 4-bit selector nibbles (bit 3 = replicate the sign bit of the selected
 // byte); __byte_perm only honours the low three bits of each nibble.
 __device__ __forceinline__ uint32_t prmt(uint32_t a, uint32_t b, uint32_t sel) {
@@ -177,6 +199,18 @@ __device__ __forceinline__ uint32_t load_word_checked(const Params &p, long long
 // else byte by byte with bytes outside [off0, vbytes) read as zero.
 __device__ __forceinline__ uint4 load_chunk(const Params &p, long long c, bool inside) {
   if (inside) return ldg_stream(p.base + c);
+  uint4 v;
+  v.x = load_word_checked(p, c);
+  v.y = load_word_checked(p, c + 4);
+  v.z = load_word_checked(p, c + 8);
+  v.w = load_word_checked(p, c + 12);
+  return v;
+}
+
+// load_chunk with an L2 cache policy on the fast path.
+__device__ __forceinline__ uint4 load_chunk_hint(const Params &p, long long c, bool inside,
+                                                 uint64_t pol) {
+  if (inside) return ldg_stream_hint(p.base + c, pol);
   uint4 v;
   v.x = load_word_checked(p, c);
   v.y = load_word_checked(p, c + 4);

@@ -39,9 +39,10 @@ constexpr uint32_t REGION_BYTES = 32 * CHUNK;          // 512 bytes per warp per
 static_assert(SLICE_BYTES == REGION_BYTES * PART_ROUNDS, "a slice is PART_ROUNDS regions");
 
 struct Region {
-  uint32_t total;  // units counted for the region
+  uint32_t total;  // units to store for the region (clamped to the staging buffer)
   uint32_t skip;   // leading units written by the previous region (not to be stored here)
   uint32_t extra;  // units this region writes past its end (a pair cut by the region end)
+  uint32_t units;  // units counted for the region (unclamped: the region's output length)
 };
 
 struct __align__(16) PartCounts {
@@ -74,9 +75,12 @@ __device__ __forceinline__ void count_partition(const Params &p, uint32_t part, 
   const long long p0 = (long long)part * PART_BYTES;
   const long long lo = p.off0, hi = (long long)p.vbytes;
   const bool inside = p0 >= lo && p0 + (long long)PART_BYTES <= hi;
+  // the partition is read again by its conversion one partition later: keep it in L2
+  const uint64_t keep = l2_policy_keep();
   uint4 v[PART_ROUNDS];
 #pragma unroll
-  for (int r = 0; r < PART_ROUNDS; ++r) v[r] = load_chunk(p, chunk_pos(part, warp, r, lane), inside);
+  for (int r = 0; r < PART_ROUNDS; ++r)
+    v[r] = load_chunk_hint(p, chunk_pos(part, warp, r, lane), inside, keep);
   uint32_t packed[PART_ROUNDS / 2];
 #pragma unroll
   for (int r = 0; r < PART_ROUNDS; r += 2) {
@@ -211,14 +215,15 @@ __device__ __forceinline__ void transcode(const Params &p, XSmem<Codec> &sm, Fin
     const uint32_t before = slice_inside ? ldg_word(p.base + s0 - 4) : load_word_checked(p, s0 - 4);
     const uint32_t after =
         slice_inside ? ldg_word(p.base + s0 + SLICE_BYTES) : load_word_checked(p, s0 + SLICE_BYTES);
-    uint4 v_next = load_chunk(p, s0 + CHUNK * lane, slice_inside);
+    const uint64_t last_use = l2_policy_last_use();
+    uint4 v_next = load_chunk_hint(p, s0 + CHUNK * lane, slice_inside, last_use);
     uint32_t prev_last = before;  // last word of the previous region (lane 31's), for lane 0
 #pragma unroll 1
     for (int r = 0; r < PART_ROUNDS; ++r, ++use) {
       const long long c = s0 + (long long)r * REGION_BYTES + CHUNK * lane;
       const bool edge = c < lo || c + 16 > hi;
       const uint4 v = v_next;
-      if (r + 1 < PART_ROUNDS) v_next = load_chunk(p, c + REGION_BYTES, slice_inside);
+      if (r + 1 < PART_ROUNDS) v_next = load_chunk_hint(p, c + REGION_BYTES, slice_inside, last_use);
       uint32_t prev = __shfl_up_sync(0xffffffffu, v.w, 1);
       uint32_t next = __shfl_down_sync(0xffffffffu, v.x, 1);
       const uint32_t next_first = __shfl_sync(0xffffffffu, v_next.x, 0);  // next region's first word
