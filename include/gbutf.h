@@ -60,7 +60,8 @@ typedef enum {
   GBU_OUTPUT_TOO_SMALL = 16,
   GBU_BAD_ARGUMENT = 17,
   GBU_CUDA_ERROR = 18,
-  GBU_TIMEOUT = 19
+  GBU_TIMEOUT = 19,
+  GBU_NOALLOC_TOO_LARGE = 20 /* n above GBU_NOALLOC_MAX_UNITS (gbu_convert_utf8_to_utf16le_noalloc) */
 } gbu_status;
 
 typedef struct {
@@ -109,6 +110,27 @@ int gbu_convert_utf8_to_utf16le(gbu_ctx *ctx, const uint8_t *src, uint64_t n, ui
                                 uint64_t cap, gbu_result *result, gbu_stream stream);
 int gbu_convert_utf16le_to_utf8(gbu_ctx *ctx, const uint16_t *src, uint64_t n, uint8_t *dst,
                                 uint64_t cap, gbu_result *result, gbu_stream stream);
+
+/* Context-free, allocation-free form of gbu_convert_utf8_to_utf16le, for callers that cannot
+ * allocate device memory: creating a context calls cudaMalloc, which can synchronise the
+ * whole device (stalling every stream of a latency-bound serving loop) and fails where
+ * another allocator already owns the device's memory.  The paper has no counterpart: it is
+ * a deployment form of the same Section 3 / Section 5 transcoding, with identical results.
+ *
+ * The workspace is a static device array of the library (128 B + 8 B per 64 KiB partition),
+ * sized for n <= GBU_NOALLOC_MAX_UNITS bytes; a larger n returns GBU_NOALLOC_TOO_LARGE and
+ * enqueues nothing.  Runs on the CURRENT device.  The first call on each device does a
+ * one-time setup there (looks up the array's device address, queries the occupancy, clears
+ * the array with synchronous copies and a device synchronise), so make that first call before
+ * any stream capture.  The library never allocates on any call.
+ *
+ * There is ONE workspace per device, shared by every call: two calls whose kernels overlap
+ * (different streams, or threads, without ordering between them) race on it and both give
+ * undefined results.  Order them (one stream, or events).  Arguments, results, alignment and
+ * the other return values are as for gbu_convert_utf8_to_utf16le. */
+#define GBU_NOALLOC_MAX_UNITS ((uint64_t)1 << 28) /* 256 MiB of UTF-8 input */
+int gbu_convert_utf8_to_utf16le_noalloc(const uint8_t *src, uint64_t n, uint16_t *dst, uint64_t cap,
+                                        gbu_result *result, gbu_stream stream);
 
 /* Number of kernel launches the library made through this context so far (for accounting). */
 uint64_t gbu_launch_count(const gbu_ctx *ctx);

@@ -4,8 +4,9 @@ The work runs in the CUDA library built from ``csrc/`` (C ABI: ``include/gbutf.h
 ``binding`` is a thin ctypes layer over it.
 """
 from .binding import (  # noqa: F401
-    STATUS, STATUS_CODE, Codec, GbuError, GbuResult, gbu_convert_utf16le_to_utf8,
-    gbu_convert_utf8_to_utf16le, gbu_create, gbu_debug_skip_publish, gbu_destroy,
+    NOALLOC_MAX_UNITS, STATUS, STATUS_CODE, Codec, GbuError, GbuResult, gbu_convert_utf16le_to_utf8,
+    convert_utf8_to_utf16le_noalloc, gbu_convert_utf8_to_utf16le,
+    gbu_convert_utf8_to_utf16le_noalloc, gbu_create, gbu_debug_skip_publish, gbu_destroy,
     gbu_launch_config, gbu_launch_count, gbu_reset, gbu_set_wait_limit, gbu_utf16_length_from_utf8,
     gbu_utf8_length_from_utf16le, gbu_validate_utf16le, gbu_validate_utf8, lib, library_path,
     result_tuple)

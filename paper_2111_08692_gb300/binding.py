@@ -16,7 +16,10 @@ from . import build as _build
 STATUS = {
     0: "OK", 1: "HEADER_BITS", 2: "TOO_SHORT", 3: "TOO_LONG", 4: "OVERLONG", 5: "TOO_LARGE",
     6: "SURROGATE", 16: "OUTPUT_TOO_SMALL", 17: "BAD_ARGUMENT", 18: "CUDA_ERROR", 19: "TIMEOUT",
+    20: "NOALLOC_TOO_LARGE",
 }
+# Largest input (bytes) of gbu_convert_utf8_to_utf16le_noalloc (GBU_NOALLOC_MAX_UNITS).
+NOALLOC_MAX_UNITS = 1 << 28
 STATUS_CODE = {v: k for k, v in STATUS.items()}
 
 
@@ -68,6 +71,8 @@ def lib() -> ctypes.CDLL:
                 f = getattr(L, name)
                 f.restype = i32
                 f.argtypes = [vp, vp, u64, vp, u64, vp, vp]
+            L.gbu_convert_utf8_to_utf16le_noalloc.restype = i32
+            L.gbu_convert_utf8_to_utf16le_noalloc.argtypes = [vp, u64, vp, u64, vp, vp]
             _lib = L
     return _lib
 
@@ -126,6 +131,10 @@ def gbu_convert_utf8_to_utf16le(ctx, src, n, dst, cap, result, stream) -> int:
 
 def gbu_convert_utf16le_to_utf8(ctx, src, n, dst, cap, result, stream) -> int:
     return lib().gbu_convert_utf16le_to_utf8(ctx, src, n, dst, cap, result, stream)
+
+
+def gbu_convert_utf8_to_utf16le_noalloc(src, n, dst, cap, result, stream) -> int:
+    return lib().gbu_convert_utf8_to_utf16le_noalloc(src, n, dst, cap, result, stream)
 
 
 # ---- torch marshalling --------------------------------------------------------------------
@@ -244,3 +253,21 @@ class Codec:
                                            result.data_ptr(), self._stream(stream)),
                "gbu_convert_utf16le_to_utf8")
         return result
+
+
+def convert_utf8_to_utf16le_noalloc(src, dst, result, stream=None, cap=None):
+    """The context-free transcoder on the current device (no allocation: the caller passes
+    ``dst`` and ``result``).  ``src`` holds at most NOALLOC_MAX_UNITS bytes; calls must not
+    overlap one another (they share one workspace per device)."""
+    import torch
+    if src.numel() > NOALLOC_MAX_UNITS:
+        raise GbuError(f"gbu_convert_utf8_to_utf16le_noalloc: input of {src.numel()} bytes is above "
+                       f"the limit of {NOALLOC_MAX_UNITS} bytes of the allocation-free form")
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    s = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+    cap = dst.numel() if cap is None else cap
+    _check(gbu_convert_utf8_to_utf16le_noalloc(Codec._ptr(src), src.numel(), Codec._ptr(dst), cap,
+                                               result.data_ptr(), s),
+           "gbu_convert_utf8_to_utf16le_noalloc")
+    return result
