@@ -111,6 +111,94 @@ int gbu_convert_utf8_to_utf16le(gbu_ctx *ctx, const uint8_t *src, uint64_t n, ui
 int gbu_convert_utf16le_to_utf8(gbu_ctx *ctx, const uint16_t *src, uint64_t n, uint8_t *dst,
                                 uint64_t cap, gbu_result *result, gbu_stream stream);
 
+/* ---- Batched forms ------------------------------------------------------------------------
+ * The same six operations over B strings in ONE launch (a persistent grid; strings never wait
+ * on one another).  The strings lie back to back in src; string i is src[off[i] : off[i+1]]
+ * (code units of src).  off (B+1 entries), dst_off (B+1 entries), results (B entries) and
+ * lens (B entries) are 8-byte-aligned DEVICE arrays.  off and dst_off must be non-decreasing
+ * and inside their buffers (they are not checked; a decreasing pair reads as an empty
+ * string).  Each string's result is exactly the single-buffer call's result on that string
+ * alone: results[i] as for the single-buffer call (offsets relative to the string), lens[i]
+ * its output length.  Transcoders write string i's output to dst[dst_off[i] : dst_off[i+1]]
+ * (capacity dst_off[i+1] - dst_off[i]); dst_off is typically the exclusive scan of the
+ * batched length call (gbu_exclusive_scan_u64) or a worst-case layout (n units out per UTF-8
+ * unit in, 3 bytes out per UTF-16 unit in).  B == 0 enqueues nothing.  Return values as for
+ * the single-buffer calls; GBU_BAD_ARGUMENT also for a NULL or misaligned array when B > 0.
+ * The launch geometry is the context's per-operation gbu_batch_config (gbu_tune_batched picks
+ * it by timing).  No call allocates or synchronises, so all of them can be captured in a
+ * CUDA graph (gbu_graph_begin / gbu_graph_end).  Not in the paper, which handles one buffer
+ * per call: this is a serving form of the same per-string operations. */
+int gbu_validate_utf8_batched(gbu_ctx *ctx, const uint8_t *src, const uint64_t *off, uint64_t B,
+                              gbu_result *results, gbu_stream stream);
+int gbu_validate_utf16le_batched(gbu_ctx *ctx, const uint16_t *src, const uint64_t *off, uint64_t B,
+                                 gbu_result *results, gbu_stream stream);
+int gbu_utf16_length_from_utf8_batched(gbu_ctx *ctx, const uint8_t *src, const uint64_t *off, uint64_t B,
+                                       uint64_t *lens, gbu_stream stream);
+int gbu_utf8_length_from_utf16le_batched(gbu_ctx *ctx, const uint16_t *src, const uint64_t *off,
+                                         uint64_t B, uint64_t *lens, gbu_stream stream);
+int gbu_convert_utf8_to_utf16le_batched(gbu_ctx *ctx, const uint8_t *src, const uint64_t *off, uint64_t B,
+                                        uint16_t *dst, const uint64_t *dst_off, gbu_result *results,
+                                        gbu_stream stream);
+int gbu_convert_utf16le_to_utf8_batched(gbu_ctx *ctx, const uint16_t *src, const uint64_t *off, uint64_t B,
+                                        uint8_t *dst, const uint64_t *dst_off, gbu_result *results,
+                                        gbu_stream stream);
+
+/* out[k] = in[0] + ... + in[k-1] for k = 0 .. count (out has count + 1 entries, out[count] is
+ * the total): output offsets from batched lengths.  One launch, chained by a decoupled
+ * look-back (Merrill & Garland, 2016).  *result = {GBU_OK, total}; GBU_TIMEOUT as for the
+ * transcoders; GBU_BAD_ARGUMENT if the total reaches 2^44 (then out is not valid).  Needs
+ * count + 1 <= 4096 x (the context's tile states: max_units + 1 values always fit); returns
+ * GBU_BAD_ARGUMENT beyond. */
+int gbu_exclusive_scan_u64(gbu_ctx *ctx, const uint64_t *in, uint64_t count, uint64_t *out,
+                           gbu_result *result, gbu_stream stream);
+
+/* Operation codes of the batched calls (same order as gbu_launch_config). */
+typedef enum {
+  GBU_OP_VALIDATE_UTF8 = 0,
+  GBU_OP_UTF16_LENGTH_FROM_UTF8 = 1,
+  GBU_OP_CONVERT_UTF8_TO_UTF16LE = 2,
+  GBU_OP_VALIDATE_UTF16LE = 3,
+  GBU_OP_UTF8_LENGTH_FROM_UTF16LE = 4,
+  GBU_OP_CONVERT_UTF16LE_TO_UTF8 = 5
+} gbu_op;
+
+/* Launch geometry of a batched operation.  A CTA of warps_per_cta warps claims
+ * strings_per_claim consecutive strings at a time; each warp takes one string at a time,
+ * except that strings of at least long_bytes input bytes are handled afterwards by the whole
+ * CTA (warps_per_cta x 512 bytes per step). */
+typedef struct {
+  int32_t warps_per_cta;      /* 4, 8 or 16 (default 8) */
+  uint32_t strings_per_claim; /* 1 .. 1024 (default 64) */
+  uint32_t long_bytes;        /* >= 512 (default 4096) */
+  float tuned_ms;             /* the tuner's best time for this geometry; 0 if set by hand */
+} gbu_batch_config;
+
+int gbu_get_batch_config(const gbu_ctx *ctx, int op, gbu_batch_config *cfg);
+int gbu_set_batch_config(gbu_ctx *ctx, int op, const gbu_batch_config *cfg); /* checks ranges */
+/* Autotuner: runs operation `op` on the given batch (arguments as for the batched call of
+ * that operation; `out` is results or lens) for each candidate geometry (warps 4/8/16 x
+ * claims of 8/32/128/512 strings x long-string thresholds of 2/4/8/16 KiB), one untimed and
+ * `reps` timed launches each (CUDA events on `stream`), keeps the fastest in the context and
+ * writes it to *chosen (may be NULL).  The last launch uses the chosen geometry, so the
+ * outputs are valid.  Synchronous; not capturable. */
+int gbu_tune_batched(gbu_ctx *ctx, int op, const void *src, const uint64_t *off, uint64_t B, void *dst,
+                     const uint64_t *dst_off, void *out, int reps, gbu_stream stream,
+                     gbu_batch_config *chosen);
+
+/* ---- CUDA graphs --------------------------------------------------------------------------
+ * gbu_graph_begin starts capturing `stream` (not the legacy default stream); every library
+ * call made on it, by this thread, until gbu_graph_end is recorded instead of run (calls are
+ * launches only: none allocates or synchronises).  gbu_graph_end instantiates the graph
+ * (NULL on failure).  gbu_graph_launch replays it on any stream of the context's device; the
+ * pointers and sizes captured are fixed.  The context must outlive its graphs, and the
+ * one-stream-at-a-time rule of the context holds for replays too. */
+typedef struct gbu_graph gbu_graph;
+int gbu_graph_begin(gbu_ctx *ctx, gbu_stream stream);
+gbu_graph *gbu_graph_end(gbu_ctx *ctx, gbu_stream stream);
+int gbu_graph_launch(gbu_graph *graph, gbu_stream stream);
+uint64_t gbu_graph_kernels(const gbu_graph *graph); /* library kernels per replay */
+void gbu_graph_destroy(gbu_graph *graph);
+
 /* Context-free, allocation-free form of gbu_convert_utf8_to_utf16le, for callers that cannot
  * allocate device memory: creating a context calls cudaMalloc, which can synchronise the
  * whole device (stalling every stream of a latency-bound serving loop) and fails where

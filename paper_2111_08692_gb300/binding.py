@@ -27,6 +27,19 @@ class GbuResult(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int32), ("reserved", ctypes.c_int32), ("count", ctypes.c_uint64)]
 
 
+class GbuBatchConfig(ctypes.Structure):
+    _fields_ = [("warps_per_cta", ctypes.c_int32), ("strings_per_claim", ctypes.c_uint32),
+                ("long_bytes", ctypes.c_uint32), ("tuned_ms", ctypes.c_float)]
+
+    def as_dict(self) -> dict:
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+# Operation codes of the batched calls (gbu_op).
+OPS = ("validate_utf8", "utf16_length_from_utf8", "convert_utf8_to_utf16le", "validate_utf16le",
+       "utf8_length_from_utf16le", "convert_utf16le_to_utf8")
+OP_CODE = {name: i for i, name in enumerate(OPS)}
+
 _lock = threading.Lock()
 _lib = None
 
@@ -71,6 +84,34 @@ def lib() -> ctypes.CDLL:
                 f = getattr(L, name)
                 f.restype = i32
                 f.argtypes = [vp, vp, u64, vp, u64, vp, vp]
+            for name in ("gbu_validate_utf8_batched", "gbu_validate_utf16le_batched",
+                         "gbu_utf16_length_from_utf8_batched", "gbu_utf8_length_from_utf16le_batched"):
+                f = getattr(L, name)
+                f.restype = i32
+                f.argtypes = [vp, vp, vp, u64, vp, vp]
+            for name in ("gbu_convert_utf8_to_utf16le_batched", "gbu_convert_utf16le_to_utf8_batched"):
+                f = getattr(L, name)
+                f.restype = i32
+                f.argtypes = [vp, vp, vp, u64, vp, vp, vp, vp]
+            L.gbu_exclusive_scan_u64.restype = i32
+            L.gbu_exclusive_scan_u64.argtypes = [vp, vp, u64, vp, vp, vp]
+            L.gbu_get_batch_config.restype = i32
+            L.gbu_get_batch_config.argtypes = [vp, i32, ctypes.POINTER(GbuBatchConfig)]
+            L.gbu_set_batch_config.restype = i32
+            L.gbu_set_batch_config.argtypes = [vp, i32, ctypes.POINTER(GbuBatchConfig)]
+            L.gbu_tune_batched.restype = i32
+            L.gbu_tune_batched.argtypes = [vp, i32, vp, vp, u64, vp, vp, vp, i32, vp,
+                                           ctypes.POINTER(GbuBatchConfig)]
+            L.gbu_graph_begin.restype = i32
+            L.gbu_graph_begin.argtypes = [vp, vp]
+            L.gbu_graph_end.restype = vp
+            L.gbu_graph_end.argtypes = [vp, vp]
+            L.gbu_graph_launch.restype = i32
+            L.gbu_graph_launch.argtypes = [vp, vp]
+            L.gbu_graph_kernels.restype = u64
+            L.gbu_graph_kernels.argtypes = [vp]
+            L.gbu_graph_destroy.restype = None
+            L.gbu_graph_destroy.argtypes = [vp]
             L.gbu_convert_utf8_to_utf16le_noalloc.restype = i32
             L.gbu_convert_utf8_to_utf16le_noalloc.argtypes = [vp, u64, vp, u64, vp, vp]
             _lib = L
@@ -131,6 +172,68 @@ def gbu_convert_utf8_to_utf16le(ctx, src, n, dst, cap, result, stream) -> int:
 
 def gbu_convert_utf16le_to_utf8(ctx, src, n, dst, cap, result, stream) -> int:
     return lib().gbu_convert_utf16le_to_utf8(ctx, src, n, dst, cap, result, stream)
+
+
+def gbu_validate_utf8_batched(ctx, src, off, B, results, stream) -> int:
+    return lib().gbu_validate_utf8_batched(ctx, src, off, B, results, stream)
+
+
+def gbu_validate_utf16le_batched(ctx, src, off, B, results, stream) -> int:
+    return lib().gbu_validate_utf16le_batched(ctx, src, off, B, results, stream)
+
+
+def gbu_utf16_length_from_utf8_batched(ctx, src, off, B, lens, stream) -> int:
+    return lib().gbu_utf16_length_from_utf8_batched(ctx, src, off, B, lens, stream)
+
+
+def gbu_utf8_length_from_utf16le_batched(ctx, src, off, B, lens, stream) -> int:
+    return lib().gbu_utf8_length_from_utf16le_batched(ctx, src, off, B, lens, stream)
+
+
+def gbu_convert_utf8_to_utf16le_batched(ctx, src, off, B, dst, dst_off, results, stream) -> int:
+    return lib().gbu_convert_utf8_to_utf16le_batched(ctx, src, off, B, dst, dst_off, results, stream)
+
+
+def gbu_convert_utf16le_to_utf8_batched(ctx, src, off, B, dst, dst_off, results, stream) -> int:
+    return lib().gbu_convert_utf16le_to_utf8_batched(ctx, src, off, B, dst, dst_off, results, stream)
+
+
+def gbu_exclusive_scan_u64(ctx, src, count, out, result, stream) -> int:
+    return lib().gbu_exclusive_scan_u64(ctx, src, count, out, result, stream)
+
+
+def gbu_get_batch_config(ctx, op: int) -> GbuBatchConfig:
+    cfg = GbuBatchConfig()
+    _check(lib().gbu_get_batch_config(ctx, op, ctypes.byref(cfg)), "gbu_get_batch_config")
+    return cfg
+
+
+def gbu_set_batch_config(ctx, op: int, cfg: GbuBatchConfig) -> int:
+    return lib().gbu_set_batch_config(ctx, op, ctypes.byref(cfg))
+
+
+def gbu_tune_batched(ctx, op, src, off, B, dst, dst_off, out, reps, stream, chosen) -> int:
+    return lib().gbu_tune_batched(ctx, op, src, off, B, dst, dst_off, out, reps, stream, chosen)
+
+
+def gbu_graph_begin(ctx, stream) -> int:
+    return lib().gbu_graph_begin(ctx, stream)
+
+
+def gbu_graph_end(ctx, stream) -> int:
+    return lib().gbu_graph_end(ctx, stream)
+
+
+def gbu_graph_launch(graph, stream) -> int:
+    return lib().gbu_graph_launch(graph, stream)
+
+
+def gbu_graph_kernels(graph) -> int:
+    return lib().gbu_graph_kernels(graph)
+
+
+def gbu_graph_destroy(graph) -> None:
+    lib().gbu_graph_destroy(graph)
 
 
 def gbu_convert_utf8_to_utf16le_noalloc(src, n, dst, cap, result, stream) -> int:
@@ -246,6 +349,83 @@ class Codec:
                "gbu_convert_utf8_to_utf16le")
         return result
 
+    # batched forms: src is the concatenation, off the B+1 offsets (int64 tensor, code units)
+    def new_results(self, B: int):
+        return self.torch.empty((B, 2), dtype=self.torch.int64, device=f"cuda:{self.device}")
+
+    def _batched(self, fn, name, src, off, out, dst=None, dst_off=None, stream=None):
+        B = off.numel() - 1
+        args = [self.ctx, self._ptr(src), self._ptr(off), max(B, 0)]
+        if dst is not None:
+            args += [self._ptr(dst), self._ptr(dst_off)]
+        _check(fn(*args, self._ptr(out), self._stream(stream)), name)
+        return out
+
+    def validate_utf8_batched(self, src, off, results=None, stream=None):
+        results = self.new_results(off.numel() - 1) if results is None else results
+        return self._batched(gbu_validate_utf8_batched, "gbu_validate_utf8_batched", src, off, results,
+                             stream=stream)
+
+    def validate_utf16le_batched(self, src, off, results=None, stream=None):
+        results = self.new_results(off.numel() - 1) if results is None else results
+        return self._batched(gbu_validate_utf16le_batched, "gbu_validate_utf16le_batched", src, off, results,
+                             stream=stream)
+
+    def utf16_length_from_utf8_batched(self, src, off, lens=None, stream=None):
+        lens = self.torch.empty(off.numel() - 1, dtype=self.torch.int64, device=off.device) if lens is None else lens
+        return self._batched(gbu_utf16_length_from_utf8_batched, "gbu_utf16_length_from_utf8_batched", src, off,
+                             lens, stream=stream)
+
+    def utf8_length_from_utf16le_batched(self, src, off, lens=None, stream=None):
+        lens = self.torch.empty(off.numel() - 1, dtype=self.torch.int64, device=off.device) if lens is None else lens
+        return self._batched(gbu_utf8_length_from_utf16le_batched, "gbu_utf8_length_from_utf16le_batched", src,
+                             off, lens, stream=stream)
+
+    def convert_utf8_to_utf16le_batched(self, src, off, dst, dst_off, results=None, stream=None):
+        results = self.new_results(off.numel() - 1) if results is None else results
+        return self._batched(gbu_convert_utf8_to_utf16le_batched, "gbu_convert_utf8_to_utf16le_batched", src, off,
+                             results, dst, dst_off, stream=stream)
+
+    def convert_utf16le_to_utf8_batched(self, src, off, dst, dst_off, results=None, stream=None):
+        results = self.new_results(off.numel() - 1) if results is None else results
+        return self._batched(gbu_convert_utf16le_to_utf8_batched, "gbu_convert_utf16le_to_utf8_batched", src, off,
+                             results, dst, dst_off, stream=stream)
+
+    def exclusive_scan_u64(self, values, out=None, result=None, stream=None):
+        """out[k] = sum(values[:k]) for k = 0 .. len(values) (int64 tensors on this device)."""
+        out = self.torch.empty(values.numel() + 1, dtype=self.torch.int64, device=values.device) if out is None else out
+        result = self.new_result() if result is None else result
+        _check(gbu_exclusive_scan_u64(self.ctx, self._ptr(values), values.numel(), out.data_ptr(),
+                                      result.data_ptr(), self._stream(stream)), "gbu_exclusive_scan_u64")
+        return out, result
+
+    def batch_config(self, op: str) -> dict:
+        return gbu_get_batch_config(self.ctx, OP_CODE[op]).as_dict()
+
+    def set_batch_config(self, op: str, warps_per_cta: int, strings_per_claim: int, long_bytes: int):
+        cfg = GbuBatchConfig(warps_per_cta, strings_per_claim, long_bytes, 0.0)
+        _check(gbu_set_batch_config(self.ctx, OP_CODE[op], cfg), "gbu_set_batch_config")
+
+    def tune_batched(self, op: str, src, off, out, dst=None, dst_off=None, reps: int = 3, stream=None) -> dict:
+        """Autotunes the geometry of batched `op` on this batch; returns the chosen one."""
+        chosen = GbuBatchConfig()
+        _check(gbu_tune_batched(self.ctx, OP_CODE[op], self._ptr(src), self._ptr(off), max(off.numel() - 1, 0),
+                                self._ptr(dst), self._ptr(dst_off), self._ptr(out), reps, self._stream(stream),
+                                ctypes.byref(chosen)), "gbu_tune_batched")
+        return chosen.as_dict()
+
+    def capture(self, fn, stream):
+        """Runs fn() with `stream` captured into a CUDA graph of library calls; returns a Graph."""
+        s = self._stream(stream)
+        _check(gbu_graph_begin(self.ctx, s), "gbu_graph_begin")
+        try:
+            fn()
+        finally:
+            g = gbu_graph_end(self.ctx, s)
+        if not g:
+            raise GbuError("gbu_graph_end failed")
+        return Graph(g, self)
+
     def convert_utf16le_to_utf8(self, src, dst, result=None, stream=None, cap=None):
         result = self.new_result() if result is None else result
         cap = dst.numel() if cap is None else cap
@@ -271,3 +451,28 @@ def convert_utf8_to_utf16le_noalloc(src, dst, result, stream=None, cap=None):
                                                result.data_ptr(), s),
            "gbu_convert_utf8_to_utf16le_noalloc")
     return result
+
+
+class Graph:
+    """An instantiated CUDA graph of library calls (Codec.capture)."""
+
+    def __init__(self, handle: int, codec: Codec):
+        self.handle = handle
+        self.codec = codec  # keeps the context alive
+
+    def launch(self, stream=None):
+        _check(gbu_graph_launch(self.handle, self.codec._stream(stream)), "gbu_graph_launch")
+
+    def kernels(self) -> int:
+        return gbu_graph_kernels(self.handle)
+
+    def close(self):
+        if self.handle:
+            gbu_graph_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

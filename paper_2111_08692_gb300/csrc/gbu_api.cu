@@ -5,6 +5,7 @@
 #include <string.h>
 
 #include <atomic>
+#include <vector>
 
 #include "gbu_device.cuh"
 #include "gbu_kernels.h"
@@ -57,8 +58,16 @@ struct gbu_ctx {
   uint32_t wait_limit;
   long long skip_tile;
   int blocks_per_sm[K_COUNT];
+  int batch_blocks_per_sm[K_COUNT][3];  // per batched mode and warps per CTA (4, 8, 16)
+  int scan_blocks_per_sm;
+  gbu_batch_config batch_cfg[K_COUNT];  // launch geometry of the batched kernels
   std::atomic<uint64_t> launches;
+  uint64_t capture_start;               // launches when the current graph capture began
 };
+
+namespace {
+int warps_index(int w) { return w == 4 ? 0 : (w == 16 ? 2 : 1); }
+}  // namespace
 
 static int init_workspace(gbu_ctx *c) {
   gbu::WsHeader h;
@@ -86,7 +95,10 @@ extern "C" gbu_ctx *gbu_create(int device, uint64_t max_units) {
   }
   // scan states: one per transcoder partition of the largest input (UTF-16: 2 bytes per
   // unit), plus the extra partition UTF-8 inputs may use past their end
-  const uint64_t tiles = (2 * max_units + 64) / gbu::PART_BYTES + 4;
+  uint64_t tiles = (2 * max_units + 64) / gbu::PART_BYTES + 4;
+  // ... and one per tile of the u64 scan of up to max_units + 1 values
+  const uint64_t scan_tiles = (max_units + 1) / gbu::scan_tile_items() + 2;
+  if (scan_tiles > tiles) tiles = scan_tiles;
   if (tiles > 0xFFFFFFF0ull) {
     delete c;
     return nullptr;
@@ -115,6 +127,25 @@ extern "C" gbu_ctx *gbu_create(int device, uint64_t max_units) {
     }
     c->blocks_per_sm[k] = bps;
   }
+  static const int kWarps[3] = {4, 8, 16};
+  bool occ_ok = true;
+  for (int m = 0; m < K_COUNT && occ_ok; ++m)
+    for (int w = 0; w < 3 && occ_ok; ++w) {
+      int bps = 0;
+      occ_ok = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, gbu::batch_kernel_ptr(m, kWarps[w]),
+                                                             kWarps[w] * 32, 0) == cudaSuccess && bps >= 1;
+      c->batch_blocks_per_sm[m][w] = bps;
+    }
+  occ_ok = occ_ok && cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c->scan_blocks_per_sm, gbu::scan_kernel_ptr(),
+                                                                   gbu::scan_threads(), 0) == cudaSuccess &&
+           c->scan_blocks_per_sm >= 1;
+  if (!occ_ok) {
+    cudaFree(c->states);
+    cudaFree(c->ws);
+    delete c;
+    return nullptr;
+  }
+  for (int m = 0; m < K_COUNT; ++m) c->batch_cfg[m] = gbu_batch_config{8, 64, 4096, 0};
   if (init_workspace(c) != GBU_OK) {
     cudaFree(c->states);
     cudaFree(c->ws);
@@ -276,4 +307,270 @@ extern "C" int gbu_convert_utf16le_to_utf8(gbu_ctx *c, const uint16_t *src, uint
   p.result = result;
   set_dst(&p, dst, cap, 1);
   return launch(c, K_C16, p, stream);
+}
+
+// ---- batched forms -----------------------------------------------------------------------
+
+static int batch_check_config(const gbu_batch_config &b) {
+  if (b.warps_per_cta != 4 && b.warps_per_cta != 8 && b.warps_per_cta != 16) return GBU_BAD_ARGUMENT;
+  if (b.strings_per_claim < 1 || b.strings_per_claim > 1024) return GBU_BAD_ARGUMENT;
+  if (b.long_bytes < 512) return GBU_BAD_ARGUMENT;  // at least one 512-byte warp region
+  return GBU_OK;
+}
+
+// Launches batched mode m over B strings with geometry cfg.
+static int batch_launch(gbu_ctx *c, int m, const gbu_batch_config &cfg, const void *src, const uint64_t *off,
+                        uint64_t B, void *dst, const uint64_t *dst_off, gbu_result *results, uint64_t *lens,
+                        gbu_stream stream) {
+  if (B == 0) return GBU_OK;  // nothing to write
+  gbu::BatchParams bp;
+  memset(&bp, 0, sizeof(bp));
+  bp.src = (const uint8_t *)src;
+  bp.off = off;
+  bp.B = B;
+  bp.dst = (uint8_t *)dst;
+  bp.dst_off = dst_off;
+  bp.results = results;
+  bp.lens = lens;
+  bp.ws = c->ws;
+  bp.grab = cfg.strings_per_claim;
+  bp.long_bytes = cfg.long_bytes;
+  DeviceGuard g(c->device);
+  uint64_t grid = (uint64_t)c->num_sms * (uint64_t)c->batch_blocks_per_sm[m][warps_index(cfg.warps_per_cta)];
+  const uint64_t claims = (B + cfg.strings_per_claim - 1) / cfg.strings_per_claim;
+  if (claims < grid) grid = claims;
+  if (grid < 1) grid = 1;
+  void *args[] = {(void *)&bp};
+  cudaError_t e = cudaLaunchKernel(gbu::batch_kernel_ptr(m, cfg.warps_per_cta), dim3((unsigned)grid),
+                                   dim3(cfg.warps_per_cta * 32), args, 0, (cudaStream_t)stream);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return GBU_CUDA_ERROR;
+  }
+  c->launches.fetch_add(1);
+  return GBU_OK;
+}
+
+// Argument checks shared by the batched calls.
+static int batch_args(gbu_ctx *c, int m, const void *src, const uint64_t *off, uint64_t B, const void *dst,
+                      const uint64_t *dst_off, const void *out) {
+  if (!c || m < 0 || m >= K_COUNT) return GBU_BAD_ARGUMENT;
+  if (B == 0) return GBU_OK;
+  if (!src || !off || !out) return GBU_BAD_ARGUMENT;
+  const bool utf16_in = m >= K_V16;
+  if (utf16_in && ((uintptr_t)src & 1)) return GBU_BAD_ARGUMENT;
+  if (is_transcoder(m)) {
+    if (!dst || !dst_off) return GBU_BAD_ARGUMENT;
+    if (m == K_C8 && ((uintptr_t)dst & 1)) return GBU_BAD_ARGUMENT;
+  }
+  if (((uintptr_t)off & 7) || ((uintptr_t)dst_off & 7) || ((uintptr_t)out & 7)) return GBU_BAD_ARGUMENT;
+  return GBU_OK;
+}
+
+static int batch_call(gbu_ctx *c, int m, const void *src, const uint64_t *off, uint64_t B, void *dst,
+                      const uint64_t *dst_off, void *out, gbu_stream stream) {
+  int rc = batch_args(c, m, src, off, B, dst, dst_off, out);
+  if (rc != GBU_OK) return rc;
+  const bool length = m == K_L8 || m == K_L16;
+  return batch_launch(c, m, c->batch_cfg[m], src, off, B, dst, dst_off, length ? nullptr : (gbu_result *)out,
+                      length ? (uint64_t *)out : nullptr, stream);
+}
+
+extern "C" int gbu_validate_utf8_batched(gbu_ctx *c, const uint8_t *src, const uint64_t *off, uint64_t B,
+                                         gbu_result *results, gbu_stream stream) {
+  return batch_call(c, K_V8, src, off, B, nullptr, nullptr, results, stream);
+}
+
+extern "C" int gbu_validate_utf16le_batched(gbu_ctx *c, const uint16_t *src, const uint64_t *off, uint64_t B,
+                                            gbu_result *results, gbu_stream stream) {
+  return batch_call(c, K_V16, src, off, B, nullptr, nullptr, results, stream);
+}
+
+extern "C" int gbu_utf16_length_from_utf8_batched(gbu_ctx *c, const uint8_t *src, const uint64_t *off,
+                                                  uint64_t B, uint64_t *lens, gbu_stream stream) {
+  return batch_call(c, K_L8, src, off, B, nullptr, nullptr, lens, stream);
+}
+
+extern "C" int gbu_utf8_length_from_utf16le_batched(gbu_ctx *c, const uint16_t *src, const uint64_t *off,
+                                                    uint64_t B, uint64_t *lens, gbu_stream stream) {
+  return batch_call(c, K_L16, src, off, B, nullptr, nullptr, lens, stream);
+}
+
+extern "C" int gbu_convert_utf8_to_utf16le_batched(gbu_ctx *c, const uint8_t *src, const uint64_t *off,
+                                                   uint64_t B, uint16_t *dst, const uint64_t *dst_off,
+                                                   gbu_result *results, gbu_stream stream) {
+  return batch_call(c, K_C8, src, off, B, dst, dst_off, results, stream);
+}
+
+extern "C" int gbu_convert_utf16le_to_utf8_batched(gbu_ctx *c, const uint16_t *src, const uint64_t *off,
+                                                   uint64_t B, uint8_t *dst, const uint64_t *dst_off,
+                                                   gbu_result *results, gbu_stream stream) {
+  return batch_call(c, K_C16, src, off, B, dst, dst_off, results, stream);
+}
+
+extern "C" int gbu_exclusive_scan_u64(gbu_ctx *c, const uint64_t *in, uint64_t count, uint64_t *out,
+                                      gbu_result *result, gbu_stream stream) {
+  if (!c || !out || !result || (count > 0 && !in)) return GBU_BAD_ARGUMENT;
+  if (((uintptr_t)in & 7) || ((uintptr_t)out & 7)) return GBU_BAD_ARGUMENT;
+  const uint64_t tile = gbu::scan_tile_items();
+  const uint64_t ntiles = (count + 1 + tile - 1) / tile;
+  if (ntiles > c->max_states) return GBU_BAD_ARGUMENT;
+  gbu::ScanParams sp;
+  memset(&sp, 0, sizeof(sp));
+  sp.in = in;
+  sp.out = out;
+  sp.count = count;
+  sp.result = result;
+  sp.lb.ntiles = (uint32_t)ntiles;
+  sp.lb.ws = c->ws;
+  sp.lb.states = c->states;
+  sp.lb.max_states = c->max_states;
+  sp.lb.wait_limit = c->wait_limit;
+  sp.lb.skip_tile = c->skip_tile;
+  DeviceGuard g(c->device);
+  uint64_t grid = (uint64_t)c->num_sms * (uint64_t)c->scan_blocks_per_sm;
+  if (ntiles < grid) grid = ntiles;
+  void *args[] = {(void *)&sp};
+  cudaError_t e = cudaLaunchKernel(gbu::scan_kernel_ptr(), dim3((unsigned)grid), dim3(gbu::scan_threads()),
+                                   args, 0, (cudaStream_t)stream);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return GBU_CUDA_ERROR;
+  }
+  c->launches.fetch_add(1);
+  return GBU_OK;
+}
+
+extern "C" int gbu_get_batch_config(const gbu_ctx *c, int op, gbu_batch_config *cfg) {
+  if (!c || !cfg || op < 0 || op >= K_COUNT) return GBU_BAD_ARGUMENT;
+  *cfg = c->batch_cfg[op];
+  return GBU_OK;
+}
+
+extern "C" int gbu_set_batch_config(gbu_ctx *c, int op, const gbu_batch_config *cfg) {
+  if (!c || !cfg || op < 0 || op >= K_COUNT) return GBU_BAD_ARGUMENT;
+  const int rc = batch_check_config(*cfg);
+  if (rc != GBU_OK) return rc;
+  c->batch_cfg[op] = *cfg;
+  return GBU_OK;
+}
+
+// Times every candidate geometry on the caller's batch (one untimed launch, then the best of
+// `reps` timed launches each) and keeps the fastest in the context.  The last launch uses the
+// chosen geometry, so the outputs are those of a normal call.  Synchronous.
+extern "C" int gbu_tune_batched(gbu_ctx *c, int op, const void *src, const uint64_t *off, uint64_t B, void *dst,
+                                const uint64_t *dst_off, void *out, int reps, gbu_stream stream,
+                                gbu_batch_config *chosen) {
+  int rc = batch_args(c, op, src, off, B, dst, dst_off, out);
+  if (rc != GBU_OK) return rc;
+  if (reps < 1) reps = 1;
+  DeviceGuard g(c->device);
+  const bool length = op == K_L8 || op == K_L16;
+  gbu_result *results = length ? nullptr : (gbu_result *)out;
+  uint64_t *lens = length ? (uint64_t *)out : nullptr;
+  static const int kWarps[3] = {4, 8, 16};
+  static const uint32_t kGrab[4] = {8, 32, 128, 512};
+  static const uint32_t kLong[4] = {2048, 4096, 8192, 16384};
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess) return GBU_CUDA_ERROR;
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return GBU_CUDA_ERROR;
+  }
+  gbu_batch_config best = c->batch_cfg[op];
+  float best_ms = -1.0f;
+  rc = GBU_OK;
+  for (int w = 0; w < 3 && rc == GBU_OK; ++w)
+    for (int gi = 0; gi < 4 && rc == GBU_OK; ++gi)
+      for (int li = 0; li < 4 && rc == GBU_OK; ++li) {
+        const gbu_batch_config cand{kWarps[w], kGrab[gi], kLong[li], 0.0f};
+        rc = batch_launch(c, op, cand, src, off, B, dst, dst_off, results, lens, stream);
+        float t_best = -1.0f;
+        for (int r = 0; r < reps && rc == GBU_OK; ++r) {
+          if (cudaEventRecord(e0, (cudaStream_t)stream) != cudaSuccess) rc = GBU_CUDA_ERROR;
+          if (rc == GBU_OK) rc = batch_launch(c, op, cand, src, off, B, dst, dst_off, results, lens, stream);
+          if (rc == GBU_OK && cudaEventRecord(e1, (cudaStream_t)stream) != cudaSuccess) rc = GBU_CUDA_ERROR;
+          float ms = 0.0f;
+          if (rc == GBU_OK && (cudaEventSynchronize(e1) != cudaSuccess ||
+                               cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
+            rc = GBU_CUDA_ERROR;
+          if (rc == GBU_OK && (t_best < 0.0f || ms < t_best)) t_best = ms;
+        }
+        if (rc == GBU_OK && (best_ms < 0.0f || t_best < best_ms)) {
+          best_ms = t_best;
+          best = cand;
+        }
+      }
+  if (rc == GBU_OK) {
+    best.tuned_ms = best_ms;
+    c->batch_cfg[op] = best;
+    rc = batch_launch(c, op, best, src, off, B, dst, dst_off, results, lens, stream);
+    if (rc == GBU_OK && cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) rc = GBU_CUDA_ERROR;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc == GBU_OK && chosen) *chosen = best;
+  return rc;
+}
+
+// ---- CUDA graphs ---------------------------------------------------------------------------
+
+struct gbu_graph {
+  int device;
+  cudaGraph_t graph;
+  cudaGraphExec_t exec;
+  uint64_t kernels;  // library launches captured into the graph
+  gbu_ctx *ctx;
+};
+
+extern "C" int gbu_graph_begin(gbu_ctx *c, gbu_stream stream) {
+  if (!c || !stream) return GBU_BAD_ARGUMENT;  // the legacy default stream cannot be captured
+  DeviceGuard g(c->device);
+  if (cudaStreamBeginCapture((cudaStream_t)stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    cudaGetLastError();
+    return GBU_CUDA_ERROR;
+  }
+  c->capture_start = c->launches.load();
+  return GBU_OK;
+}
+
+extern "C" gbu_graph *gbu_graph_end(gbu_ctx *c, gbu_stream stream) {
+  if (!c || !stream) return nullptr;
+  DeviceGuard g(c->device);
+  cudaGraph_t graph = nullptr;
+  if (cudaStreamEndCapture((cudaStream_t)stream, &graph) != cudaSuccess || !graph) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  cudaGraphExec_t exec = nullptr;
+  if (cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess) {
+    cudaGetLastError();
+    cudaGraphDestroy(graph);
+    return nullptr;
+  }
+  gbu_graph *gr = new gbu_graph{c->device, graph, exec, c->launches.load() - c->capture_start, c};
+  // captured launches did not run: they are counted when the graph is launched
+  c->launches.fetch_sub(gr->kernels);
+  return gr;
+}
+
+extern "C" int gbu_graph_launch(gbu_graph *gr, gbu_stream stream) {
+  if (!gr) return GBU_BAD_ARGUMENT;
+  DeviceGuard g(gr->device);
+  if (cudaGraphLaunch(gr->exec, (cudaStream_t)stream) != cudaSuccess) {
+    cudaGetLastError();
+    return GBU_CUDA_ERROR;
+  }
+  gr->ctx->launches.fetch_add(gr->kernels);
+  return GBU_OK;
+}
+
+extern "C" uint64_t gbu_graph_kernels(const gbu_graph *gr) { return gr ? gr->kernels : 0; }
+
+extern "C" void gbu_graph_destroy(gbu_graph *gr) {
+  if (!gr) return;
+  DeviceGuard g(gr->device);
+  cudaGraphExecDestroy(gr->exec);
+  cudaGraphDestroy(gr->graph);
+  delete gr;
 }

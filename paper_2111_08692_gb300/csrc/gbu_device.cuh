@@ -74,6 +74,30 @@ struct Params {
   long long skip_tile;     // test hook: this partition never publishes (-1: off)
 };
 
+// Batched operations (gbu_batch.cu), in the order of the single-buffer kernels.
+enum BatchMode { B_V8 = 0, B_L16 = 1, B_C8 = 2, B_V16 = 3, B_L8 = 4, B_C16 = 5 };
+
+struct BatchParams {
+  const uint8_t *src;        // the strings, back to back
+  const uint64_t *off;       // B+1 input offsets (input code units)
+  uint64_t B;                // number of strings
+  uint8_t *dst;              // transcoders: the outputs, back to back
+  const uint64_t *dst_off;   // transcoders: B+1 output offsets (output code units)
+  gbu_result *results;       // validation, transcoding: B results
+  uint64_t *lens;            // length functions: B lengths
+  WsHeader *ws;              // claim counter (ticket) and completion counter (done)
+  uint32_t grab;             // strings per claim
+  uint32_t long_bytes;       // strings of at least this many input bytes go to a whole CTA
+};
+
+struct ScanParams {
+  const uint64_t *in;
+  uint64_t *out;             // count + 1 entries
+  uint64_t count;
+  gbu_result *result;        // {status, total}
+  Params lb;                 // ws, states, ntiles, max_states, wait_limit, skip_tile
+};
+
 // ---- small PTX wrappers -----------------------------------------------------------------
 
 __device__ __forceinline__ uint32_t smem_addr(const void *p) {

@@ -15,4 +15,10 @@ uint32_t stream_tile_bytes();
 const void *utf8_to_utf16_kernel_ptr();
 const void *utf16_to_utf8_kernel_ptr();
 
+// batched kernels (mode: BatchMode; nwarps: 4, 8 or 16 warps per CTA) and the u64 scan
+const void *batch_kernel_ptr(int mode, int nwarps);
+const void *scan_kernel_ptr();
+uint32_t scan_tile_items();
+int scan_threads();
+
 }  // namespace gbu
