@@ -61,7 +61,9 @@ typedef enum {
   GBU_BAD_ARGUMENT = 17,
   GBU_CUDA_ERROR = 18,
   GBU_TIMEOUT = 19,
-  GBU_NOALLOC_TOO_LARGE = 20 /* n above GBU_NOALLOC_MAX_UNITS (gbu_convert_utf8_to_utf16le_noalloc) */
+  GBU_NOALLOC_TOO_LARGE = 20, /* n above GBU_NOALLOC_MAX_UNITS (gbu_convert_utf8_to_utf16le_noalloc) */
+  GBU_CANCELLED = 21,         /* serving: the request was cancelled before admission       */
+  GBU_OVER_BUDGET = 22        /* serving: the request can never fit the memory budget      */
 } gbu_status;
 
 typedef struct {
@@ -198,6 +200,94 @@ gbu_graph *gbu_graph_end(gbu_ctx *ctx, gbu_stream stream);
 int gbu_graph_launch(gbu_graph *graph, gbu_stream stream);
 uint64_t gbu_graph_kernels(const gbu_graph *graph); /* library kernels per replay */
 void gbu_graph_destroy(gbu_graph *graph);
+
+/* ---- Serving loop --------------------------------------------------------------------------
+ * Continuous batching of validation and transcoding requests on one device (not in the
+ * paper, which measures one buffer at a time: this is a serving form of the same calls).
+ * A scheduler thread admits requests in submission order once their scheduled arrival time
+ * (server clock, gbu_server_now_ns) has passed, while an in-flight slot is free and the
+ * device-memory budget covers the inputs and worst-case outputs of everything admitted;
+ * outputs come from a device arena of budget_bytes allocated at creation.  Admitted small
+ * requests of one operation share ONE batched launch (device descriptors); requests of at
+ * least large_bytes get single-buffer launches.  Launch groups are spread over `streams`
+ * CUDA streams, `groups_per_stream` in flight on each, so newly admitted work overlaps with
+ * running work.  Each request's result is the one the single-buffer call gives on it.
+ * Request inputs are DEVICE buffers that must stay valid until the request completes.
+ * Submit requests in non-decreasing arrival order (a later arrival at the head of the queue
+ * holds back the ones behind it). */
+typedef struct {
+  uint64_t budget_bytes;      /* device memory for inputs + outputs in flight (default 8 GiB) */
+  int32_t streams;            /* CUDA streams (default 4)                                   */
+  int32_t groups_per_stream;  /* launch groups in flight per stream (default 4)             */
+  uint32_t max_group;         /* small requests per batched launch (default 4096)           */
+  uint32_t max_large_group;   /* single-buffer launches per group (default 32)              */
+  uint64_t large_bytes;       /* input bytes from which a request runs alone (default 64 KiB) */
+  uint64_t max_request_units; /* largest request accepted, code units (default 16 Mi)       */
+  uint32_t max_inflight;      /* admitted, not yet completed requests (default 65536)       */
+  uint32_t reserved;
+} gbu_server_config;
+
+typedef struct {
+  int32_t op;           /* GBU_OP_VALIDATE_UTF8, _VALIDATE_UTF16LE, _CONVERT_UTF8_TO_UTF16LE or
+                           _CONVERT_UTF16LE_TO_UTF8 */
+  int32_t reserved;
+  const void *src;      /* device pointer, n code units */
+  uint64_t n;
+  uint64_t arrival_ns;  /* scheduled arrival on the server clock (0: at once) */
+  uint64_t tag;         /* returned in the completion */
+} gbu_request;
+
+typedef struct {
+  uint64_t id;
+  uint64_t tag;
+  gbu_result result;    /* as the single-buffer call's; GBU_CANCELLED for a cancelled request */
+  void *dst;            /* transcodings: device output (result.count units when GBU_OK),
+                           valid until gbu_server_release(id); NULL otherwise */
+  uint64_t arrival_ns, admit_ns, complete_ns;  /* server clock */
+} gbu_completion;
+
+typedef struct {
+  uint64_t submitted, admitted, completed;
+  uint64_t launches, groups;     /* library launches and launch groups enqueued */
+  uint64_t budget_used_bytes, peak_budget_bytes;
+  uint64_t inflight, pending;
+} gbu_server_stats;
+
+void gbu_server_default_config(gbu_server_config *cfg);
+/* Allocates the arena, streams, contexts and pinned staging, and starts the scheduler
+ * thread.  cfg NULL = defaults.  Returns NULL on failure. */
+typedef struct gbu_server gbu_server;
+gbu_server *gbu_server_create(int device, const gbu_server_config *cfg);
+/* Stops after the admitted work is done; requests not yet admitted are dropped. */
+void gbu_server_destroy(gbu_server *server);
+uint64_t gbu_server_now_ns(const gbu_server *server);
+/* Queues count requests; their ids are *first_id, *first_id + 1, ...  GBU_BAD_ARGUMENT (bad
+ * op, NULL src with n > 0, misaligned UTF-16, n above max_request_units) or GBU_OVER_BUDGET
+ * (a request larger than the whole budget): then none is queued.  Thread-safe. */
+int gbu_server_submit(gbu_server *server, const gbu_request *reqs, uint64_t count, uint64_t *first_id);
+/* Cancels a request not yet admitted (it completes with GBU_CANCELLED); GBU_BAD_ARGUMENT if
+ * it is unknown or already admitted. */
+int gbu_server_cancel(gbu_server *server, uint64_t id);
+/* Moves up to max completions (oldest first) into out; returns how many.  Non-blocking. */
+int gbu_server_poll(gbu_server *server, gbu_completion *out, int max);
+/* Returns a completed transcoding's output buffer to the arena (and its bytes to the budget). */
+int gbu_server_release(gbu_server *server, uint64_t id);
+int gbu_server_get_stats(gbu_server *server, gbu_server_stats *out);
+/* Copies the first `bytes` bytes of a completed, unreleased transcoding's output into host
+ * memory (synchronous; for clients that want the text on the host). */
+int gbu_server_copy_output(gbu_server *server, uint64_t id, void *host, uint64_t bytes);
+
+/* The server's arena bookkeeping (first-fit offsets with coalescing; no memory behind it),
+ * exported for host-side tests.  gbu_arena_alloc returns GBU_OVER_BUDGET when no free block
+ * is large enough. */
+typedef struct gbu_arena gbu_arena;
+gbu_arena *gbu_arena_create(uint64_t capacity, uint64_t align);
+int gbu_arena_alloc(gbu_arena *arena, uint64_t size, uint64_t *off);
+int gbu_arena_free(gbu_arena *arena, uint64_t off);
+uint64_t gbu_arena_used(const gbu_arena *arena);
+uint64_t gbu_arena_largest_free(const gbu_arena *arena);
+uint64_t gbu_arena_free_blocks(const gbu_arena *arena);
+void gbu_arena_destroy(gbu_arena *arena);
 
 /* Context-free, allocation-free form of gbu_convert_utf8_to_utf16le, for callers that cannot
  * allocate device memory: creating a context calls cudaMalloc, which can synchronise the

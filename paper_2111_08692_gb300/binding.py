@@ -16,7 +16,7 @@ from . import build as _build
 STATUS = {
     0: "OK", 1: "HEADER_BITS", 2: "TOO_SHORT", 3: "TOO_LONG", 4: "OVERLONG", 5: "TOO_LARGE",
     6: "SURROGATE", 16: "OUTPUT_TOO_SMALL", 17: "BAD_ARGUMENT", 18: "CUDA_ERROR", 19: "TIMEOUT",
-    20: "NOALLOC_TOO_LARGE",
+    20: "NOALLOC_TOO_LARGE", 21: "CANCELLED", 22: "OVER_BUDGET",
 }
 # Largest input (bytes) of gbu_convert_utf8_to_utf16le_noalloc (GBU_NOALLOC_MAX_UNITS).
 NOALLOC_MAX_UNITS = 1 << 28
@@ -33,6 +33,30 @@ class GbuBatchConfig(ctypes.Structure):
 
     def as_dict(self) -> dict:
         return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class GbuServerConfig(ctypes.Structure):
+    _fields_ = [("budget_bytes", ctypes.c_uint64), ("streams", ctypes.c_int32),
+                ("groups_per_stream", ctypes.c_int32), ("max_group", ctypes.c_uint32),
+                ("max_large_group", ctypes.c_uint32), ("large_bytes", ctypes.c_uint64),
+                ("max_request_units", ctypes.c_uint64), ("max_inflight", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32)]
+
+
+class GbuRequest(ctypes.Structure):
+    _fields_ = [("op", ctypes.c_int32), ("reserved", ctypes.c_int32), ("src", ctypes.c_void_p),
+                ("n", ctypes.c_uint64), ("arrival_ns", ctypes.c_uint64), ("tag", ctypes.c_uint64)]
+
+
+class GbuCompletion(ctypes.Structure):
+    _fields_ = [("id", ctypes.c_uint64), ("tag", ctypes.c_uint64), ("result", GbuResult),
+                ("dst", ctypes.c_void_p), ("arrival_ns", ctypes.c_uint64), ("admit_ns", ctypes.c_uint64),
+                ("complete_ns", ctypes.c_uint64)]
+
+
+class GbuServerStats(ctypes.Structure):
+    _fields_ = [(f, ctypes.c_uint64) for f in ("submitted", "admitted", "completed", "launches", "groups",
+                                                "budget_used_bytes", "peak_budget_bytes", "inflight", "pending")]
 
 
 # Operation codes of the batched calls (gbu_op).
@@ -112,6 +136,37 @@ def lib() -> ctypes.CDLL:
             L.gbu_graph_kernels.argtypes = [vp]
             L.gbu_graph_destroy.restype = None
             L.gbu_graph_destroy.argtypes = [vp]
+            L.gbu_server_default_config.restype = None
+            L.gbu_server_default_config.argtypes = [ctypes.POINTER(GbuServerConfig)]
+            L.gbu_server_create.restype = vp
+            L.gbu_server_create.argtypes = [i32, ctypes.POINTER(GbuServerConfig)]
+            L.gbu_server_destroy.restype = None
+            L.gbu_server_destroy.argtypes = [vp]
+            L.gbu_server_now_ns.restype = u64
+            L.gbu_server_now_ns.argtypes = [vp]
+            L.gbu_server_submit.restype = i32
+            L.gbu_server_submit.argtypes = [vp, vp, u64, ctypes.POINTER(ctypes.c_uint64)]
+            L.gbu_server_cancel.restype = i32
+            L.gbu_server_cancel.argtypes = [vp, u64]
+            L.gbu_server_poll.restype = i32
+            L.gbu_server_poll.argtypes = [vp, vp, i32]
+            L.gbu_server_release.restype = i32
+            L.gbu_server_release.argtypes = [vp, u64]
+            L.gbu_server_get_stats.restype = i32
+            L.gbu_server_get_stats.argtypes = [vp, ctypes.POINTER(GbuServerStats)]
+            L.gbu_server_copy_output.restype = i32
+            L.gbu_server_copy_output.argtypes = [vp, u64, vp, u64]
+            L.gbu_arena_create.restype = vp
+            L.gbu_arena_create.argtypes = [u64, u64]
+            L.gbu_arena_alloc.restype = i32
+            L.gbu_arena_alloc.argtypes = [vp, u64, ctypes.POINTER(ctypes.c_uint64)]
+            L.gbu_arena_free.restype = i32
+            L.gbu_arena_free.argtypes = [vp, u64]
+            for name in ("gbu_arena_used", "gbu_arena_largest_free", "gbu_arena_free_blocks"):
+                getattr(L, name).restype = u64
+                getattr(L, name).argtypes = [vp]
+            L.gbu_arena_destroy.restype = None
+            L.gbu_arena_destroy.argtypes = [vp]
             L.gbu_convert_utf8_to_utf16le_noalloc.restype = i32
             L.gbu_convert_utf8_to_utf16le_noalloc.argtypes = [vp, u64, vp, u64, vp, vp]
             _lib = L
@@ -469,6 +524,162 @@ class Graph:
     def close(self):
         if self.handle:
             gbu_graph_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ---- serving loop -------------------------------------------------------------------------
+
+def gbu_server_default_config() -> GbuServerConfig:
+    cfg = GbuServerConfig()
+    lib().gbu_server_default_config(ctypes.byref(cfg))
+    return cfg
+
+
+def gbu_server_create(device: int, cfg: GbuServerConfig | None) -> int:
+    return lib().gbu_server_create(device, ctypes.byref(cfg) if cfg is not None else None)
+
+
+def gbu_server_destroy(server) -> None:
+    lib().gbu_server_destroy(server)
+
+
+def gbu_server_now_ns(server) -> int:
+    return lib().gbu_server_now_ns(server)
+
+
+def gbu_server_submit(server, reqs, count, first_id) -> int:
+    return lib().gbu_server_submit(server, reqs, count, first_id)
+
+
+def gbu_server_cancel(server, rid) -> int:
+    return lib().gbu_server_cancel(server, rid)
+
+
+def gbu_server_poll(server, out, max_out) -> int:
+    return lib().gbu_server_poll(server, out, max_out)
+
+
+def gbu_server_release(server, rid) -> int:
+    return lib().gbu_server_release(server, rid)
+
+
+def gbu_server_copy_output(server, rid, host, nbytes) -> int:
+    return lib().gbu_server_copy_output(server, rid, host, nbytes)
+
+
+def gbu_server_get_stats(server, out) -> int:
+    return lib().gbu_server_get_stats(server, out)
+
+
+class Server:
+    """The serving loop (gbu_server_*) on one device.  Requests are (op, src tensor, arrival
+    time in server-clock ns, tag); completions come back as dicts."""
+
+    def __init__(self, device: int = 0, **cfg):
+        c = gbu_server_default_config()
+        for k, v in cfg.items():
+            setattr(c, k, v)
+        self.cfg = c
+        self.handle = gbu_server_create(device, c)
+        if not self.handle:
+            raise GbuError("gbu_server_create failed")
+        self._buf = (GbuCompletion * 4096)()
+
+    def now_ns(self) -> int:
+        return gbu_server_now_ns(self.handle)
+
+    def submit(self, requests) -> int:
+        """requests: iterable of (op name, src tensor or (pointer, n), arrival_ns, tag)."""
+        reqs = list(requests)
+        arr = (GbuRequest * max(len(reqs), 1))()
+        for i, (op, src, arrival, tag) in enumerate(reqs):
+            ptr, n = (src.data_ptr() if src.numel() else 0, src.numel()) if hasattr(src, "data_ptr") else src
+            arr[i] = GbuRequest(OP_CODE[op], 0, ptr, n, int(arrival), int(tag))
+        first = ctypes.c_uint64(0)
+        _check(gbu_server_submit(self.handle, arr, len(reqs), ctypes.byref(first)), "gbu_server_submit")
+        return first.value
+
+    def submit_raw(self, arr, count: int) -> int:
+        """Submits a prepared (GbuRequest * k) array."""
+        first = ctypes.c_uint64(0)
+        _check(gbu_server_submit(self.handle, arr, count, ctypes.byref(first)), "gbu_server_submit")
+        return first.value
+
+    def cancel(self, rid: int) -> bool:
+        return gbu_server_cancel(self.handle, rid) == 0
+
+    def poll(self, max_out: int = 4096) -> list[dict]:
+        k = gbu_server_poll(self.handle, self._buf, min(max_out, len(self._buf)))
+        out = []
+        for i in range(k):
+            c = self._buf[i]
+            out.append({"id": c.id, "tag": c.tag, "status": STATUS.get(c.result.status, c.result.status),
+                        "count": c.result.count, "dst": c.dst, "arrival_ns": c.arrival_ns,
+                        "admit_ns": c.admit_ns, "complete_ns": c.complete_ns})
+        return out
+
+    def release(self, rid: int) -> None:
+        _check(gbu_server_release(self.handle, rid), "gbu_server_release")
+
+    def copy_output(self, rid: int, units: int, dtype):
+        """The first `units` output units of completed request rid, as a numpy array."""
+        import numpy as np
+        out = np.empty(units, dtype=dtype)
+        _check(gbu_server_copy_output(self.handle, rid, out.ctypes.data if units else None, out.nbytes),
+               "gbu_server_copy_output")
+        return out
+
+    def stats(self) -> dict:
+        st = GbuServerStats()
+        _check(gbu_server_get_stats(self.handle, ctypes.byref(st)), "gbu_server_get_stats")
+        return {f: getattr(st, f) for f, _ in st._fields_}
+
+    def close(self):
+        if self.handle:
+            gbu_server_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Arena:
+    """The server's arena bookkeeping (offsets only), for host-side tests."""
+
+    def __init__(self, capacity: int, align: int = 256):
+        self.handle = lib().gbu_arena_create(capacity, align)
+        if not self.handle:
+            raise GbuError("gbu_arena_create failed")
+
+    def alloc(self, size: int):
+        off = ctypes.c_uint64(0)
+        rc = lib().gbu_arena_alloc(self.handle, size, ctypes.byref(off))
+        return off.value if rc == 0 else None
+
+    def free(self, off: int) -> bool:
+        return lib().gbu_arena_free(self.handle, off) == 0
+
+    def used(self) -> int:
+        return lib().gbu_arena_used(self.handle)
+
+    def largest_free(self) -> int:
+        return lib().gbu_arena_largest_free(self.handle)
+
+    def free_blocks(self) -> int:
+        return lib().gbu_arena_free_blocks(self.handle)
+
+    def close(self):
+        if self.handle:
+            lib().gbu_arena_destroy(self.handle)
             self.handle = None
 
     def __del__(self):

@@ -8,6 +8,7 @@
 #include <vector>
 
 #include "gbu_device.cuh"
+#include "gbu_internal.h"
 #include "gbu_kernels.h"
 #include "gbutf.h"
 
@@ -321,10 +322,11 @@ static int batch_check_config(const gbu_batch_config &b) {
 // Launches batched mode m over B strings with geometry cfg.
 static int batch_launch(gbu_ctx *c, int m, const gbu_batch_config &cfg, const void *src, const uint64_t *off,
                         uint64_t B, void *dst, const uint64_t *dst_off, gbu_result *results, uint64_t *lens,
-                        gbu_stream stream) {
+                        gbu_stream stream, const gbu::StringDesc *desc = nullptr) {
   if (B == 0) return GBU_OK;  // nothing to write
   gbu::BatchParams bp;
   memset(&bp, 0, sizeof(bp));
+  bp.desc = desc;
   bp.src = (const uint8_t *)src;
   bp.off = off;
   bp.B = B;
@@ -573,4 +575,14 @@ extern "C" void gbu_graph_destroy(gbu_graph *gr) {
   cudaGraphExecDestroy(gr->exec);
   cudaGraphDestroy(gr->graph);
   delete gr;
+}
+
+// ---- library-internal entry points (gbu_internal.h) ---------------------------------------
+
+int gbu_internal_batch_desc(gbu_ctx *c, int op, const gbu::StringDesc *desc, uint64_t B, gbu_result *results,
+                            gbu_stream stream) {
+  if (!c || op < 0 || op >= K_COUNT || op == K_L8 || op == K_L16) return GBU_BAD_ARGUMENT;
+  if (B > 0 && (!desc || !results)) return GBU_BAD_ARGUMENT;
+  return batch_launch(c, op, c->batch_cfg[op], nullptr, nullptr, B, nullptr, nullptr, results, nullptr, stream,
+                      desc);
 }

@@ -1,8 +1,9 @@
 // gbu_batch.cu -- batched forms of the six operations: many strings in one launch, and the
 // exclusive scan that turns batched output lengths into output offsets.
 //
-// The strings come in CSR form: one buffer holding them back to back and B+1 offsets in
-// code units.  A persistent grid of CTAs (NWARPS warps each) claims GRAB consecutive
+// The strings come in CSR form (one buffer holding them back to back and B+1 offsets in
+// code units) or as an array of descriptors (pointer and length of each input and output).
+// A persistent grid of CTAs (NWARPS warps each) claims GRAB consecutive
 // strings at a time from a counter in the workspace; inside a claim,
 //   * every warp takes strings one by one (a shared-memory counter) and handles each on its
 //     own, walking it in 512-byte regions (one 16-byte chunk per lane) with the same per-chunk
@@ -66,26 +67,43 @@ struct __align__(128) BatchSmem {
 template <int MODE>
 __device__ __forceinline__ Params string_params(const BatchParams &bp, uint64_t i) {
   using T = BatchTraits<MODE>;
+  constexpr uint32_t OUT_UNIT = MODE == B_C8 ? 2u : 1u;
   Params sp;
-  const uint64_t start = bp.off[i], end = bp.off[i + 1];
-  const uint64_t n = end > start ? end - start : 0;
-  const uintptr_t a = (uintptr_t)(bp.src + start * T::IN_UNIT);
+  uintptr_t a, da = 0;
+  uint64_t n, cap = 0;
+  if (bp.desc) {
+    const StringDesc d = bp.desc[i];
+    a = (uintptr_t)d.src;
+    n = d.n;
+    if (T::CONVERT) {
+      da = (uintptr_t)d.dst;
+      cap = d.cap;
+    }
+  } else {
+    const uint64_t start = bp.off[i], end = bp.off[i + 1];
+    n = end > start ? end - start : 0;
+    a = (uintptr_t)(bp.src + start * T::IN_UNIT);
+    if (T::CONVERT) {
+      const uint64_t d0 = bp.dst_off[i], d1 = bp.dst_off[i + 1];
+      da = (uintptr_t)(bp.dst + d0 * OUT_UNIT);
+      cap = d1 > d0 ? d1 - d0 : 0;
+    }
+  }
   sp.base = (const uint8_t *)(a & ~(uintptr_t)15);
   sp.off0 = (uint32_t)(a & 15);
   sp.n = n;
   sp.vbytes = sp.off0 + n * T::IN_UNIT;
-  sp.dbase = nullptr;
-  sp.dshift = 0;
-  sp.cap = 0;
-  if (T::CONVERT) {
-    constexpr uint32_t OUT_UNIT = MODE == B_C8 ? 2u : 1u;
-    const uint64_t d0 = bp.dst_off[i], d1 = bp.dst_off[i + 1];
-    const uintptr_t da = (uintptr_t)(bp.dst + d0 * OUT_UNIT);
-    sp.dbase = (uint8_t *)(da & ~(uintptr_t)15);
-    sp.dshift = (uint32_t)((da & 15) / OUT_UNIT);
-    sp.cap = d1 > d0 ? d1 - d0 : 0;
-  }
+  sp.dbase = (uint8_t *)(da & ~(uintptr_t)15);
+  sp.dshift = (uint32_t)((da & 15) / OUT_UNIT);
+  sp.cap = cap;
   return sp;
+}
+
+// Input code units of string i.
+__device__ __forceinline__ uint64_t string_units(const BatchParams &bp, uint64_t i) {
+  if (bp.desc) return bp.desc[i].n;
+  const uint64_t s = bp.off[i], e = bp.off[i + 1];
+  return e > s ? e - s : 0;
 }
 
 // Virtual end of the positions to judge (0 for an empty string).
@@ -289,8 +307,7 @@ __global__ void __launch_bounds__(NWARPS * 32) batch_kernel(const BatchParams bp
       j = __shfl_sync(0xffffffffu, j, 0);
       if (j >= gn) break;
       const uint64_t i = g0 + j;
-      const uint64_t s = bp.off[i], e = bp.off[i + 1];
-      if (e > s && (e - s) * T::IN_UNIT >= bp.long_bytes) {
+      if (string_units(bp, i) * T::IN_UNIT >= bp.long_bytes) {
         if (lane == 0) sm.longs[atomicAdd(&sm.nlong, 1u)] = j;
         continue;
       }

@@ -77,7 +77,17 @@ struct Params {
 // Batched operations (gbu_batch.cu), in the order of the single-buffer kernels.
 enum BatchMode { B_V8 = 0, B_L16 = 1, B_C8 = 2, B_V16 = 3, B_L8 = 4, B_C16 = 5 };
 
+// One string given by pointers instead of CSR offsets (the serving loop's requests).
+struct StringDesc {
+  const void *src;           // n input code units
+  uint64_t n;
+  void *dst;                 // transcoders: cap output code units
+  uint64_t cap;
+};
+static_assert(sizeof(StringDesc) == 32, "descriptor layout");
+
 struct BatchParams {
+  const StringDesc *desc;    // non-NULL: string i is desc[i] (src, off, dst, dst_off unused)
   const uint8_t *src;        // the strings, back to back
   const uint64_t *off;       // B+1 input offsets (input code units)
   uint64_t B;                // number of strings

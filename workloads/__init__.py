@@ -468,3 +468,67 @@ def _same_length_error(size: int, rng) -> np.ndarray:
                         dtype=np.uint8)
     return np.array([0xF4, r(0x90, 0xC0), r(0x80, 0xC0), r(0x80, 0xC0)] if form == 0
                     else [0xF0, r(0x80, 0x90), r(0x80, 0xC0), r(0x80, 0xC0)], dtype=np.uint8)
+
+
+# ---- serving: request pools and arrival traces ---------------------------------------------
+
+SERVING_OPS = ("validate_utf8", "validate_utf16le", "convert_utf8_to_utf16le", "convert_utf16le_to_utf8")
+
+
+def serving_pools(pool_bytes: int = 64 << 20, seed: int = 2000, error_every: int = 1 << 16):
+    """Per profile: a UTF-8 text of pool_bytes bytes and the UTF-16LE text of pool_bytes / 2
+    words (seeded like the profile buffers), the indices where characters start in each, and
+    a copy of each with one corrupted character about every `error_every` units (a byte F8-FF
+    over a UTF-8 lead byte, a lone low surrogate over a UTF-16 word).  Requests are slices of
+    these pools between character starts, so a request taken from a clean pool is valid."""
+    pools = {}
+    for k, prof in enumerate(PROFILE_ORDER):
+        u8, u16 = profile_buffers(prof, pool_bytes, pool_bytes // 2, seed + k, cache=pool_bytes >= (16 << 20))
+        starts8 = np.flatnonzero((u8 & 0xC0) != 0x80)
+        starts16 = np.flatnonzero((u16 < 0xDC00) | (u16 >= 0xE000))
+        rng = np.random.default_rng(seed + 100 + k)
+        bad8, bad16 = u8.copy(), u16.copy()
+        pos8 = starts8[rng.integers(0, starts8.size, size=max(1, u8.size // error_every))]
+        bad8[pos8] = rng.integers(0xF8, 0x100, size=pos8.size)
+        pos16 = starts16[rng.integers(0, starts16.size, size=max(1, u16.size // error_every))]
+        bad16[pos16] = rng.integers(0xDC00, 0xE000, size=pos16.size)
+        pools[prof] = {"u8": u8, "u16": u16, "starts8": np.append(starts8, u8.size),
+                       "starts16": np.append(starts16, u16.size), "bad8": bad8, "bad16": bad16}
+    return pools
+
+
+def serving_trace(count: int, rate: float, pools, seed: int = 3000, min_bytes: int = 16,
+                  max_bytes: int = 16 << 20, p_validate: float = 0.10, p_bad: float = 0.0):
+    """`count` requests with Poisson arrivals at `rate` per second (arrival_ns from 0), sizes
+    log-uniform on [min_bytes, max_bytes] bytes of input, 10% validate-only (half UTF-8, half
+    UTF-16LE) and the rest split 50/50 between the two transcoding directions, each of a
+    profile drawn uniformly, starting at a random character start of that profile's pool (the
+    corrupted copy with probability p_bad) and ending at the last character start that keeps
+    the request within its size.  Returns a dict of numpy arrays: op (index into
+    SERVING_OPS), profile (index into PROFILE_ORDER), bad, start, n (code units), arrival_ns."""
+    rng = np.random.default_rng(seed)
+    gaps = rng.exponential(1.0 / rate, size=count)
+    arrival = np.rint(np.cumsum(gaps) * 1e9).astype(np.int64)
+    arrival -= arrival[0] if count else 0
+    size = np.exp(rng.uniform(np.log(min_bytes), np.log(max_bytes), size=count))
+    u = rng.random(count)
+    op = np.where(u < p_validate / 2, 0, np.where(u < p_validate, 1,
+                  np.where(u < p_validate + (1 - p_validate) / 2, 2, 3))).astype(np.int8)
+    prof = rng.integers(0, len(PROFILE_ORDER), size=count).astype(np.int8)
+    bad = rng.random(count) < p_bad
+    start = np.zeros(count, np.int64)
+    n = np.zeros(count, np.int64)
+    pos = rng.random(count)
+    for i in range(count):
+        p = pools[PROFILE_ORDER[prof[i]]]
+        utf16 = op[i] in (1, 3)
+        st = p["starts16"] if utf16 else p["starts8"]
+        units = max(1, int(size[i] / (2 if utf16 else 1)))
+        total = st[-1]
+        units = min(units, total)
+        # a character start at or before total - units, then the last start within the size
+        j = int(pos[i] * np.searchsorted(st, total - units, side="right"))
+        s0 = int(st[j])
+        e = int(st[np.searchsorted(st, s0 + units, side="right") - 1])
+        start[i], n[i] = s0, max(e - s0, 0)
+    return {"op": op, "profile": prof, "bad": bad, "start": start, "n": n, "arrival_ns": arrival}
