@@ -49,6 +49,13 @@ def parse():
     ap.add_argument("--batched-steps", type=int, default=10)
     ap.add_argument("--loop-sample", type=int, default=3000,
                     help="strings timed through the per-string launch loop")
+    ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--serving-loads", default="1e4,3e4,1e5,3e5,1e6", help="offered loads, requests/s")
+    ap.add_argument("--serving-requests", type=int, default=20000, help="requests per offered load (at most)")
+    ap.add_argument("--serving-seconds", type=float, default=1.0, help="arrival window per load (at most)")
+    ap.add_argument("--serving-streams", type=int, default=None)
+    ap.add_argument("--serving-groups", type=int, default=None, help="launch groups in flight per stream")
+    ap.add_argument("--serving-large-group", type=int, default=None)
     return ap.parse_args()
 
 
@@ -319,6 +326,8 @@ def run_ours(args):
         line["cpu_baseline"] = cpu_baseline(bufs, args.cpu_sample)
     if not args.no_batched and args.batched_strings > 0:
         line["batched"] = run_batched(args, codec, dev, dist, world)
+    if not args.no_serving:
+        line["serving"] = run_serving(args, dev, dist, world)
     if rank == 0:
         print(json.dumps(line), flush=True)
     codec.close()
@@ -463,6 +472,93 @@ def run_batched(args, codec, dev, dist, world):
             "config": {"workload": f"{B} strings, log-normal UTF-8 lengths (median 64 B, sigma 1.5, 1 B..64 KiB), "
                                    "five profiles, 1% with one injected error; both directions into packed outputs",
                        "graph": "6 kernels per replay", "l2": "inputs (198 MB + 285 MB) larger than L2"}}
+
+
+def run_serving(args, dev, dist, world):
+    """Serving: requests arrive as a Poisson process at each offered load, with input sizes
+    log-uniform on 16 B - 16 MiB, 10% validate-only, the rest split 50/50 between the two
+    transcoding directions, the five profiles mixed; inputs are slices of device-resident
+    per-profile pools (64 MiB of UTF-8 and 32 Mi words of UTF-16LE each).  The library's
+    serving loop admits them against an 8 GiB budget and batches them continuously; the
+    client discards outputs at completion.  Latency = completion - scheduled arrival."""
+    import numpy as np
+    import torch
+    import workloads as W
+    from paper_2111_08692_gb300 import REQ_DISCARD_OUTPUT, Server
+    host = W.serving_pools(64 << 20, seed=2000)
+    pools = {}
+    for prof, p in host.items():
+        pools[prof] = (torch.from_numpy(p["u8"]).to(dev), torch.from_numpy(p["u16"].view(np.int16)).to(dev))
+    req_dt = np.dtype([("op", "<i4"), ("flags", "<i4"), ("src", "<u8"), ("n", "<u8"), ("arrival", "<u8"),
+                       ("tag", "<u8")])
+    comp_dt = np.dtype([("id", "<u8"), ("tag", "<u8"), ("status", "<i4"), ("res", "<i4"), ("count", "<u8"),
+                        ("dst", "<u8"), ("arrival", "<u8"), ("admit", "<u8"), ("complete", "<u8")])
+    from paper_2111_08692_gb300 import OP_CODE, gbu_server_poll
+    scfg = {"budget_bytes": 8 << 30}
+    for key, val in (("streams", args.serving_streams), ("groups_per_stream", args.serving_groups),
+                     ("max_large_group", args.serving_large_group)):
+        if val is not None:
+            scfg[key] = val
+    srv = Server(dev.index if dev.index is not None else 0, **scfg)
+    out = []
+    try:
+        for rate in [float(x) for x in args.serving_loads.split(",") if x]:
+            count = int(min(args.serving_requests, max(100, rate * args.serving_seconds)))
+            tr = W.serving_trace(count, rate, host, seed=3000 + int(rate) % 1000)
+            reqs = np.zeros(count, dtype=req_dt)
+            base = np.zeros(count, dtype=np.uint64)
+            in_bytes = 0
+            for k, prof in enumerate(W.PROFILE_ORDER):
+                sel = tr["profile"] == k
+                u8p, u16p = pools[prof][0].data_ptr(), pools[prof][1].data_ptr()
+                utf16 = (tr["op"] == 1) | (tr["op"] == 3)
+                base[sel & ~utf16] = u8p
+                base[sel & utf16] = u16p
+            utf16 = (tr["op"] == 1) | (tr["op"] == 3)
+            unit = np.where(utf16, 2, 1).astype(np.uint64)
+            reqs["op"] = [OP_CODE[W.SERVING_OPS[o]] for o in tr["op"]]
+            reqs["flags"] = REQ_DISCARD_OUTPUT
+            reqs["src"] = base + tr["start"].astype(np.uint64) * unit
+            reqs["n"] = tr["n"]
+            reqs["tag"] = np.arange(count)
+            in_bytes = int(np.sum(tr["n"].astype(np.uint64) * unit))
+            t0 = srv.now_ns() + 20_000_000
+            reqs["arrival"] = t0 + tr["arrival_ns"]
+            srv.submit_raw(reqs.ctypes.data, count)
+            got = np.zeros(count, dtype=comp_dt)
+            buf = np.zeros(8192, dtype=comp_dt)
+            k = 0
+            t_end = time.time() + 120
+            while k < count and time.time() < t_end:
+                m = gbu_server_poll(srv.handle, buf.ctypes.data, buf.size)
+                if m > 0:
+                    got[k:k + m] = buf[:m]
+                    k += m
+                else:
+                    time.sleep(0.0002)
+            assert k == count, f"serving: {count - k} requests did not complete"
+            assert np.all(got["status"] == 0), "serving: a request failed"
+            lat_us = (got["complete"].astype(np.int64) - got["arrival"].astype(np.int64)) / 1e3
+            span_s = (int(got["complete"].max()) - t0) / 1e9
+            st = srv.stats()
+            out.append({"offered_rps": rate, "requests": count,
+                        "achieved_rps": round(count / span_s, 1),
+                        "input_gbs": round(in_bytes / span_s / 1e9, 2),
+                        "p50_us": round(float(np.percentile(lat_us, 50)), 1),
+                        "p99_us": round(float(np.percentile(lat_us, 99)), 1),
+                        "max_us": round(float(lat_us.max()), 1)})
+        st = srv.stats()
+    finally:
+        srv.close()
+    return {"metric": "serving p50/p99 latency at each offered load", "loads": out,
+            "launches": int(st["launches"]), "groups": int(st["groups"]), "completed": int(st["completed"]),
+            "peak_budget_bytes": int(st["peak_budget_bytes"]),
+            "config": {"workload": "Poisson arrivals; input sizes log-uniform 16 B - 16 MiB; 10% validate-only, "
+                                   "45%/45% UTF-8->UTF-16LE / UTF-16LE->UTF-8; five profiles mixed; inputs "
+                                   "resident on the device, outputs discarded at completion",
+                       "budget_bytes": 8 << 30, "streams": srv.cfg.streams,
+                       "groups_per_stream": srv.cfg.groups_per_stream, "max_large_group": srv.cfg.max_large_group,
+                       "large_bytes": srv.cfg.large_bytes}}
 
 
 def run_e2e(args, codec, bufs, stream, dist, world, call):

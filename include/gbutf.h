@@ -217,10 +217,10 @@ void gbu_graph_destroy(gbu_graph *graph);
  * holds back the ones behind it). */
 typedef struct {
   uint64_t budget_bytes;      /* device memory for inputs + outputs in flight (default 8 GiB) */
-  int32_t streams;            /* CUDA streams (default 4)                                   */
-  int32_t groups_per_stream;  /* launch groups in flight per stream (default 4)             */
+  int32_t streams;            /* CUDA streams (default 16)                                  */
+  int32_t groups_per_stream;  /* launch groups in flight per stream (default 8)             */
   uint32_t max_group;         /* small requests per batched launch (default 4096)           */
-  uint32_t max_large_group;   /* single-buffer launches per group (default 32)              */
+  uint32_t max_large_group;   /* single-buffer launches per group (default 2)               */
   uint64_t large_bytes;       /* input bytes from which a request runs alone (default 64 KiB) */
   uint64_t max_request_units; /* largest request accepted, code units (default 16 Mi)       */
   uint32_t max_inflight;      /* admitted, not yet completed requests (default 65536)       */
@@ -230,12 +230,15 @@ typedef struct {
 typedef struct {
   int32_t op;           /* GBU_OP_VALIDATE_UTF8, _VALIDATE_UTF16LE, _CONVERT_UTF8_TO_UTF16LE or
                            _CONVERT_UTF16LE_TO_UTF8 */
-  int32_t reserved;
+  int32_t flags;        /* GBU_REQ_DISCARD_OUTPUT: free the output at completion (only the
+                           result is wanted) */
   const void *src;      /* device pointer, n code units */
   uint64_t n;
   uint64_t arrival_ns;  /* scheduled arrival on the server clock (0: at once) */
   uint64_t tag;         /* returned in the completion */
 } gbu_request;
+
+#define GBU_REQ_DISCARD_OUTPUT 1
 
 typedef struct {
   uint64_t id;

@@ -4,7 +4,7 @@ The work runs in the CUDA library built from ``csrc/`` (C ABI: ``include/gbutf.h
 ``binding`` is a thin ctypes layer over it.
 """
 from .binding import (  # noqa: F401
-    OP_CODE, OPS, Arena, GbuBatchConfig, GbuCompletion, GbuRequest, GbuServerConfig, GbuServerStats, Graph,
+    OP_CODE, OPS, REQ_DISCARD_OUTPUT, Arena, GbuBatchConfig, GbuCompletion, GbuRequest, GbuServerConfig, GbuServerStats, Graph,
     Server, gbu_server_cancel, gbu_server_copy_output, gbu_server_create, gbu_server_default_config, gbu_server_destroy,
     gbu_server_get_stats, gbu_server_now_ns, gbu_server_poll, gbu_server_release, gbu_server_submit, gbu_convert_utf16le_to_utf8_batched,
     gbu_convert_utf8_to_utf16le_batched, gbu_exclusive_scan_u64, gbu_get_batch_config,

@@ -44,7 +44,7 @@ class GbuServerConfig(ctypes.Structure):
 
 
 class GbuRequest(ctypes.Structure):
-    _fields_ = [("op", ctypes.c_int32), ("reserved", ctypes.c_int32), ("src", ctypes.c_void_p),
+    _fields_ = [("op", ctypes.c_int32), ("flags", ctypes.c_int32), ("src", ctypes.c_void_p),
                 ("n", ctypes.c_uint64), ("arrival_ns", ctypes.c_uint64), ("tag", ctypes.c_uint64)]
 
 
@@ -58,6 +58,8 @@ class GbuServerStats(ctypes.Structure):
     _fields_ = [(f, ctypes.c_uint64) for f in ("submitted", "admitted", "completed", "launches", "groups",
                                                 "budget_used_bytes", "peak_budget_bytes", "inflight", "pending")]
 
+
+REQ_DISCARD_OUTPUT = 1  # gbu_request.flags: free the output at completion
 
 # Operation codes of the batched calls (gbu_op).
 OPS = ("validate_utf8", "utf16_length_from_utf8", "convert_utf8_to_utf16le", "validate_utf16le",

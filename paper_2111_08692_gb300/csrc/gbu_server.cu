@@ -183,7 +183,15 @@ void complete_locked(gbu_server *s, const Req &q, const gbu_result &res, uint64_
   c.arrival_ns = q.r.arrival_ns;
   c.admit_ns = q.admit_ns;
   c.complete_ns = now;
-  if (q.out_off != ~0ull) s->outputs[q.id] = {q.out_off, out_budget(q.r.op, q.r.n)};
+  if (q.out_off != ~0ull) {
+    if (q.r.flags & GBU_REQ_DISCARD_OUTPUT) {
+      s->arena.release(q.out_off);
+      s->budget_used -= out_budget(q.r.op, q.r.n);
+      c.dst = nullptr;
+    } else {
+      s->outputs[q.id] = {q.out_off, out_budget(q.r.op, q.r.n)};
+    }
+  }
   s->done.push_back(c);
   s->stats.completed++;
 }
@@ -382,10 +390,12 @@ extern "C" void gbu_server_default_config(gbu_server_config *cfg) {
   if (!cfg) return;
   memset(cfg, 0, sizeof(*cfg));
   cfg->budget_bytes = 8ull << 30;
-  cfg->streams = 4;
-  cfg->groups_per_stream = 4;
+  // 16 streams x 8 groups x 2 single-buffer launches per group: the best of a sweep on GB300
+  // (enough launches in flight that mid-sized requests, a few partitions each, fill the SMs)
+  cfg->streams = 16;
+  cfg->groups_per_stream = 8;
   cfg->max_group = 4096;
-  cfg->max_large_group = 32;
+  cfg->max_large_group = 2;
   cfg->large_bytes = 64 << 10;
   cfg->max_request_units = 16ull << 20;
   cfg->max_inflight = 1u << 16;
