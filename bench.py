@@ -64,6 +64,26 @@ def dist_env():
     return int(os.environ.get("RANK", "0")), int(os.environ.get("LOCAL_RANK", "0")), ws
 
 
+def max_over_ranks(x: float, dist, device) -> float:
+    """The largest value of x over all ranks (x itself without a process group)."""
+    if not dist:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(x: float, dist, device) -> float:
+    """The sum of x over all ranks (x itself without a process group)."""
+    if not dist:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
 def workload_config(args, profiles):
     return {
         "workload": f"single {args.size >> 20} MiB buffers per profile ({', '.join(profiles)}): "
@@ -270,16 +290,14 @@ def run_ours(args):
         t1.record(stream)
         torch.cuda.synchronize()
     launches = codec.launches() - launches0
-    total_ms = t0.elapsed_time(t1)
+    total_ms = max_over_ranks(t0.elapsed_time(t1), dist, dev)
     if dist:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
         dist.barrier()
 
     in_bytes_step = sum(b["s8"].numel() * 3 + 2 * b["s16"].numel() * 3 for b in bufs)
     ms_per_step = total_ms / args.steps
-    value = world * in_bytes_step / (ms_per_step * 1e-3) / 1e9
+    # whole job: the input bytes every rank processed in one step over the slowest rank's time
+    value = sum_over_ranks(in_bytes_step, dist, dev) / (ms_per_step * 1e-3) / 1e9
 
     # per-kernel durations (same stream, inside the timed region)
     per = {}
@@ -407,11 +425,8 @@ def run_batched(args, codec, dev, dist, world):
     e1.record(side)
     side.synchronize()
     launches = codec.launches() - launches0
-    ms = e0.elapsed_time(e1) / args.batched_steps
-    if dist:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(e0.elapsed_time(e1) / args.batched_steps, dist, dev)
+    strings_all = sum_over_ranks(B, dist, dev)
     graph.close()
     # per-kernel times (each call bracketed by events, outside the graph)
     per = {}
@@ -459,7 +474,7 @@ def run_batched(args, codec, dev, dist, world):
     loop_launches = codec.launches() - l0
     loop_ms = a.elapsed_time(z)
     loop_sps = S / (loop_ms * 1e-3)
-    value = world * B / (ms * 1e-3)
+    value = strings_all / (ms * 1e-3)
     return {"metric": "batched strings/s", "value": round(value, 1), "unit": "strings/s",
             "ms_per_step": round(ms, 4), "steps": args.batched_steps, "strings_per_step": B,
             "input_bytes_per_step": int(b["u8"].size + 2 * b["u16"].size),
@@ -600,15 +615,12 @@ def run_e2e(args, codec, bufs, stream, dist, world, call):
         step()
     e1.record(stream)
     torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1)
-    if dist:
-        t = torch.tensor([ms], device=bufs[0]["s8"].device)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(e0.elapsed_time(e1), dist, bufs[0]["s8"].device)
     in_bytes = sum(b["s8"].numel() * 3 + 2 * b["s16"].numel() * 3 for b in bufs)
+    in_all = sum_over_ranks(in_bytes, dist, bufs[0]["s8"].device)
     h2d = sum(b["s8"].numel() + 2 * b["s16"].numel() for b in bufs)
     d2h = sum(2 * b["n16"] + b["n8"] + 6 * 16 + 2 * 8 for b in bufs)
-    return {"value": round(world * in_bytes * args.e2e_steps / (ms * 1e-3) / 1e9, 2), "unit": "GB/s",
+    return {"value": round(in_all * args.e2e_steps / (ms * 1e-3) / 1e9, 2), "unit": "GB/s",
             "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "steps": args.e2e_steps,
             "ms_per_step": round(ms / args.e2e_steps, 3)}
 

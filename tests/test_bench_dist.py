@@ -1,0 +1,70 @@
+"""The host logic of the multi-GPU bench path (replicas: one process per GPU, no data-path
+collective), run as two gloo ranks on the CPU: rank bookkeeping from the launcher's
+environment, the max over ranks of the timed region, and the whole-job sum of units."""
+import os
+import socket
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank_main(rank, world, port, queue):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), LOCAL_RANK=str(rank),
+                      WORLD_SIZE=str(world))
+    sys.path.insert(0, ROOT)
+    import torch
+    import torch.distributed as dist
+    import bench
+    r, lr, ws = bench.dist_env()
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        dev = torch.device("cpu")
+        # each rank timed a different duration and processed a different number of units
+        ms = bench.max_over_ranks(10.0 + 5.0 * rank, dist, dev)
+        units = bench.sum_over_ranks(1000 * (rank + 1), dist, dev)
+        dist.barrier()
+        queue.put((r, lr, ws, ms, units))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_two_rank_aggregation_over_gloo():
+    import torch.multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_rank_main, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(timeout=120)
+    assert all(p.exitcode == 0 for p in procs)
+    got = sorted(q.get(timeout=5) for _ in range(2))
+    for r, (rank, local_rank, world, ms, units) in enumerate(got):
+        assert (rank, local_rank, world) == (r, r, 2)
+        assert ms == 15.0  # the slowest rank's time
+        assert units == 3000  # all ranks' units
+
+
+def test_single_process_has_no_group():
+    sys.path.insert(0, ROOT)
+    import bench
+    assert bench.max_over_ranks(3.5, None, None) == 3.5
+    assert bench.sum_over_ranks(7, None, None) == 7.0
+
+
+@pytest.mark.parametrize("flag", ["--no-batched", "--no-serving", "--no-e2e"])
+def test_bench_arguments_parse(flag, monkeypatch):
+    sys.path.insert(0, ROOT)
+    import bench
+    monkeypatch.setattr(sys, "argv", ["bench.py", flag, "--steps", "4", "--warmup", "3"])
+    a = bench.parse()
+    assert a.steps == 4 and a.warmup == 3 and a.gpus == 1
