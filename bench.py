@@ -178,12 +178,12 @@ def measured_peak():
 
 def ncu_traffic(op: str):
     """DRAM bytes per launch (read + write) from the committed ncu summary, if it was taken
-    on the current kernel sources (the summary records their hash), else None."""
+    on the current sources of that kernel (the summary records their hash), else None."""
     path = os.path.join(ROOT, "profiles", "ncu_traffic.txt")
     if not os.path.exists(path):
         return None, None
-    from paper_2111_08692_gb300.build import sources_hash
-    want = sources_hash()
+    from paper_2111_08692_gb300.build import kernel_hash
+    want = kernel_hash(op)
     for line in open(path):
         parts = line.split()
         if len(parts) >= 5 and parts[0] == op and parts[1] == want:

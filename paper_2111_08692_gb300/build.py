@@ -51,6 +51,29 @@ def sources_hash() -> str:
     return h.hexdigest()[:12]
 
 
+# The sources each single-buffer kernel is compiled from (its device code), by operation.
+_STREAM = ["gbu_stream.cu", "gbu_chunk.cuh", "gbu_device.cuh"]
+KERNEL_SOURCES = {
+    "validate_utf8": _STREAM, "utf16_length_from_utf8": _STREAM,
+    "validate_utf16le": _STREAM, "utf8_length_from_utf16le": _STREAM,
+    "convert_utf8_to_utf16le": ["gbu_utf8.cu", "gbu_codec_utf8.cuh", "gbu_xcode.cuh", "gbu_chunk.cuh",
+                                "gbu_device.cuh"],
+    "convert_utf16le_to_utf8": ["gbu_utf16.cu", "gbu_codec_utf16.cuh", "gbu_xcode.cuh", "gbu_chunk.cuh",
+                                "gbu_device.cuh"],
+}
+
+
+def kernel_hash(op: str) -> str:
+    """Short hash of the sources of the kernel behind single-buffer operation `op` (ties an ncu
+    capture of that kernel to the code it measured)."""
+    import hashlib
+    h = hashlib.sha1()
+    for name in KERNEL_SOURCES[op]:
+        h.update(name.encode())
+        h.update(open(os.path.join(CSRC, name), "rb").read())
+    return h.hexdigest()[:12]
+
+
 def up_to_date() -> bool:
     if not os.path.exists(LIB_PATH):
         return False
