@@ -30,10 +30,49 @@ struct Utf16ToUtf8 {
   // a region of 256 words yields at most 768 bytes, +2 for a pair cut at its end, plus 15
   // bytes of alignment slack
   static constexpr uint32_t STAGE = 3 * 256 + 32;
+  // the most a region stages: 256 words of 3 bytes (a pair: 2 + 2), 2 bytes of a pair cut at
+  // its end, 15 bytes of alignment offset
+  static_assert(3 * 256 + 2 + 15 + 1 <= STAGE, "staging buffer too small");
+
+  // Bit 15 of each 16-bit lane of the result is set where that word is >= 0x80, >= 0x800, or
+  // a surrogate (D800-DFFF).  The additions cannot carry out of a lane (bit 15 is masked off
+  // first and the sum stays below 0x10000).
+  __device__ __forceinline__ static uint32_t lanes_ge80(uint32_t X) {
+    return (((X & 0x7FFF7FFFu) + 0x7F807F80u) | X) & 0x80008000u;
+  }
+  __device__ __forceinline__ static uint32_t lanes_ge800(uint32_t X) {
+    return (((X & 0x7FFF7FFFu) + 0x78007800u) | X) & 0x80008000u;
+  }
+  __device__ __forceinline__ static uint32_t lanes_sur(uint32_t X) {
+    const uint32_t s = (X & 0xF800F800u) ^ 0xD800D800u;  // a zero lane is a surrogate
+    return ~(((s & 0x7FFF7FFFu) + 0x7FFF7FFFu) | s) & 0x80008000u;
+  }
+
+  // UTF-8 bytes of the 8 words of a chunk that lies wholly inside the buffer: one per word,
+  // one more per word >= 0x80 and one more per word >= 0x800, one less per surrogate word
+  // (Section 3 sizes; a pair counts 2 + 2).  The flags are summed with byte dot products
+  // (0x80 per flag), which run on the FMA pipe.
+  __device__ __forceinline__ static uint32_t count_inside(const uint32_t W[4], uint32_t *sur_any) {
+    uint32_t acc = 0, sub = 0, sa = 0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const uint32_t sr = lanes_sur(W[k]);
+      acc = __dp4a(lanes_ge80(W[k]), 0x01000100u, acc);
+      acc = __dp4a(lanes_ge800(W[k]), 0x01000100u, acc);
+      sub = __dp4a(sr, 0x01000100u, sub);
+      sa |= sr;
+    }
+    *sur_any = sa;
+    return 8u + ((acc - sub) >> 7);
+  }
 
   __device__ __forceinline__ static uint32_t count(const Params &p, uint4 v, long long c, bool edge) {
     const uint32_t W[4] = {v.x, v.y, v.z, v.w};
-    if (!edge && ((W[0] | W[1] | W[2] | W[3]) & 0xFF80FF80u) == 0) return 8;  // all ASCII
+    if (!edge) {
+      if (((W[0] | W[1] | W[2] | W[3]) & 0xFF80FF80u) == 0) return 8;  // all ASCII
+      uint32_t sa;
+      return count_inside(W, &sa);
+    }
     uint32_t cnt = 0;
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
@@ -48,6 +87,111 @@ struct Utf16ToUtf8 {
                                                    uint32_t next, long long c, bool edge,
                                                    uint8_t *st, uint32_t base,
                                                    unsigned long long &err_pos) {
+    if (__any_sync(0xffffffffu, edge)) return convert_generic(p, v, prev, next, c, edge, st, base, err_pos);
+    return convert_inside(v, prev, next, c, st, base, err_pos);
+  }
+
+  // Stores the UTF-8 form of one word that is not part of a surrogate pair at st[o..]: one,
+  // two or three bytes (a lone surrogate takes the three-byte form; its third byte lands in
+  // the next word's slot, and is overwritten there, or lies after the first error).
+  __device__ __forceinline__ static void store_bmp(uint8_t *st, uint32_t o, uint32_t w, bool g1, bool g2) {
+    const uint32_t c6 = w & 0x3Fu, t6 = w >> 6;
+    const uint32_t b0 = g2 ? 0xE0u + (w >> 12) : (g1 ? 0xC0u + t6 : w);
+    const uint32_t b1 = g2 ? (0x80u | (t6 & 0x3Fu)) : 0x80u + c6;
+    st[o] = (uint8_t)b0;
+    if (g1) st[o + 1] = (uint8_t)b1;
+    if (g2) st[o + 2] = (uint8_t)(0x80u + c6);
+  }
+
+  // A region none of whose chunks touches a buffer end.
+  __device__ __forceinline__ static Region convert_inside(uint4 v, uint32_t prev, uint32_t next, long long c,
+                                                          uint8_t *st, uint32_t base,
+                                                          unsigned long long &err_pos) {
+    const int lane = threadIdx.x & 31;
+    const uint32_t W[4] = {v.x, v.y, v.z, v.w};
+    if (__all_sync(0xffffffffu, ((W[0] | W[1] | W[2] | W[3]) & 0xFF80FF80u) == 0)) {
+      // an all-ASCII region: one byte per word (Section 4's ASCII route)
+      const uint32_t x0 = base + 8 * lane;
+      const uint32_t lo8 = __byte_perm(W[0], W[1], 0x6420);
+      const uint32_t hi8 = __byte_perm(W[2], W[3], 0x6420);
+      if ((x0 & 7) == 0) {
+        *reinterpret_cast<uint2 *>(st + x0) = make_uint2(lo8, hi8);
+      } else if ((x0 & 3) == 0) {
+        reinterpret_cast<uint32_t *>(st + x0)[0] = lo8;
+        reinterpret_cast<uint32_t *>(st + x0)[1] = hi8;
+      } else {
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+          st[x0 + b] = (uint8_t)(lo8 >> (8 * b));
+          st[x0 + 4 + b] = (uint8_t)(hi8 >> (8 * b));
+        }
+      }
+      return Region{256u, 0u, 0u, 256u};
+    }
+    uint32_t sur_any;
+    const uint32_t cnt = count_inside(W, &sur_any);
+    Region g;
+    uint32_t o = base + warp_exclusive_scan(cnt, &g.total);
+    g.units = g.total;
+    g.skip = 0;
+    g.extra = 0;
+    if (!__any_sync(0xffffffffu, sur_any != 0)) {
+      // no surrogate in the region: every word is a character of one to three bytes
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const uint32_t w = (j & 1) ? W[j >> 1] >> 16 : W[j >> 1] & 0xFFFFu;
+        const bool g1 = w >= 0x80u, g2 = w >= 0x800u;
+        store_bmp(st, o, w, g1, g2);
+        o += 1u + (g1 ? 1u : 0u) + (g2 ? 1u : 0u);
+      }
+      return g;
+    }
+    // Surrogates present.  A first surrogate followed by a second one writes all four bytes
+    // of the pair (its two slots and its partner's); the second writes nothing.  A pair cut
+    // by the region's end is written by this region (2 bytes past its end), a pair cut by
+    // its start by the previous region.
+    uint32_t u[10];  // u[0] = word before the chunk, u[1..8] own words, u[9] = word after
+    u[0] = prev >> 16;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      u[1 + 2 * k] = W[k] & 0xFFFFu;
+      u[2 + 2 * k] = W[k] >> 16;
+    }
+    u[9] = next & 0xFFFFu;
+    bool err = false;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const uint32_t w = u[j + 1];
+      const bool g1 = w >= 0x80u, g2 = w >= 0x800u;
+      const bool hs = is_high16(w), ls = is_low16(w);
+      const bool pair = hs && is_low16(u[j + 2]);
+      const bool follows = ls && is_high16(u[j]);
+      err |= (hs && !pair) || (ls && !follows);
+      if (pair) {
+        const uint32_t wn = u[j + 2];
+        const uint32_t t = (w & 0x3FFu) + 0x40u;  // the code point >> 10
+        st[o] = (uint8_t)(0xF0u | (t >> 8));
+        st[o + 1] = (uint8_t)(0x80u | ((t >> 2) & 0x3Fu));
+        st[o + 2] = (uint8_t)(0x80u | ((t & 3u) << 4) | ((wn >> 6) & 0xFu));
+        st[o + 3] = (uint8_t)(0x80u | (wn & 0x3Fu));
+      } else if (!follows) {
+        store_bmp(st, o, w, g1, g2);
+      }
+      o += (hs || ls) ? 2u : 1u + (g1 ? 1u : 0u) + (g2 ? 1u : 0u);
+    }
+    if (err && (unsigned long long)c < err_pos) err_pos = (unsigned long long)c;
+    const bool cut_start = is_low16(u[1]) && is_high16(u[0]);
+    const bool cut_end = is_high16(u[8]) && is_low16(u[9]);
+    g.skip = __shfl_sync(0xffffffffu, cut_start ? 2u : 0u, 0);
+    g.extra = __shfl_sync(0xffffffffu, cut_end ? 2u : 0u, 31);
+    return g;
+  }
+
+  // Any region (also one that touches a buffer end: positions outside it are not data).
+  __device__ __forceinline__ static Region convert_generic(const Params &p, uint4 v, uint32_t prev,
+                                                           uint32_t next, long long c, bool edge,
+                                                           uint8_t *st, uint32_t base,
+                                                           unsigned long long &err_pos) {
     const int lane = threadIdx.x & 31;
     if (__all_sync(0xffffffffu, ((v.x | v.y | v.z | v.w) & 0xFF80FF80u) == 0 && !edge)) {
       // an all-ASCII region: one byte per word, no surrogate among its words (a first
