@@ -28,7 +28,11 @@ const void *kernel_ptr(int k) {
   }
 }
 bool is_transcoder(int k) { return k == K_C8 || k == K_C16; }
-size_t kernel_smem(int) { return 0; }
+size_t kernel_smem(int k) {
+  if (k == K_C8) return gbu::utf8_to_utf16_smem_bytes();
+  if (k == K_C16) return gbu::utf16_to_utf8_smem_bytes();
+  return 0;
+}
 int kernel_threads(int k) { return is_transcoder(k) ? gbu::XT : gbu::STREAM_THREADS; }
 uint32_t kernel_tile_bytes(int k) {
   return is_transcoder(k) ? gbu::PART_BYTES : gbu::stream_tile_bytes();

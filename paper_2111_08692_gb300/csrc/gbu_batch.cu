@@ -178,7 +178,9 @@ __device__ __forceinline__ uint32_t region_convert(const Params &sp, long long c
   const uint32_t h = (uint32_t)((sp.dshift + S) & (V - 1));
   if (lane == 0) bulk_wait_read<1>();  // the store of two regions ago has read this buffer
   __syncwarp();
-  const Region g = C::convert(sp, v, prev, next, c, edge, st, h, err_pos);
+  const long long r0 = c - (long long)CHUNK * lane;  // the region's start
+  const bool inside = r0 >= (long long)sp.off0 && r0 + (long long)REGION_BYTES <= (long long)sp.vbytes;
+  const Region g = convert_counted<C>(sp, v, prev, next, c, edge, inside, st, h, err_pos);
   fence_proxy_async_smem();
   __syncwarp();
   store_region(sp, st, S, g.skip, g.total, g.extra);
@@ -255,7 +257,8 @@ __device__ __forceinline__ void cta_string(const BatchParams &bp, uint64_t i, Ba
     if (T::CONVERT) {
       // region offsets inside the step: count first, then scan the NWARPS region counts
       const bool edge = c < lo || c + 16 > hi;
-      uint32_t cnt = C::count(sp, v, c, edge);
+      bool cf;
+      uint32_t cnt = C::count(sp, v, c, edge, cf);
 #pragma unroll
       for (int d = 16; d >= 1; d >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, d);
       if (lane == 0) sm.rcount[buf][warp] = cnt;

@@ -66,12 +66,17 @@ struct Utf16ToUtf8 {
     return 8u + ((acc - sub) >> 7);
   }
 
-  __device__ __forceinline__ static uint32_t count(const Params &p, uint4 v, long long c, bool edge) {
+  // flag: the chunk holds a surrogate word (or touches a buffer end).
+  __device__ __forceinline__ static uint32_t count(const Params &p, uint4 v, long long c, bool edge,
+                                                   bool &flag) {
     const uint32_t W[4] = {v.x, v.y, v.z, v.w};
+    flag = edge;
     if (!edge) {
       if (((W[0] | W[1] | W[2] | W[3]) & 0xFF80FF80u) == 0) return 8;  // all ASCII
       uint32_t sa;
-      return count_inside(W, &sa);
+      const uint32_t n = count_inside(W, &sa);
+      flag = sa != 0;
+      return n;
     }
     uint32_t cnt = 0;
 #pragma unroll
@@ -84,11 +89,11 @@ struct Utf16ToUtf8 {
   }
 
   __device__ __forceinline__ static Region convert(const Params &p, uint4 v, uint32_t prev,
-                                                   uint32_t next, long long c, bool edge,
-                                                   uint8_t *st, uint32_t base,
-                                                   unsigned long long &err_pos) {
-    if (__any_sync(0xffffffffu, edge)) return convert_generic(p, v, prev, next, c, edge, st, base, err_pos);
-    return convert_inside(v, prev, next, c, st, base, err_pos);
+                                                   uint32_t next, long long c, bool edge, bool inside,
+                                                   uint8_t *st, uint32_t base, uint32_t x0, uint32_t rtot,
+                                                   bool rflag, unsigned long long &err_pos) {
+    if (!inside) return convert_generic(p, v, prev, next, c, edge, st, base, x0, rtot, err_pos);
+    return convert_inside(v, prev, next, c, st, base, x0, rtot, rflag, err_pos);
   }
 
   // Stores the UTF-8 form of one word that is not part of a surrogate pair at st[o..]: one,
@@ -103,39 +108,36 @@ struct Utf16ToUtf8 {
     if (g2) st[o + 2] = (uint8_t)(0x80u + c6);
   }
 
-  // A region none of whose chunks touches a buffer end.
+  // A region none of whose chunks touches a buffer end; x0 / rtot / rflag come from the
+  // count pass (rflag: a surrogate in the region).
   __device__ __forceinline__ static Region convert_inside(uint4 v, uint32_t prev, uint32_t next, long long c,
-                                                          uint8_t *st, uint32_t base,
+                                                          uint8_t *st, uint32_t base, uint32_t x0,
+                                                          uint32_t rtot, bool rflag,
                                                           unsigned long long &err_pos) {
     const int lane = threadIdx.x & 31;
     const uint32_t W[4] = {v.x, v.y, v.z, v.w};
-    if (__all_sync(0xffffffffu, ((W[0] | W[1] | W[2] | W[3]) & 0xFF80FF80u) == 0)) {
-      // an all-ASCII region: one byte per word (Section 4's ASCII route)
-      const uint32_t x0 = base + 8 * lane;
+    if (rtot == 256u) {
+      // 256 words and 256 bytes: every word is ASCII (Section 4's ASCII route)
+      const uint32_t xa = base + 8 * lane;
       const uint32_t lo8 = __byte_perm(W[0], W[1], 0x6420);
       const uint32_t hi8 = __byte_perm(W[2], W[3], 0x6420);
-      if ((x0 & 7) == 0) {
-        *reinterpret_cast<uint2 *>(st + x0) = make_uint2(lo8, hi8);
-      } else if ((x0 & 3) == 0) {
-        reinterpret_cast<uint32_t *>(st + x0)[0] = lo8;
-        reinterpret_cast<uint32_t *>(st + x0)[1] = hi8;
+      if ((xa & 7) == 0) {
+        *reinterpret_cast<uint2 *>(st + xa) = make_uint2(lo8, hi8);
+      } else if ((xa & 3) == 0) {
+        reinterpret_cast<uint32_t *>(st + xa)[0] = lo8;
+        reinterpret_cast<uint32_t *>(st + xa)[1] = hi8;
       } else {
 #pragma unroll
         for (int b = 0; b < 4; ++b) {
-          st[x0 + b] = (uint8_t)(lo8 >> (8 * b));
-          st[x0 + 4 + b] = (uint8_t)(hi8 >> (8 * b));
+          st[xa + b] = (uint8_t)(lo8 >> (8 * b));
+          st[xa + 4 + b] = (uint8_t)(hi8 >> (8 * b));
         }
       }
       return Region{256u, 0u, 0u, 256u};
     }
-    uint32_t sur_any;
-    const uint32_t cnt = count_inside(W, &sur_any);
-    Region g;
-    uint32_t o = base + warp_exclusive_scan(cnt, &g.total);
-    g.units = g.total;
-    g.skip = 0;
-    g.extra = 0;
-    if (!__any_sync(0xffffffffu, sur_any != 0)) {
+    Region g{rtot, 0u, 0u, rtot};
+    uint32_t o = base + x0;
+    if (!rflag) {
       // no surrogate in the region: every word is a character of one to three bytes
 #pragma unroll
       for (int j = 0; j < 8; ++j) {
@@ -187,32 +189,12 @@ struct Utf16ToUtf8 {
     return g;
   }
 
-  // Any region (also one that touches a buffer end: positions outside it are not data).
+  // A region that touches a buffer end (positions outside [off0, vbytes) are not data; the
+  // count pass gave them no units).  Word by word, with the pair rules of convert_inside.
   __device__ __forceinline__ static Region convert_generic(const Params &p, uint4 v, uint32_t prev,
                                                            uint32_t next, long long c, bool edge,
-                                                           uint8_t *st, uint32_t base,
-                                                           unsigned long long &err_pos) {
-    const int lane = threadIdx.x & 31;
-    if (__all_sync(0xffffffffu, ((v.x | v.y | v.z | v.w) & 0xFF80FF80u) == 0 && !edge)) {
-      // an all-ASCII region: one byte per word, no surrogate among its words (a first
-      // surrogate just before the region is judged by the region that owns it)
-      const uint32_t x0 = base + 8 * lane;
-      const uint32_t lo8 = __byte_perm(v.x, v.y, 0x6420);
-      const uint32_t hi8 = __byte_perm(v.z, v.w, 0x6420);
-      if ((x0 & 7) == 0) {
-        *reinterpret_cast<uint2 *>(st + x0) = make_uint2(lo8, hi8);
-      } else if ((x0 & 3) == 0) {
-        reinterpret_cast<uint32_t *>(st + x0)[0] = lo8;
-        reinterpret_cast<uint32_t *>(st + x0)[1] = hi8;
-      } else {
-#pragma unroll
-        for (int b = 0; b < 4; ++b) {
-          st[x0 + b] = (uint8_t)(lo8 >> (8 * b));
-          st[x0 + 4 + b] = (uint8_t)(hi8 >> (8 * b));
-        }
-      }
-      return Region{256u, 0u, 0u, 256u};
-    }
+                                                           uint8_t *st, uint32_t base, uint32_t x0,
+                                                           uint32_t rtot, unsigned long long &err_pos) {
     const uint32_t W[4] = {v.x, v.y, v.z, v.w};
     uint32_t u[10];  // u[0] = word before the chunk, u[1..8] own words, u[9] = word after
     u[0] = prev >> 16;
@@ -226,81 +208,37 @@ struct Utf16ToUtf8 {
 #pragma unroll
     for (int j = 0; j < 8; ++j)
       valid[j] = !edge || (c + 2 * j >= (long long)p.off0 && c + 2 * j < (long long)p.vbytes);
-
-    const uint32_t nonascii = (W[0] | W[1] | W[2] | W[3]) & 0xFF80FF80u;
-    const bool warp_ascii = __all_sync(0xffffffffu, nonascii == 0 && !edge);
-    uint32_t cnt = 0;
-    uint32_t sz[8];
     bool err = false;
-    if (warp_ascii) {
-      cnt = 8;
-    } else {
+    uint32_t o = base + x0;
 #pragma unroll
-      for (int j = 0; j < 8; ++j) {
-        const uint32_t w = u[j + 1];
-        sz[j] = valid[j] ? len8_of_word(w) : 0u;
-        cnt += sz[j];
-        const bool hw = is_high16(w), lw = is_low16(w);
-        err |= valid[j] && ((hw && !is_low16(u[j + 2])) || (lw && !is_high16(u[j])));
+    for (int j = 0; j < 8; ++j) {
+      if (!valid[j]) continue;
+      const uint32_t w = u[j + 1];
+      const bool g1 = w >= 0x80u, g2 = w >= 0x800u;
+      const bool hs = is_high16(w), ls = is_low16(w);
+      // a word outside the buffer reads as 0: never a surrogate
+      const bool pair = hs && is_low16(u[j + 2]);
+      const bool follows = ls && is_high16(u[j]);
+      err |= (hs && !pair) || (ls && !follows);
+      if (pair) {
+        const uint32_t wn = u[j + 2];
+        const uint32_t t = (w & 0x3FFu) + 0x40u;
+        st[o] = (uint8_t)(0xF0u | (t >> 8));
+        st[o + 1] = (uint8_t)(0x80u | ((t >> 2) & 0x3Fu));
+        st[o + 2] = (uint8_t)(0x80u | ((t & 3u) << 4) | ((wn >> 6) & 0xFu));
+        st[o + 3] = (uint8_t)(0x80u | (wn & 0x3Fu));
+      } else if (!follows) {
+        store_bmp(st, o, w, g1, g2);
       }
+      o += (hs || ls) ? 2u : 1u + (g1 ? 1u : 0u) + (g2 ? 1u : 0u);
     }
     if (err && (unsigned long long)c < err_pos) err_pos = (unsigned long long)c;
-
-    Region g;
-    const uint32_t x0 = base + warp_exclusive_scan(cnt, &g.total);
-    g.units = g.total;
+    Region g{rtot, 0u, 0u, rtot};
     // a pair cut by the region's start or end (lane 0's first word, lane 31's last word)
     const bool cut_start = valid[0] && is_low16(u[1]) && is_high16(u[0]);
     const bool cut_end = valid[7] && is_high16(u[8]) && is_low16(u[9]);
     g.skip = __shfl_sync(0xffffffffu, cut_start ? 2u : 0u, 0);
     g.extra = __shfl_sync(0xffffffffu, cut_end ? 2u : 0u, 31);
-    if (warp_ascii) {
-      const uint32_t lo8 = __byte_perm(W[0], W[1], 0x6420);
-      const uint32_t hi8 = __byte_perm(W[2], W[3], 0x6420);
-      if ((x0 & 7) == 0) {
-        *reinterpret_cast<uint2 *>(st + x0) = make_uint2(lo8, hi8);
-      } else if ((x0 & 3) == 0) {
-        reinterpret_cast<uint32_t *>(st + x0)[0] = lo8;
-        reinterpret_cast<uint32_t *>(st + x0)[1] = hi8;
-      } else {
-#pragma unroll
-        for (int b = 0; b < 4; ++b) {
-          st[x0 + b] = (uint8_t)(lo8 >> (8 * b));
-          st[x0 + 4 + b] = (uint8_t)(hi8 >> (8 * b));
-        }
-      }
-    } else if (x0 + cnt + 2 <= STAGE) {  // else: after the first error, nothing to store
-      const bool has_sur = __any_sync(0xffffffffu, ((W[0] | W[1] | W[2] | W[3]) & 0x80008000u) != 0);
-      uint32_t o = x0;
-#pragma unroll
-      for (int j = 0; j < 8; ++j) {
-        const uint32_t w = u[j + 1];
-        uint32_t nb = sz[j];  // bytes written by this word
-        // the one-, two- and three-byte forms (a lone surrogate takes the two-byte form's
-        // slots with unspecified bytes: it only occurs after the first error)
-        const uint32_t b2 = 0x80C0u | (w >> 6) | ((w & 0x3Fu) << 8);
-        const uint32_t b3 = 0x8080E0u | (w >> 12) | (((w >> 6) & 0x3Fu) << 8) | ((w & 0x3Fu) << 16);
-        uint32_t bytes = nb == 1 ? w : (nb == 2 ? b2 : b3);
-        if (has_sur) {
-          if (is_high16(w) && is_low16(u[j + 2])) {
-            const uint32_t cp = (((w & 0x3FFu) << 10) | (u[j + 2] & 0x3FFu)) + 0x10000u;
-            bytes = (0xF0u | (cp >> 18)) | ((0x80u | ((cp >> 12) & 0x3Fu)) << 8) |
-                    ((0x80u | ((cp >> 6) & 0x3Fu)) << 16) | ((0x80u | (cp & 0x3Fu)) << 24);
-            nb = valid[j] ? 4u : 0u;
-          } else if (is_low16(w) && is_high16(u[j])) {
-            nb = 0;  // written with its first word
-          }
-        }
-#pragma unroll
-        for (uint32_t q = 0; q < 4; ++q)
-          if (q < nb) st[o + q] = (uint8_t)(bytes >> (8 * q));
-        o += sz[j];
-      }
-    }
-    if (g.total + g.extra > STAGE - base) {  // only after the first error
-      g.extra = 0;
-      if (g.total > STAGE - base) g.total = STAGE - base;
-    }
     return g;
   }
 };

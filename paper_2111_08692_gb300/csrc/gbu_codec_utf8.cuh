@@ -48,9 +48,15 @@ struct Utf8ToUtf16 {
   // the first error and are dropped
   static constexpr uint32_t STAGE = 512 + 16 + 16;
 
-  __device__ __forceinline__ static uint32_t count(const Params &p, uint4 v, long long c, bool edge) {
+  // flag: the chunk holds a byte >= 0x80 (or touches a buffer end).
+  __device__ __forceinline__ static uint32_t count(const Params &p, uint4 v, long long c, bool edge,
+                                                   bool &flag) {
     const uint32_t W[4] = {v.x, v.y, v.z, v.w};
-    if (!edge && ((W[0] | W[1] | W[2] | W[3]) & 0x80808080u) == 0) return 16;  // all ASCII
+    flag = true;
+    if (!edge && ((W[0] | W[1] | W[2] | W[3]) & 0x80808080u) == 0) {  // all ASCII
+      flag = false;
+      return 16;
+    }
     uint32_t cnt = 0;
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
@@ -61,15 +67,16 @@ struct Utf8ToUtf16 {
     return cnt;
   }
 
-  // Validates the chunk and stages its UTF-16 words.  Offsets come first (per-byte counts,
-  // then a warp scan), so each pair of positions is decoded and stored in one pass without
-  // keeping decoded words in registers.
+  // Validates the chunk and stages its UTF-16 words.  The lane's offset x0 (inside the
+  // region), the region total rtot and the region flag rflag (a byte >= 0x80 in the region,
+  // or a chunk at a buffer end) come from the count pass, so each pair of positions is
+  // decoded and stored in one pass without keeping decoded words in registers.
   __device__ __forceinline__ static Region convert(const Params &p, uint4 v, uint32_t prev,
-                                                   uint32_t next, long long c, bool edge,
-                                                   uint16_t *st, uint32_t base,
-                                                   unsigned long long &err_pos) {
+                                                   uint32_t next, long long c, bool edge, bool inside,
+                                                   uint16_t *st, uint32_t base, uint32_t x0, uint32_t rtot,
+                                                   bool rflag, unsigned long long &err_pos) {
     const int lane = threadIdx.x & 31;
-    if (__all_sync(0xffffffffu, ((v.x | v.y | v.z | v.w) & 0x80808080u) == 0 && !edge)) {
+    if (!rflag) {
       // an all-ASCII region: one word per byte; the only possible error is a leading byte
       // just before the region that wants continuation bytes inside it (lane 0's chunk)
       if (lane == 0) {
@@ -103,25 +110,13 @@ struct Utf8ToUtf16 {
       cnt = __dp4a(uw[k], 0x01010101u, cnt);
     }
     uint32_t err = utf8_structure_errors(f);
-    const uint32_t nonascii = (W[1] | W[2] | W[3] | W[4]) & 0x80808080u;
-    const bool warp_ascii = __all_sync(0xffffffffu, nonascii == 0 && !edge);
 
-    Region g;
-    const uint32_t x0 = base + warp_exclusive_scan(cnt, &g.total);
-    g.skip = 0;
-    g.extra = 0;
+    Region g{rtot, 0u, 0u, rtot};
+    x0 += base;
     // a chunk that would overflow the staging buffer lies after the first error: it stores
     // nothing (its validation still runs)
     const bool store = x0 + cnt <= STAGE;
-    if (warp_ascii) {
-      uint32_t u[8];
-#pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        u[2 * k] = __byte_perm(W[k + 1], 0, 0x4140);
-        u[2 * k + 1] = __byte_perm(W[k + 1], 0, 0x4342);
-      }
-      stage16(st, x0, u);  // an all-ASCII region fits: x0 + 16 <= 7 + 512
-    } else {
+    {
       uint32_t c2 = 0, c3 = 0, c4 = 0;
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
@@ -181,7 +176,6 @@ struct Utf8ToUtf16 {
       err |= bad;
     }
     if (err && (unsigned long long)c < err_pos) err_pos = (unsigned long long)c;
-    g.units = g.total;
     if (g.total > STAGE - base) g.total = STAGE - base;  // only after the first error
     return g;
   }

@@ -11,9 +11,12 @@ namespace gbu {
 const void *stream_kernel_ptr(int mode);
 uint32_t stream_tile_bytes();
 
-// transcoders (static shared memory only)
+// transcoders (dynamic shared memory of the given size; above 48 KB it needs the
+// cudaFuncAttributeMaxDynamicSharedMemorySize opt-in before the first launch)
 const void *utf8_to_utf16_kernel_ptr();
 const void *utf16_to_utf8_kernel_ptr();
+size_t utf8_to_utf16_smem_bytes();
+size_t utf16_to_utf8_smem_bytes();
 
 // batched kernels (mode: BatchMode; nwarps: 4, 8 or 16 warps per CTA) and the u64 scan
 const void *batch_kernel_ptr(int mode, int nwarps);

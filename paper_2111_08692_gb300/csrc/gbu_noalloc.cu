@@ -49,7 +49,8 @@ struct DeviceSetup {
 };
 DeviceSetup setups[MAX_DEVICES];
 
-// One-time setup on `device` (which is current): the symbol's device address, the grid size,
+// One-time setup on `device` (which is current): the kernel's shared-memory opt-in, the
+// symbol's device address, the grid size,
 // and the workspace's initial contents: every state word zero (epoch 0, never a live epoch),
 // the header's counters zero, its epoch 1 and its first-error key "none".
 void setup_device(DeviceSetup &s, int device) {
@@ -59,8 +60,11 @@ void setup_device(DeviceSetup &s, int device) {
     return;
   }
   int sms = 0, bps = 0;
-  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess ||
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, gbu::utf8_to_utf16_kernel_ptr(), gbu::XT, 0) !=
+  const size_t smem = gbu::utf8_to_utf16_smem_bytes();
+  if (cudaFuncSetAttribute(gbu::utf8_to_utf16_kernel_ptr(), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)smem) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, gbu::utf8_to_utf16_kernel_ptr(), gbu::XT, smem) !=
           cudaSuccess ||
       sms < 1 || bps < 1) {
     cudaGetLastError();
@@ -121,8 +125,8 @@ extern "C" int gbu_convert_utf8_to_utf16le_noalloc(const uint8_t *src, uint64_t 
   if (p.ntiles < grid) grid = p.ntiles;
   if (grid < 1) grid = 1;
   void *args[] = {(void *)&p};
-  if (cudaLaunchKernel(gbu::utf8_to_utf16_kernel_ptr(), dim3(grid), dim3(gbu::XT), args, 0,
-                       (cudaStream_t)stream) != cudaSuccess) {
+  if (cudaLaunchKernel(gbu::utf8_to_utf16_kernel_ptr(), dim3(grid), dim3(gbu::XT), args,
+                       gbu::utf8_to_utf16_smem_bytes(), (cudaStream_t)stream) != cudaSuccess) {
     cudaGetLastError();
     return GBU_CUDA_ERROR;
   }

@@ -8,7 +8,8 @@
 namespace gbu {
 
 __global__ void __launch_bounds__(XT, 2) utf16_to_utf8_kernel(const Params p) {
-  __shared__ XSmem<Utf16ToUtf8> sm;
+  extern __shared__ __align__(128) unsigned char smem_raw[];  // sizeof(XSmem), set at launch
+  XSmem<Utf16ToUtf8> &sm = *reinterpret_cast<XSmem<Utf16ToUtf8> *>(smem_raw);
   transcode<Utf16ToUtf8>(p, sm, [&](uint32_t status, unsigned long long key, unsigned long long tot) {
     if (status) {
       write_result(p.result, GBU_TIMEOUT, 0);
@@ -24,5 +25,6 @@ __global__ void __launch_bounds__(XT, 2) utf16_to_utf8_kernel(const Params p) {
 }
 
 const void *utf16_to_utf8_kernel_ptr() { return (const void *)utf16_to_utf8_kernel; }
+size_t utf16_to_utf8_smem_bytes() { return sizeof(XSmem<Utf16ToUtf8>); }
 
 }  // namespace gbu

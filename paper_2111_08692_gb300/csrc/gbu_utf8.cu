@@ -8,7 +8,8 @@
 namespace gbu {
 
 __global__ void __launch_bounds__(XT, 2) utf8_to_utf16_kernel(const Params p) {
-  __shared__ XSmem<Utf8ToUtf16> sm;
+  extern __shared__ __align__(128) unsigned char smem_raw[];  // sizeof(XSmem), set at launch
+  XSmem<Utf8ToUtf16> &sm = *reinterpret_cast<XSmem<Utf8ToUtf16> *>(smem_raw);
   transcode<Utf8ToUtf16>(p, sm, [&](uint32_t status, unsigned long long key, unsigned long long tot) {
     if (status) {
       write_result(p.result, GBU_TIMEOUT, 0);
@@ -24,5 +25,6 @@ __global__ void __launch_bounds__(XT, 2) utf8_to_utf16_kernel(const Params p) {
 }
 
 const void *utf8_to_utf16_kernel_ptr() { return (const void *)utf8_to_utf16_kernel; }
+size_t utf8_to_utf16_smem_bytes() { return sizeof(XSmem<Utf8ToUtf16>); }
 
 }  // namespace gbu

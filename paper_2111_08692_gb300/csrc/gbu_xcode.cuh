@@ -17,15 +17,19 @@
 //   struct Codec {
 //     using Out = uint8_t or uint16_t;                 // output code unit
 //     static constexpr uint32_t STAGE;                 // staged units per warp buffer
-//     __device__ static uint32_t count(const Params&, uint4 v, long long c, bool edge);
+//     __device__ static uint32_t count(const Params&, uint4 v, long long c, bool edge, bool& flag);
 //     __device__ static Region convert(const Params&, uint4 v, uint32_t prev, uint32_t next,
-//                                      long long c, bool edge, Out* st, uint32_t base,
+//                                      long long c, bool edge, bool inside, Out* st,
+//                                      uint32_t base, uint32_t x0, uint32_t rtot, bool rflag,
 //                                      unsigned long long& err_pos);
 //   };
 // count() returns the units one chunk contributes to its region (the total that converting
-// the region stages); convert() stages the chunk's units at base + (the lane's exclusive
-// prefix inside the warp) and returns the region's unit count and the units it writes past
-// its end or leaves to its predecessor at its start.
+// the region stages) and sets a codec-defined flag (the region's flag is the OR over its
+// lanes).  The count pass keeps, for every region, each lane's exclusive offset x0, the
+// region total rtot and the flag, so convert() neither recounts nor rescans: it stages the
+// lane's units at base + x0 and returns the region's unit count and the units it writes past
+// its end or leaves to its predecessor at its start.  `inside` (uniform over the warp) says
+// that no chunk of the region touches a buffer end.
 #pragma once
 
 #include <stdint.h>
@@ -45,8 +49,13 @@ struct Region {
   uint32_t units;  // units counted for the region (unclamped: the region's output length)
 };
 
+constexpr int PART_REGIONS = PART_ROUNDS * XWARPS;  // 128 regions per partition
+
 struct __align__(16) PartCounts {
-  uint32_t off[PART_ROUNDS * XWARPS];  // region offsets inside the partition, in byte order
+  uint32_t off[PART_REGIONS];           // region offsets inside the partition, in byte order
+  uint16_t lane_off[PART_REGIONS][32];  // each lane's exclusive offset inside its region
+  uint16_t rtot[PART_REGIONS];          // region totals
+  uint8_t flags[PART_REGIONS];          // OR of the codec flags of the region's lanes
   uint32_t total;
 };
 
@@ -67,8 +76,9 @@ __device__ __forceinline__ long long chunk_pos(uint32_t part, int w, int r, int 
          (long long)lane * CHUNK;
 }
 
-// Counts partition `part` into pc (all threads).  Region (w, r)'s units are summed by warp w
-// (two regions packed per register), then warp 0 turns the 128 counts into offsets.
+// Counts partition `part` into pc (all threads).  Warp w scans the lane counts of each of its
+// regions (two regions packed per register: a region has at most 32 x 48 units), keeping
+// every lane's exclusive offset; then warp 0 turns the 128 region totals into offsets.
 template <class Codec>
 __device__ __forceinline__ void count_partition(const Params &p, uint32_t part, PartCounts &pc) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -81,31 +91,40 @@ __device__ __forceinline__ void count_partition(const Params &p, uint32_t part, 
 #pragma unroll
   for (int r = 0; r < PART_ROUNDS; ++r)
     v[r] = load_chunk_hint(p, chunk_pos(part, warp, r, lane), inside, keep);
-  uint32_t packed[PART_ROUNDS / 2];
 #pragma unroll
   for (int r = 0; r < PART_ROUNDS; r += 2) {
     uint32_t a[2];
+    bool f[2];
 #pragma unroll
     for (int q = 0; q < 2; ++q) {
       const long long c = chunk_pos(part, warp, r + q, lane);
       const bool edge = !inside && (c < lo || c + 16 > hi);
-      a[q] = Codec::count(p, v[r + q], c, edge);
+      a[q] = Codec::count(p, v[r + q], c, edge, f[q]);
     }
-    packed[r / 2] = a[0] | (a[1] << 16);  // a region has at most 32 x 48 units
-  }
+    const uint32_t x = a[0] | (a[1] << 16);
+    uint32_t incl = x;
 #pragma unroll
-  for (int i = 0; i < PART_ROUNDS / 2; ++i) {
-#pragma unroll
-    for (int d = 16; d >= 1; d >>= 1) packed[i] += __shfl_xor_sync(0xffffffffu, packed[i], d);
-  }
-  if (lane == 0) {
-#pragma unroll
-    for (int r = 0; r < PART_ROUNDS; ++r)
-      pc.off[warp * PART_ROUNDS + r] = (packed[r / 2] >> (16 * (r & 1))) & 0xFFFFu;
+    for (int d = 1; d < 32; d <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, incl, d);
+      if (lane >= d) incl += y;
+    }
+    const uint32_t ex = incl - x;
+    const int ri = warp * PART_ROUNDS + r;
+    pc.lane_off[ri][lane] = (uint16_t)(ex & 0xFFFFu);
+    pc.lane_off[ri + 1][lane] = (uint16_t)(ex >> 16);
+    const uint32_t fb = __ballot_sync(0xffffffffu, f[0]), fb1 = __ballot_sync(0xffffffffu, f[1]);
+    if (lane == 31) {
+      pc.off[ri] = incl & 0xFFFFu;
+      pc.off[ri + 1] = incl >> 16;
+      pc.rtot[ri] = (uint16_t)(incl & 0xFFFFu);
+      pc.rtot[ri + 1] = (uint16_t)(incl >> 16);
+      pc.flags[ri] = fb != 0;
+      pc.flags[ri + 1] = fb1 != 0;
+    }
   }
   __syncthreads();
   if (warp == 0) {
-    constexpr int PER = PART_ROUNDS * XWARPS / 32;  // consecutive values per lane
+    constexpr int PER = PART_REGIONS / 32;  // consecutive values per lane
     uint32_t vals[PER], s = 0;
 #pragma unroll
     for (int i = 0; i < PER; ++i) {
@@ -139,24 +158,23 @@ template <typename U>
 __device__ __forceinline__ void store_region(const Params &p, const U *staging, uint64_t S,
                                              uint32_t skip, uint32_t cnt, uint32_t extra) {
   constexpr uint32_t V = 16 / sizeof(U);
-  const int lane = threadIdx.x & 31;
-  const uint32_t h = (uint32_t)((p.dshift + S) & (V - 1));
-  uint64_t lim = (uint64_t)cnt + extra;
-  if (S >= p.cap) lim = 0;
-  else if (p.cap - S < lim) lim = p.cap - S;
-  const uint64_t A0 = (p.dshift + S) - h;
-  U *gdst = reinterpret_cast<U *>(p.dbase) + A0;
-  const uint32_t beg = h + (skip < lim ? skip : (uint32_t)lim);
-  const uint32_t end = h + (uint32_t)lim;
-  const uint32_t first_full = (beg + V - 1) / V;
-  const uint32_t last_full = end / V;
-  if (first_full < last_full) {
-    if (lane == 0)
-      bulk_store(gdst + first_full * V, staging + first_full * V, (last_full - first_full) * 16u);
-    for (uint32_t i = beg + lane; i < first_full * V; i += 32) gdst[i] = staging[i];
-    for (uint32_t i = last_full * V + lane; i < end; i += 32) gdst[i] = staging[i];
-  } else {
-    for (uint32_t i = beg + lane; i < end; i += 32) gdst[i] = staging[i];
+  const uint32_t lane = threadIdx.x & 31;
+  const uint32_t h = (uint32_t)(p.dshift + S) & (V - 1);
+  uint32_t lim = cnt + extra;
+  const uint64_t room = p.cap > S ? p.cap - S : 0;
+  if (room < lim) lim = (uint32_t)room;
+  U *gdst = reinterpret_cast<U *>(p.dbase) + ((p.dshift + S) - h);
+  const uint32_t beg = h + (skip < lim ? skip : lim);
+  const uint32_t end = h + lim;
+  const uint32_t head_end = (beg + V - 1) & ~(V - 1);  // first 16-byte boundary at or after beg
+  const uint32_t tail_beg = end & ~(V - 1);            // last 16-byte boundary at or before end
+  if (head_end < tail_beg) {
+    if (lane == 0) bulk_store(gdst + head_end, staging + head_end, (tail_beg - head_end) * 16u / V);
+    // the ragged ends hold fewer than V <= 16 units each
+    if (beg + lane < head_end) gdst[beg + lane] = staging[beg + lane];
+    if (tail_beg + lane < end) gdst[tail_beg + lane] = staging[tail_beg + lane];
+  } else if (beg + lane < end) {  // fewer than 2V <= 32 units
+    gdst[beg + lane] = staging[beg + lane];
   }
   if (lane == 0) bulk_commit();
 }
@@ -172,6 +190,19 @@ __device__ __forceinline__ uint32_t warp_exclusive_scan(uint32_t x, uint32_t *to
   }
   *total = __shfl_sync(0xffffffffu, incl, 31);
   return incl - x;
+}
+
+// Converts one region without a count pass (one warp): counts and scans the lanes first.
+template <class Codec>
+__device__ __forceinline__ Region convert_counted(const Params &p, uint4 v, uint32_t prev, uint32_t next,
+                                                  long long c, bool edge, bool inside, typename Codec::Out *st,
+                                                  uint32_t base, unsigned long long &err_pos) {
+  bool f;
+  const uint32_t cnt = Codec::count(p, v, c, edge, f);
+  uint32_t tot;
+  const uint32_t x0 = warp_exclusive_scan(cnt, &tot);
+  const bool rf = __any_sync(0xffffffffu, f);
+  return Codec::convert(p, v, prev, next, c, edge, inside, st, base, x0, tot, rf, err_pos);
 }
 
 // The whole transcoder kernel body.  finalize(status, key, total) runs in thread 0 of the
@@ -232,12 +263,19 @@ __device__ __forceinline__ void transcode(const Params &p, XSmem<Codec> &sm, Fin
       prev_last = __shfl_sync(0xffffffffu, v.w, 31);
 
       typename Codec::Out *st = sm.staging[warp][use & 1];
-      const uint64_t S = S0 + sm.counts[cb].off[warp * PART_ROUNDS + r];
+      const PartCounts &pc = sm.counts[cb];
+      const int ri = warp * PART_ROUNDS + r;
+      const uint64_t S = S0 + pc.off[ri];
+      const uint32_t x0 = pc.lane_off[ri][lane];
+      const uint32_t rtot = pc.rtot[ri];
+      const bool rflag = pc.flags[ri] != 0;
+      const long long rc = s0 + (long long)r * REGION_BYTES;
+      const bool rin = rc >= lo && rc + (long long)REGION_BYTES <= hi;  // uniform over the warp
       constexpr uint32_t V = 16 / sizeof(typename Codec::Out);
-      const uint32_t h = (uint32_t)((p.dshift + S) & (V - 1));
+      const uint32_t h = (uint32_t)(p.dshift + S) & (V - 1);
       if (lane == 0) bulk_wait_read<1>();  // the store of two regions ago has read this buffer
       __syncwarp();
-      const Region g = Codec::convert(p, v, prev, next, c, edge, st, h, err_pos);
+      const Region g = Codec::convert(p, v, prev, next, c, edge, rin, st, h, x0, rtot, rflag, err_pos);
       fence_proxy_async_smem();
       __syncwarp();
       store_region(p, st, S, g.skip, g.total, g.extra);
