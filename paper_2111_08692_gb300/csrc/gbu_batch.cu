@@ -257,7 +257,7 @@ __device__ __forceinline__ void cta_string(const BatchParams &bp, uint64_t i, Ba
     if (T::CONVERT) {
       // region offsets inside the step: count first, then scan the NWARPS region counts
       const bool edge = c < lo || c + 16 > hi;
-      bool cf;
+      uint32_t cf;
       uint32_t cnt = C::count(sp, v, c, edge, cf);
 #pragma unroll
       for (int d = 16; d >= 1; d >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, d);

@@ -52,30 +52,52 @@ struct Utf16ToUtf8 {
   // one more per word >= 0x80 and one more per word >= 0x800, one less per surrogate word
   // (Section 3 sizes; a pair counts 2 + 2).  The flags are summed with byte dot products
   // (0x80 per flag), which run on the FMA pipe.
-  __device__ __forceinline__ static uint32_t count_inside(const uint32_t W[4], uint32_t *sur_any) {
-    uint32_t acc = 0, sub = 0, sa = 0;
+  __device__ __forceinline__ static uint32_t count_inside(const uint32_t W[4], uint32_t *sur_any,
+                                                         uint32_t *ge800_any) {
+    uint32_t acc = 0, sub = 0, sa = 0, g3 = 0;
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
       const uint32_t sr = lanes_sur(W[k]);
+      const uint32_t t = lanes_ge800(W[k]);
       acc = __dp4a(lanes_ge80(W[k]), 0x01000100u, acc);
-      acc = __dp4a(lanes_ge800(W[k]), 0x01000100u, acc);
+      acc = __dp4a(t, 0x01000100u, acc);
       sub = __dp4a(sr, 0x01000100u, sub);
       sa |= sr;
+      g3 |= t;
     }
     *sur_any = sa;
+    *ge800_any = g3;
     return 8u + ((acc - sub) >> 7);
   }
 
-  // flag: the chunk holds a surrogate word (or touches a buffer end).
+  // Flag bits of a chunk (and, ORed over the lanes, of a region).
+  static constexpr uint32_t F_SUR = 1;     // a surrogate word (or a chunk at a buffer end)
+  static constexpr uint32_t F_THREE = 2;   // a word of three UTF-8 bytes (>= 0x800)
+
+  static constexpr uint32_t REGION_UNITS = 256;  // bytes out of an all-ASCII region
+  static constexpr uint32_t DIRECT_ALIGN = 8;    // its lanes store 8 bytes each
+
+  __device__ __forceinline__ static bool ascii_region(uint32_t rtot, uint32_t) { return rtot == 256u; }
+
+  // An all-ASCII region inside the buffer, output 8-byte aligned: each lane narrows its 8
+  // words and stores them with one 8-byte store (Section 4's ASCII route).
+  __device__ __forceinline__ static void ascii_direct(const Params &p, uint4 v, uint32_t, long long,
+                                                      uint64_t S, unsigned long long &) {
+    const int lane = threadIdx.x & 31;
+    uint2 *d = reinterpret_cast<uint2 *>(p.dbase + p.dshift + S) + lane;
+    *d = make_uint2(__byte_perm(v.x, v.y, 0x6420), __byte_perm(v.z, v.w, 0x6420));
+  }
+
   __device__ __forceinline__ static uint32_t count(const Params &p, uint4 v, long long c, bool edge,
-                                                   bool &flag) {
+                                                   uint32_t &flags) {
     const uint32_t W[4] = {v.x, v.y, v.z, v.w};
-    flag = edge;
+    flags = F_SUR | F_THREE;
     if (!edge) {
+      flags = 0;
       if (((W[0] | W[1] | W[2] | W[3]) & 0xFF80FF80u) == 0) return 8;  // all ASCII
-      uint32_t sa;
-      const uint32_t n = count_inside(W, &sa);
-      flag = sa != 0;
+      uint32_t sa, g3;
+      const uint32_t n = count_inside(W, &sa, &g3);
+      flags = (sa != 0 ? F_SUR : 0u) | (g3 != 0 ? F_THREE : 0u);
       return n;
     }
     uint32_t cnt = 0;
@@ -91,9 +113,9 @@ struct Utf16ToUtf8 {
   __device__ __forceinline__ static Region convert(const Params &p, uint4 v, uint32_t prev,
                                                    uint32_t next, long long c, bool edge, bool inside,
                                                    uint8_t *st, uint32_t base, uint32_t x0, uint32_t rtot,
-                                                   bool rflag, unsigned long long &err_pos) {
+                                                   uint32_t rflags, unsigned long long &err_pos) {
     if (!inside) return convert_generic(p, v, prev, next, c, edge, st, base, x0, rtot, err_pos);
-    return convert_inside(v, prev, next, c, st, base, x0, rtot, rflag, err_pos);
+    return convert_inside(v, prev, next, c, st, base, x0, rtot, rflags, err_pos);
   }
 
   // Stores the UTF-8 form of one word that is not part of a surrogate pair at st[o..]: one,
@@ -108,11 +130,11 @@ struct Utf16ToUtf8 {
     if (g2) st[o + 2] = (uint8_t)(0x80u + c6);
   }
 
-  // A region none of whose chunks touches a buffer end; x0 / rtot / rflag come from the
-  // count pass (rflag: a surrogate in the region).
+  // A region none of whose chunks touches a buffer end; x0 / rtot / rflags come from the
+  // count pass.
   __device__ __forceinline__ static Region convert_inside(uint4 v, uint32_t prev, uint32_t next, long long c,
                                                           uint8_t *st, uint32_t base, uint32_t x0,
-                                                          uint32_t rtot, bool rflag,
+                                                          uint32_t rtot, uint32_t rflags,
                                                           unsigned long long &err_pos) {
     const int lane = threadIdx.x & 31;
     const uint32_t W[4] = {v.x, v.y, v.z, v.w};
@@ -137,7 +159,19 @@ struct Utf16ToUtf8 {
     }
     Region g{rtot, 0u, 0u, rtot};
     uint32_t o = base + x0;
-    if (!rflag) {
+    if (rflags == 0) {
+      // only words below 0x800 (Section 4's one-and-two-byte route)
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const uint32_t w = (j & 1) ? W[j >> 1] >> 16 : W[j >> 1] & 0xFFFFu;
+        const bool g1 = w >= 0x80u;
+        st[o] = (uint8_t)(g1 ? 0xC0u + (w >> 6) : w);
+        if (g1) st[o + 1] = (uint8_t)(0x80u | (w & 0x3Fu));
+        o += g1 ? 2u : 1u;
+      }
+      return g;
+    }
+    if (!(rflags & F_SUR)) {
       // no surrogate in the region: every word is a character of one to three bytes
 #pragma unroll
       for (int j = 0; j < 8; ++j) {

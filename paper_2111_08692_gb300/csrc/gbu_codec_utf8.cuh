@@ -48,13 +48,39 @@ struct Utf8ToUtf16 {
   // the first error and are dropped
   static constexpr uint32_t STAGE = 512 + 16 + 16;
 
-  // flag: the chunk holds a byte >= 0x80 (or touches a buffer end).
+  static constexpr uint32_t F_NONASCII = 1;  // flag: a byte >= 0x80 (or a chunk at a buffer end)
+
+  static constexpr uint32_t REGION_UNITS = 512;  // words out of an all-ASCII region
+  static constexpr uint32_t DIRECT_ALIGN = 8;    // its lanes store 16 words (32 bytes) each
+
+  __device__ __forceinline__ static bool ascii_region(uint32_t, uint32_t rflags) { return rflags == 0; }
+
+  // An all-ASCII region inside the buffer, output 16-byte aligned: each lane widens its 16
+  // bytes and stores them with two 16-byte stores (Section 4's ASCII path).  The only
+  // possible error is a leading byte just before the region that wants continuation bytes
+  // inside it (lane 0's chunk).
+  __device__ __forceinline__ static void ascii_direct(const Params &p, uint4 v, uint32_t prev, long long c,
+                                                      uint64_t S, unsigned long long &err_pos) {
+    const int lane = threadIdx.x & 31;
+    if (lane == 0) {
+      const Flags8 fp = classify8(prev);
+      const uint32_t req = __funnelshift_l(fp.geC0, 0u, 8) | __funnelshift_l(fp.geE0, 0u, 16) |
+                           __funnelshift_l(fp.geF0, 0u, 24);
+      if (req && (unsigned long long)c < err_pos) err_pos = (unsigned long long)c;
+    }
+    uint4 *d = reinterpret_cast<uint4 *>(reinterpret_cast<uint16_t *>(p.dbase) + p.dshift + S) + 2 * lane;
+    d[0] = make_uint4(__byte_perm(v.x, 0, 0x4140), __byte_perm(v.x, 0, 0x4342), __byte_perm(v.y, 0, 0x4140),
+                      __byte_perm(v.y, 0, 0x4342));
+    d[1] = make_uint4(__byte_perm(v.z, 0, 0x4140), __byte_perm(v.z, 0, 0x4342), __byte_perm(v.w, 0, 0x4140),
+                      __byte_perm(v.w, 0, 0x4342));
+  }
+
   __device__ __forceinline__ static uint32_t count(const Params &p, uint4 v, long long c, bool edge,
-                                                   bool &flag) {
+                                                   uint32_t &flags) {
     const uint32_t W[4] = {v.x, v.y, v.z, v.w};
-    flag = true;
+    flags = F_NONASCII;
     if (!edge && ((W[0] | W[1] | W[2] | W[3]) & 0x80808080u) == 0) {  // all ASCII
-      flag = false;
+      flags = 0;
       return 16;
     }
     uint32_t cnt = 0;
@@ -68,15 +94,15 @@ struct Utf8ToUtf16 {
   }
 
   // Validates the chunk and stages its UTF-16 words.  The lane's offset x0 (inside the
-  // region), the region total rtot and the region flag rflag (a byte >= 0x80 in the region,
-  // or a chunk at a buffer end) come from the count pass, so each pair of positions is
+  // region), the region total rtot and the region flags rflags (F_NONASCII: a byte >= 0x80
+  // in the region, or a chunk at a buffer end) come from the count pass, so each pair of positions is
   // decoded and stored in one pass without keeping decoded words in registers.
   __device__ __forceinline__ static Region convert(const Params &p, uint4 v, uint32_t prev,
                                                    uint32_t next, long long c, bool edge, bool inside,
                                                    uint16_t *st, uint32_t base, uint32_t x0, uint32_t rtot,
-                                                   bool rflag, unsigned long long &err_pos) {
+                                                   uint32_t rflags, unsigned long long &err_pos) {
     const int lane = threadIdx.x & 31;
-    if (!rflag) {
+    if (rflags == 0) {
       // an all-ASCII region: one word per byte; the only possible error is a leading byte
       // just before the region that wants continuation bytes inside it (lane 0's chunk)
       if (lane == 0) {

@@ -17,15 +17,22 @@
 //   struct Codec {
 //     using Out = uint8_t or uint16_t;                 // output code unit
 //     static constexpr uint32_t STAGE;                 // staged units per warp buffer
-//     __device__ static uint32_t count(const Params&, uint4 v, long long c, bool edge, bool& flag);
+//     static constexpr uint32_t REGION_UNITS, DIRECT_ALIGN;  // all-ASCII region output
+//     __device__ static uint32_t count(const Params&, uint4 v, long long c, bool edge,
+//                                      uint32_t& flags);
 //     __device__ static Region convert(const Params&, uint4 v, uint32_t prev, uint32_t next,
 //                                      long long c, bool edge, bool inside, Out* st,
-//                                      uint32_t base, uint32_t x0, uint32_t rtot, bool rflag,
+//                                      uint32_t base, uint32_t x0, uint32_t rtot, uint32_t rflags,
 //                                      unsigned long long& err_pos);
+//     __device__ static bool ascii_region(uint32_t rtot, uint32_t rflags);
+//     __device__ static void ascii_direct(const Params&, uint4 v, uint32_t prev, long long c,
+//                                         uint64_t S, unsigned long long& err_pos);
 //   };
 // count() returns the units one chunk contributes to its region (the total that converting
-// the region stages) and sets a codec-defined flag (the region's flag is the OR over its
-// lanes).  The count pass keeps, for every region, each lane's exclusive offset x0, the
+// the region stages) and sets codec-defined flag bits (the region's flags are the OR over its
+// lanes).  An all-ASCII region inside the buffer whose output starts on a 16-byte boundary
+// (DIRECT_ALIGN units) skips the staging: ascii_direct() stores each lane's units straight
+// to global memory.  The count pass keeps, for every region, each lane's exclusive offset x0, the
 // region total rtot and the flag, so convert() neither recounts nor rescans: it stages the
 // lane's units at base + x0 and returns the region's unit count and the units it writes past
 // its end or leaves to its predecessor at its start.  `inside` (uniform over the warp) says
@@ -93,8 +100,7 @@ __device__ __forceinline__ void count_partition(const Params &p, uint32_t part, 
     v[r] = load_chunk_hint(p, chunk_pos(part, warp, r, lane), inside, keep);
 #pragma unroll
   for (int r = 0; r < PART_ROUNDS; r += 2) {
-    uint32_t a[2];
-    bool f[2];
+    uint32_t a[2], f[2];
 #pragma unroll
     for (int q = 0; q < 2; ++q) {
       const long long c = chunk_pos(part, warp, r + q, lane);
@@ -102,24 +108,30 @@ __device__ __forceinline__ void count_partition(const Params &p, uint32_t part, 
       a[q] = Codec::count(p, v[r + q], c, edge, f[q]);
     }
     const uint32_t x = a[0] | (a[1] << 16);
-    uint32_t incl = x;
+    uint32_t incl;
+    const uint32_t x_first = __shfl_sync(0xffffffffu, x, 0);
+    if (__all_sync(0xffffffffu, x == x_first)) {
+      incl = x * (uint32_t)(lane + 1);  // equal counts (all-ASCII regions): no scan needed
+    } else {
+      incl = x;
 #pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-      const uint32_t y = __shfl_up_sync(0xffffffffu, incl, d);
-      if (lane >= d) incl += y;
+      for (int d = 1; d < 32; d <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, incl, d);
+        if (lane >= d) incl += y;
+      }
     }
     const uint32_t ex = incl - x;
     const int ri = warp * PART_ROUNDS + r;
     pc.lane_off[ri][lane] = (uint16_t)(ex & 0xFFFFu);
     pc.lane_off[ri + 1][lane] = (uint16_t)(ex >> 16);
-    const uint32_t fb = __ballot_sync(0xffffffffu, f[0]), fb1 = __ballot_sync(0xffffffffu, f[1]);
+    const uint32_t fr0 = __reduce_or_sync(0xffffffffu, f[0]), fr1 = __reduce_or_sync(0xffffffffu, f[1]);
     if (lane == 31) {
       pc.off[ri] = incl & 0xFFFFu;
       pc.off[ri + 1] = incl >> 16;
       pc.rtot[ri] = (uint16_t)(incl & 0xFFFFu);
       pc.rtot[ri + 1] = (uint16_t)(incl >> 16);
-      pc.flags[ri] = fb != 0;
-      pc.flags[ri + 1] = fb1 != 0;
+      pc.flags[ri] = (uint8_t)fr0;
+      pc.flags[ri + 1] = (uint8_t)fr1;
     }
   }
   __syncthreads();
@@ -197,11 +209,11 @@ template <class Codec>
 __device__ __forceinline__ Region convert_counted(const Params &p, uint4 v, uint32_t prev, uint32_t next,
                                                   long long c, bool edge, bool inside, typename Codec::Out *st,
                                                   uint32_t base, unsigned long long &err_pos) {
-  bool f;
+  uint32_t f;
   const uint32_t cnt = Codec::count(p, v, c, edge, f);
   uint32_t tot;
   const uint32_t x0 = warp_exclusive_scan(cnt, &tot);
-  const bool rf = __any_sync(0xffffffffu, f);
+  const uint32_t rf = __reduce_or_sync(0xffffffffu, f);
   return Codec::convert(p, v, prev, next, c, edge, inside, st, base, x0, tot, rf, err_pos);
 }
 
@@ -250,7 +262,7 @@ __device__ __forceinline__ void transcode(const Params &p, XSmem<Codec> &sm, Fin
     uint4 v_next = load_chunk_hint(p, s0 + CHUNK * lane, slice_inside, last_use);
     uint32_t prev_last = before;  // last word of the previous region (lane 31's), for lane 0
 #pragma unroll 1
-    for (int r = 0; r < PART_ROUNDS; ++r, ++use) {
+    for (int r = 0; r < PART_ROUNDS; ++r) {
       const long long c = s0 + (long long)r * REGION_BYTES + CHUNK * lane;
       const bool edge = c < lo || c + 16 > hi;
       const uint4 v = v_next;
@@ -262,20 +274,26 @@ __device__ __forceinline__ void transcode(const Params &p, XSmem<Codec> &sm, Fin
       if (lane == 31) next = r + 1 < PART_ROUNDS ? next_first : after;
       prev_last = __shfl_sync(0xffffffffu, v.w, 31);
 
-      typename Codec::Out *st = sm.staging[warp][use & 1];
       const PartCounts &pc = sm.counts[cb];
       const int ri = warp * PART_ROUNDS + r;
       const uint64_t S = S0 + pc.off[ri];
-      const uint32_t x0 = pc.lane_off[ri][lane];
       const uint32_t rtot = pc.rtot[ri];
-      const bool rflag = pc.flags[ri] != 0;
+      const uint32_t rflags = pc.flags[ri];
       const long long rc = s0 + (long long)r * REGION_BYTES;
       const bool rin = rc >= lo && rc + (long long)REGION_BYTES <= hi;  // uniform over the warp
+      if (rin && Codec::ascii_region(rtot, rflags) && ((p.dshift + S) & (Codec::DIRECT_ALIGN - 1)) == 0 &&
+          S + Codec::REGION_UNITS <= p.cap) {
+        Codec::ascii_direct(p, v, prev, c, S, err_pos);
+        continue;
+      }
+      typename Codec::Out *st = sm.staging[warp][use & 1];
+      ++use;
+      const uint32_t x0 = pc.lane_off[ri][lane];
       constexpr uint32_t V = 16 / sizeof(typename Codec::Out);
       const uint32_t h = (uint32_t)(p.dshift + S) & (V - 1);
       if (lane == 0) bulk_wait_read<1>();  // the store of two regions ago has read this buffer
       __syncwarp();
-      const Region g = Codec::convert(p, v, prev, next, c, edge, rin, st, h, x0, rtot, rflag, err_pos);
+      const Region g = Codec::convert(p, v, prev, next, c, edge, rin, st, h, x0, rtot, rflags, err_pos);
       fence_proxy_async_smem();
       __syncwarp();
       store_region(p, st, S, g.skip, g.total, g.extra);
