@@ -259,14 +259,17 @@ __device__ __forceinline__ void transcode(const Params &p, XSmem<Codec> &sm, Fin
     const uint32_t after =
         slice_inside ? ldg_word(p.base + s0 + SLICE_BYTES) : load_word_checked(p, s0 + SLICE_BYTES);
     const uint64_t last_use = l2_policy_last_use();
+    // two regions in flight ahead of the one being converted (the convert pass reads from L2)
     uint4 v_next = load_chunk_hint(p, s0 + CHUNK * lane, slice_inside, last_use);
+    uint4 v_next2 = load_chunk_hint(p, s0 + REGION_BYTES + CHUNK * lane, slice_inside, last_use);
     uint32_t prev_last = before;  // last word of the previous region (lane 31's), for lane 0
 #pragma unroll 1
     for (int r = 0; r < PART_ROUNDS; ++r) {
       const long long c = s0 + (long long)r * REGION_BYTES + CHUNK * lane;
       const bool edge = c < lo || c + 16 > hi;
       const uint4 v = v_next;
-      if (r + 1 < PART_ROUNDS) v_next = load_chunk_hint(p, c + REGION_BYTES, slice_inside, last_use);
+      v_next = v_next2;
+      if (r + 2 < PART_ROUNDS) v_next2 = load_chunk_hint(p, c + 2 * REGION_BYTES, slice_inside, last_use);
       uint32_t prev = __shfl_up_sync(0xffffffffu, v.w, 1);
       uint32_t next = __shfl_down_sync(0xffffffffu, v.x, 1);
       const uint32_t next_first = __shfl_sync(0xffffffffu, v_next.x, 0);  // next region's first word
