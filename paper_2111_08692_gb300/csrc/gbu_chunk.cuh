@@ -155,11 +155,82 @@ __device__ __forceinline__ uint32_t len8_of_word(uint32_t w) {
   return w < 0x80u ? 1u : (w < 0x800u ? 2u : ((w & 0xF800u) == 0xD800u ? 2u : 3u));
 }
 
+// ---- two UTF-16 words per 32-bit register ------------------------------------------------
+// Bit 15 of each 16-bit lane of the result is set where that word is >= 0x80, >= 0x800, a
+// surrogate (D800-DFFF), a first surrogate (D800-DBFF) or a second one (DC00-DFFF).  No
+// addition carries out of a lane (bit 15 is masked off first and the sums stay below 0x10000).
+__device__ __forceinline__ uint32_t lanes16_nonzero(uint32_t t) {
+  return (((t & 0x7FFF7FFFu) + 0x7FFF7FFFu) | t) & 0x80008000u;
+}
+__device__ __forceinline__ uint32_t lanes16_ge80(uint32_t X) {
+  return (((X & 0x7FFF7FFFu) + 0x7F807F80u) | X) & 0x80008000u;
+}
+__device__ __forceinline__ uint32_t lanes16_ge800(uint32_t X) {
+  return (((X & 0x7FFF7FFFu) + 0x78007800u) | X) & 0x80008000u;
+}
+__device__ __forceinline__ uint32_t lanes16_sur(uint32_t X) {
+  return ~lanes16_nonzero((X & 0xF800F800u) ^ 0xD800D800u) & 0x80008000u;
+}
+__device__ __forceinline__ uint32_t lanes16_high(uint32_t X) {
+  return ~lanes16_nonzero((X & 0xFC00FC00u) ^ 0xD800D800u) & 0x80008000u;
+}
+__device__ __forceinline__ uint32_t lanes16_low(uint32_t X) {
+  return ~lanes16_nonzero((X & 0xFC00FC00u) ^ 0xDC00DC00u) & 0x80008000u;
+}
+// Whether any of the 8 words is a surrogate (a test for "some lane is zero": exact as a
+// whole, although the per-lane bits it computes may not be).
+__device__ __forceinline__ bool any_surrogate16(const uint32_t W[4]) {
+  uint32_t z = 0;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const uint32_t t = (W[k] & 0xF800F800u) ^ 0xD800D800u;
+    z |= (t - 0x00010001u) & ~t;
+  }
+  return (z & 0x80008000u) != 0;
+}
+
+// UTF-8 bytes of the 8 words of a chunk inside the buffer: one per word, one more per word
+// >= 0x80 and one more per word >= 0x800, one less per surrogate (Section 3 sizes; a pair
+// counts 2 + 2).  The flags are summed by byte dot products (0x80 per flag, FMA pipe).
+__device__ __forceinline__ uint32_t utf16_len8_inside(const uint32_t W[4]) {
+  uint32_t acc = 0, sub = 0;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    acc = __dp4a(lanes16_ge80(W[k]), 0x01000100u, acc);
+    acc = __dp4a(lanes16_ge800(W[k]), 0x01000100u, acc);
+    sub = __dp4a(lanes16_sur(W[k]), 0x01000100u, sub);
+  }
+  return 8u + ((acc - sub) >> 7);
+}
+
+// Unpaired surrogates among the 8 words of a chunk inside the buffer, given the word before
+// (prevw's high half) and after (nextw's low half): a first surrogate whose next word is not
+// a second one, or a second surrogate whose previous word is not a first one.
+__device__ __forceinline__ bool utf16_pair_errors_inside(const uint32_t W[4], uint32_t prevw, uint32_t nextw) {
+  uint32_t H[5], L[5];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    H[k + 1] = lanes16_high(W[k]);
+    L[k] = lanes16_low(W[k]);
+  }
+  H[0] = lanes16_high(prevw);
+  L[4] = lanes16_low(nextw);
+  uint32_t err = 0;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const uint32_t low_after = __funnelshift_r(L[k], L[k + 1], 16);   // word i+1's flag at word i
+    const uint32_t high_before = __funnelshift_l(H[k], H[k + 1], 16);  // word i-1's flag at word i
+    err |= (H[k + 1] & ~low_after) | (L[k] & ~high_before);
+  }
+  return err != 0;
+}
+
 // Unpaired surrogates among the 8 words of a chunk, given the word before (prevw's high
 // half) and after (nextw's low half); words outside [lo, hi) are not judged.
 __device__ __forceinline__ bool utf16_chunk_errors(const uint32_t W[4], uint32_t prevw,
                                                    uint32_t nextw, long long c, bool edge,
                                                    long long lo, long long hi) {
+  if (!edge) return any_surrogate16(W) && utf16_pair_errors_inside(W, prevw, nextw);
   // fast exit: no surrogate word in the chunk, and the word before is not a first surrogate
   // followed by our first word (that one is judged by the chunk that owns it)
   const uint32_t any = (W[0] | W[1] | W[2] | W[3]);

@@ -34,20 +34,6 @@ struct Utf16ToUtf8 {
   // its end, 15 bytes of alignment offset
   static_assert(3 * 256 + 2 + 15 + 1 <= STAGE, "staging buffer too small");
 
-  // Bit 15 of each 16-bit lane of the result is set where that word is >= 0x80, >= 0x800, or
-  // a surrogate (D800-DFFF).  The additions cannot carry out of a lane (bit 15 is masked off
-  // first and the sum stays below 0x10000).
-  __device__ __forceinline__ static uint32_t lanes_ge80(uint32_t X) {
-    return (((X & 0x7FFF7FFFu) + 0x7F807F80u) | X) & 0x80008000u;
-  }
-  __device__ __forceinline__ static uint32_t lanes_ge800(uint32_t X) {
-    return (((X & 0x7FFF7FFFu) + 0x78007800u) | X) & 0x80008000u;
-  }
-  __device__ __forceinline__ static uint32_t lanes_sur(uint32_t X) {
-    const uint32_t s = (X & 0xF800F800u) ^ 0xD800D800u;  // a zero lane is a surrogate
-    return ~(((s & 0x7FFF7FFFu) + 0x7FFF7FFFu) | s) & 0x80008000u;
-  }
-
   // UTF-8 bytes of the 8 words of a chunk that lies wholly inside the buffer: one per word,
   // one more per word >= 0x80 and one more per word >= 0x800, one less per surrogate word
   // (Section 3 sizes; a pair counts 2 + 2).  The flags are summed with byte dot products
@@ -57,9 +43,9 @@ struct Utf16ToUtf8 {
     uint32_t acc = 0, sub = 0, sa = 0, g3 = 0;
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-      const uint32_t sr = lanes_sur(W[k]);
-      const uint32_t t = lanes_ge800(W[k]);
-      acc = __dp4a(lanes_ge80(W[k]), 0x01000100u, acc);
+      const uint32_t sr = lanes16_sur(W[k]);
+      const uint32_t t = lanes16_ge800(W[k]);
+      acc = __dp4a(lanes16_ge80(W[k]), 0x01000100u, acc);
       acc = __dp4a(t, 0x01000100u, acc);
       sub = __dp4a(sr, 0x01000100u, sub);
       sa |= sr;

@@ -76,11 +76,15 @@ __global__ void __launch_bounds__(STREAM_THREADS) stream_kernel(const Params p) 
         const uint32_t Wd[4] = {W[1], W[2], W[3], W[4]};
         if (MODE == S_L8) {
           uint32_t cnt = 0;
+          if (!edge) {
+            cnt = utf16_len8_inside(Wd);
+          } else {
 #pragma unroll
-          for (int j = 0; j < 8; ++j) {
-            const uint32_t w = (Wd[j >> 1] >> (16 * (j & 1))) & 0xFFFFu;
-            const bool valid = !edge || (c + 2 * j >= lo && c + 2 * j < hi);
-            cnt += valid ? len8_of_word(w) : 0u;
+            for (int j = 0; j < 8; ++j) {
+              const uint32_t w = (Wd[j >> 1] >> (16 * (j & 1))) & 0xFFFFu;
+              const bool valid = c + 2 * j >= lo && c + 2 * j < hi;
+              cnt += valid ? len8_of_word(w) : 0u;
+            }
           }
           total += cnt;
         } else if (utf16_chunk_errors(Wd, W[0], W[5], c, edge, lo, hi)) {
