@@ -143,7 +143,15 @@ __device__ __forceinline__ void region_read(const Params &sp, long long c, uint4
       total += utf8_count_units(f, c, edge, lo, hi);
     } else {
       uint32_t err = utf8_structure_errors(f);
-      err |= utf8_value_errors<false>(W, f, nullptr, nullptr);
+      uint32_t c2 = 0, c3 = 0, c4 = 0;
+#pragma unroll
+      for (int k = 1; k <= 4; ++k) {
+        c2 |= f[k].geC0 & ~f[k].geE0;
+        c3 |= f[k].geE0 & ~f[k].geF0;
+        c4 |= f[k].geF0;
+      }
+      err |= utf8_special_errors(W, __any_sync(0xffffffffu, c2 != 0), __any_sync(0xffffffffu, c3 != 0),
+                                 __any_sync(0xffffffffu, c4 != 0));
       if (err && (unsigned long long)c < err_pos) err_pos = (unsigned long long)c;
     }
   } else {

@@ -134,6 +134,40 @@ __device__ __forceinline__ uint32_t utf8_value_errors(const uint32_t W[6], const
   return bad;
 }
 
+// Bit 7 of each byte set where that byte is zero (exact per byte).
+__device__ __forceinline__ uint32_t zero_bytes(uint32_t t) {
+  return ~(((t & 0x7F7F7F7Fu) + 0x7F7F7F7Fu) | t) & 0x80808080u;
+}
+
+// Rules 4-6 (and rule 1 for F8-FF) for the 16 bytes W[1..4], with W[5] the word after, as
+// byte tests on whole words.  With the structure (rules 1-3) already checked, the value of a
+// sequence can only be out of range for these leading bytes and second bytes: C0 or C1
+// (overlong), E0 then 80-9F (overlong), ED then A0-BF (D800-DFFF), F0 then 80-8F (overlong),
+// F4 then 90-BF or F5-FF (above U+10FFFF; F8-FF also break rule 1).  Each test looks at a
+// byte and the byte after it (N = the stream shifted by one byte).  Nonzero = some position
+// of the chunk starts such a sequence (the caller only needs to know that the chunk holds an
+// error; the kind and offset are resolved separately).  has2/has3/has4: whether the warp has
+// two-, three-, four-byte leading bytes at all (absent classes cost nothing).
+__device__ __forceinline__ uint32_t utf8_special_errors(const uint32_t W[6], bool has2, bool has3, bool has4) {
+  uint32_t bad = 0;
+#pragma unroll
+  for (int k = 1; k <= 4; ++k) {
+    const uint32_t w = W[k];
+    const uint32_t n = __funnelshift_r(W[k], W[k + 1], 8);  // byte j: the byte after byte j
+    if (has2) bad |= zero_bytes((w & 0xFEFEFEFEu) ^ 0xC0C0C0C0u);
+    if (has3) {
+      bad |= zero_bytes((w ^ 0xE0E0E0E0u) | (n & 0x20202020u));
+      bad |= zero_bytes((w ^ 0xEDEDEDEDu) | (~n & 0x20202020u));
+    }
+    if (has4) {
+      bad |= zero_bytes((w ^ 0xF0F0F0F0u) | (n & 0x30303030u));
+      bad |= zero_bytes(w ^ 0xF4F4F4F4u) & ((n & 0x30303030u) + 0x70707070u);
+      bad |= ((w & 0x7F7F7F7Fu) + 0x0B0B0B0Bu) & w & 0x80808080u;  // F5-FF
+    }
+  }
+  return bad;
+}
+
 // UTF-16 words of the chunk's positions inside [lo, hi) (length formula: one per byte that is
 // not a continuation byte, one more per byte F0-FF).
 __device__ __forceinline__ uint32_t utf8_count_units(const Flags8 f[5], long long c, bool edge,

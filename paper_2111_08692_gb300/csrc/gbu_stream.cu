@@ -47,6 +47,24 @@ __global__ void __launch_bounds__(STREAM_THREADS) stream_kernel(const Params p) 
       pre = load_word_checked(p, t0 - 4);
       post = load_word_checked(p, t0 + WT_BYTES);
     }
+    if (MODE == S_V8 || MODE == S_L16) {
+      uint32_t any = 0;
+#pragma unroll
+      for (int r = 0; r < ST_ROUNDS; ++r) any |= v[r].x | v[r].y | v[r].z | v[r].w;
+      if (__all_sync(0xffffffffu, fast && (any & 0x80808080u) == 0)) {
+        // an all-ASCII warp tile: 16 units per chunk, and the only possible error is a
+        // leading byte just before the tile that wants continuation bytes in it (lane 0)
+        if (MODE == S_L16) {
+          total += 16 * ST_ROUNDS;
+        } else if (lane == 0) {
+          const Flags8 fp = classify8(pre);
+          const uint32_t req = __funnelshift_l(fp.geC0, 0u, 8) | __funnelshift_l(fp.geE0, 0u, 16) |
+                               __funnelshift_l(fp.geF0, 0u, 24);
+          if (req && (unsigned long long)t0 < err_pos) err_pos = (unsigned long long)t0;
+        }
+        continue;
+      }
+    }
 #pragma unroll
     for (int r = 0; r < ST_ROUNDS; ++r) {
       const long long c = t0 + 512 * r + 16 * lane;
@@ -69,7 +87,15 @@ __global__ void __launch_bounds__(STREAM_THREADS) stream_kernel(const Params p) 
           total += utf8_count_units(f, c, edge, lo, hi);
         } else {
           uint32_t err = utf8_structure_errors(f);
-          err |= utf8_value_errors<false>(W, f, nullptr, nullptr);
+          uint32_t c2 = 0, c3 = 0, c4 = 0;
+#pragma unroll
+          for (int k = 1; k <= 4; ++k) {
+            c2 |= f[k].geC0 & ~f[k].geE0;
+            c3 |= f[k].geE0 & ~f[k].geF0;
+            c4 |= f[k].geF0;
+          }
+          err |= utf8_special_errors(W, __any_sync(0xffffffffu, c2 != 0), __any_sync(0xffffffffu, c3 != 0),
+                                     __any_sync(0xffffffffu, c4 != 0));
           if (err && (unsigned long long)c < err_pos) err_pos = (unsigned long long)c;
         }
       } else {
