@@ -172,13 +172,16 @@ __device__ __forceinline__ uint32_t utf8_special_errors(const uint32_t W[6], boo
 // not a continuation byte, one more per byte F0-FF).
 __device__ __forceinline__ uint32_t utf8_count_units(const Flags8 f[5], long long c, bool edge,
                                                      long long lo, long long hi) {
-  uint32_t cnt = 0;
+  // flags sit in bit 7 of each byte: a byte dot product with 0x01 weights adds 0x80 per flag
+  // (FMA pipe, where a population count would take the slower XU pipe)
+  uint32_t acc = 0;
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
     const uint32_t vm = edge ? byte_range_mask(c + 4 * k, lo, hi) : 0x80808080u;
-    cnt += __popc(~f[k + 1].isC & vm) + __popc(f[k + 1].geF0 & vm);
+    acc = __dp4a(~f[k + 1].isC & vm, 0x01010101u, acc);
+    acc = __dp4a(f[k + 1].geF0 & vm, 0x01010101u, acc);
   }
-  return cnt;
+  return acc >> 7;
 }
 
 __device__ __forceinline__ bool is_high16(uint32_t w) { return (w & 0xFC00u) == 0xD800u; }
