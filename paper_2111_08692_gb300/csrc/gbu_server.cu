@@ -14,8 +14,8 @@
 //      operation go together into ONE batched launch over device descriptors (warp per
 //      string, CTA per longer string); requests of at least large_bytes each get a
 //      single-buffer launch (all SMs on one string), several per group.  A group is: the
-//      descriptors copied host -> device, the launches, the results copied device -> host,
-//      an event.  Groups are spread round-robin over several streams, so work admitted while
+//      launches and an event; descriptors and results stay in mapped pinned host memory,
+//      which the kernels read and write directly.  Groups are spread round-robin over several streams, so work admitted while
 //      earlier groups run overlaps with them on the device.
 // Requests that arrive while the GPU is busy wait only for a free slot and memory, not for
 // the earlier groups to finish: that is the continuous batching.  Latency = completion
@@ -133,10 +133,10 @@ struct Slot {
   cudaStream_t stream;
   cudaEvent_t done;
   gbu_ctx *ctx;
-  gbu::StringDesc *desc_h;  // pinned
-  gbu_result *res_h;        // pinned
-  gbu::StringDesc *desc_d;
-  gbu_result *res_d;
+  gbu::StringDesc *desc_h;  // pinned, mapped
+  gbu_result *res_h;        // pinned, mapped
+  gbu::StringDesc *desc_d;  // the device's address of desc_h
+  gbu_result *res_d;        // the device's address of res_h
   std::vector<Req> reqs;
   bool busy;
 };
@@ -152,6 +152,7 @@ struct gbu_server {
   std::vector<gbu_ctx *> ctxs;  // one per stream
   std::vector<cudaStream_t> streams;
   std::vector<Slot> slots;
+  std::vector<std::deque<int>> issued;  // per stream: busy slots in issue order
   int next_stream;
 
   std::mutex mu;                       // guards everything below (and arena)
@@ -196,27 +197,33 @@ void complete_locked(gbu_server *s, const Req &q, const gbu_result &res, uint64_
   s->stats.completed++;
 }
 
-// Step 1: retire finished groups.
+// Step 1: retire finished groups.  Groups on one stream finish in issue order, so only the
+// oldest busy group of each stream is queried (one event query per stream per pass).
 bool retire(gbu_server *s) {
   bool any = false;
-  for (Slot &sl : s->slots) {
-    if (!sl.busy) continue;
-    const cudaError_t e = cudaEventQuery(sl.done);
-    if (e == cudaErrorNotReady) continue;
-    const uint64_t now = server_now(s);
-    std::lock_guard<std::mutex> lk(s->mu);
-    for (size_t k = 0; k < sl.reqs.size(); ++k) {
-      const Req &q = sl.reqs[k];
-      gbu_result r = sl.res_h[k];
-      if (e != cudaSuccess) r = gbu_result{GBU_CUDA_ERROR, 0, 0};
-      s->budget_used -= q.r.n * in_unit(q.r.op);
-      s->inflight--;
-      complete_locked(s, q, r, now);
+  for (std::deque<int> &q_issued : s->issued) {
+    while (!q_issued.empty()) {
+      Slot &sl = s->slots[q_issued.front()];
+      const cudaError_t e = cudaEventQuery(sl.done);
+      if (e == cudaErrorNotReady) break;
+      const uint64_t now = server_now(s);
+      {
+        std::lock_guard<std::mutex> lk(s->mu);
+        for (size_t k = 0; k < sl.reqs.size(); ++k) {
+          const Req &q = sl.reqs[k];
+          gbu_result r = sl.res_h[k];
+          if (e != cudaSuccess) r = gbu_result{GBU_CUDA_ERROR, 0, 0};
+          s->budget_used -= q.r.n * in_unit(q.r.op);
+          s->inflight--;
+          complete_locked(s, q, r, now);
+        }
+      }
+      if (e != cudaSuccess) cudaGetLastError();
+      sl.reqs.clear();
+      sl.busy = false;
+      q_issued.pop_front();
+      any = true;
     }
-    if (e != cudaSuccess) cudaGetLastError();
-    sl.reqs.clear();
-    sl.busy = false;
-    any = true;
   }
   return any;
 }
@@ -305,15 +312,11 @@ void launch_group(gbu_server *s, Slot &sl, bool large) {
       sl.desc_h[k].dst = q.out_off != ~0ull ? (void *)(s->arena_base + q.out_off) : nullptr;
       sl.desc_h[k].cap = out_bytes(op, q.r.n) ? out_cap(op, q.r.n) : 0;
     }
-    if (cudaMemcpyAsync(sl.desc_d, sl.desc_h, B * sizeof(gbu::StringDesc), cudaMemcpyHostToDevice, sl.stream) !=
-        cudaSuccess)
-      rc = GBU_CUDA_ERROR;
-    if (rc == GBU_OK) rc = gbu_internal_batch_desc(sl.ctx, op, sl.desc_d, B, sl.res_d, sl.stream);
+    // the descriptors and results live in mapped pinned host memory: the kernel reads and
+    // writes them there, so a group costs its launches and one event, no copies
+    rc = gbu_internal_batch_desc(sl.ctx, op, sl.desc_d, B, sl.res_d, sl.stream);
     s->stats.launches++;
   }
-  if (rc == GBU_OK &&
-      cudaMemcpyAsync(sl.res_h, sl.res_d, B * sizeof(gbu_result), cudaMemcpyDeviceToHost, sl.stream) != cudaSuccess)
-    rc = GBU_CUDA_ERROR;
   if (rc != GBU_OK) {
     // results of a group that could not be enqueued: report the failure, keep the slot usable
     cudaGetLastError();
@@ -321,6 +324,7 @@ void launch_group(gbu_server *s, Slot &sl, bool large) {
   }
   cudaEventRecord(sl.done, sl.stream);
   sl.busy = true;
+  s->issued[(&sl - s->slots.data()) / s->cfg.groups_per_stream].push_back((int)(&sl - s->slots.data()));
   s->stats.groups++;
 }
 
@@ -376,8 +380,6 @@ void destroy_resources(gbu_server *s) {
     if (sl.done) cudaEventDestroy(sl.done);
     if (sl.desc_h) cudaFreeHost(sl.desc_h);
     if (sl.res_h) cudaFreeHost(sl.res_h);
-    if (sl.desc_d) cudaFree(sl.desc_d);
-    if (sl.res_d) cudaFree(sl.res_d);
   }
   for (gbu_ctx *c : s->ctxs) gbu_destroy(c);
   for (cudaStream_t st : s->streams) cudaStreamDestroy(st);
@@ -434,6 +436,7 @@ extern "C" gbu_server *gbu_server_create(int device, const gbu_server_config *cf
   }
   const uint32_t G = cfg.max_group > cfg.max_large_group ? cfg.max_group : cfg.max_large_group;
   s->slots.resize(ok ? (size_t)cfg.streams * cfg.groups_per_stream : 0);
+  s->issued.resize(ok ? (size_t)cfg.streams : 0);
   for (size_t i = 0; ok && i < s->slots.size(); ++i) {
     Slot &sl = s->slots[i];
     sl.done = nullptr;
@@ -445,10 +448,10 @@ extern "C" gbu_server *gbu_server_create(int device, const gbu_server_config *cf
     sl.ctx = s->ctxs[i / cfg.groups_per_stream];
     sl.busy = false;
     ok = cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming) == cudaSuccess &&
-         cudaMallocHost(&sl.desc_h, G * sizeof(gbu::StringDesc)) == cudaSuccess &&
-         cudaMallocHost(&sl.res_h, G * sizeof(gbu_result)) == cudaSuccess &&
-         cudaMalloc(&sl.desc_d, G * sizeof(gbu::StringDesc)) == cudaSuccess &&
-         cudaMalloc(&sl.res_d, G * sizeof(gbu_result)) == cudaSuccess;
+         cudaHostAlloc(&sl.desc_h, G * sizeof(gbu::StringDesc), cudaHostAllocMapped) == cudaSuccess &&
+         cudaHostAlloc(&sl.res_h, G * sizeof(gbu_result), cudaHostAllocMapped) == cudaSuccess &&
+         cudaHostGetDevicePointer((void **)&sl.desc_d, sl.desc_h, 0) == cudaSuccess &&
+         cudaHostGetDevicePointer((void **)&sl.res_d, sl.res_h, 0) == cudaSuccess;
   }
   if (!ok) {
     cudaGetLastError();
