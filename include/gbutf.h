@@ -208,8 +208,10 @@ void gbu_graph_destroy(gbu_graph *graph);
  * (server clock, gbu_server_now_ns) has passed, while an in-flight slot is free and the
  * device-memory budget covers the inputs and worst-case outputs of everything admitted;
  * outputs come from a device arena of budget_bytes allocated at creation.  Admitted small
- * requests of one operation share ONE batched launch (device descriptors); requests of at
- * least large_bytes get single-buffer launches.  Launch groups are spread over `streams`
+ * requests of one operation share ONE batched launch (device descriptors); transcodings of
+ * at least large_bytes of one direction share one partitioned launch (each request split into
+ * 64 KiB partitions with its own look-back chain, so all SMs work on the group); large
+ * validations get single-buffer launches.  Launch groups are spread over `streams`
  * CUDA streams, `groups_per_stream` in flight on each, so newly admitted work overlaps with
  * running work.  Each request's result is the one the single-buffer call gives on it.
  * Request inputs are DEVICE buffers that must stay valid until the request completes.
@@ -220,7 +222,7 @@ typedef struct {
   int32_t streams;            /* CUDA streams (default 16)                                  */
   int32_t groups_per_stream;  /* launch groups in flight per stream (default 8)             */
   uint32_t max_group;         /* small requests per batched launch (default 4096)           */
-  uint32_t max_large_group;   /* single-buffer launches per group (default 2)               */
+  uint32_t max_large_group;   /* large transcodings per launch (default 32)                 */
   uint64_t large_bytes;       /* input bytes from which a request runs alone (default 64 KiB) */
   uint64_t max_request_units; /* largest request accepted, code units (default 16 Mi)       */
   uint32_t max_inflight;      /* admitted, not yet completed requests (default 65536)       */

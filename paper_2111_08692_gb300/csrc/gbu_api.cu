@@ -65,6 +65,7 @@ struct gbu_ctx {
   int blocks_per_sm[K_COUNT];
   int batch_blocks_per_sm[K_COUNT][3];  // per batched mode and warps per CTA (4, 8, 16)
   int scan_blocks_per_sm;
+  int seg_blocks_per_sm[2];             // several-string transcoders: 8 -> 16, 16 -> 8
   gbu_batch_config batch_cfg[K_COUNT];  // launch geometry of the batched kernels
   std::atomic<uint64_t> launches;
   uint64_t capture_start;               // launches when the current graph capture began
@@ -144,6 +145,14 @@ extern "C" gbu_ctx *gbu_create(int device, uint64_t max_units) {
   occ_ok = occ_ok && cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c->scan_blocks_per_sm, gbu::scan_kernel_ptr(),
                                                                    gbu::scan_threads(), 0) == cudaSuccess &&
            c->scan_blocks_per_sm >= 1;
+  for (int d = 0; d < 2 && occ_ok; ++d) {
+    const void *f = d == 0 ? gbu::utf8_to_utf16_segments_kernel_ptr() : gbu::utf16_to_utf8_segments_kernel_ptr();
+    const size_t smem = d == 0 ? gbu::utf8_to_utf16_smem_bytes() : gbu::utf16_to_utf8_smem_bytes();
+    occ_ok = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) == cudaSuccess &&
+             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c->seg_blocks_per_sm[d], f, gbu::XT, smem) ==
+                 cudaSuccess &&
+             c->seg_blocks_per_sm[d] >= 1;
+  }
   if (!occ_ok) {
     cudaFree(c->states);
     cudaFree(c->ws);
@@ -589,4 +598,46 @@ int gbu_internal_batch_desc(gbu_ctx *c, int op, const gbu::StringDesc *desc, uin
   if (B > 0 && (!desc || !results)) return GBU_BAD_ARGUMENT;
   return batch_launch(c, op, c->batch_cfg[op], nullptr, nullptr, B, nullptr, nullptr, results, nullptr, stream,
                       desc);
+}
+
+int gbu_internal_partitions(int op, const void *src, uint64_t n) {
+  const uint64_t in_unit = op == GBU_OP_CONVERT_UTF16LE_TO_UTF8 ? 2 : 1;
+  const uint64_t tail = op == GBU_OP_CONVERT_UTF8_TO_UTF16LE ? 3 : 0;  // positions judged past the end
+  const uint64_t span = ((uintptr_t)src & 15) + n * in_unit + tail;
+  return (int)((span + gbu::PART_BYTES - 1) / gbu::PART_BYTES);
+}
+
+int gbu_internal_convert_segments(gbu_ctx *c, int op, const gbu::StringDesc *desc, const uint32_t *pstart,
+                                  uint32_t B, uint32_t ntiles, gbu::SegState *seg, gbu_result *results,
+                                  gbu_stream stream) {
+  if (!c || (op != K_C8 && op != K_C16)) return GBU_BAD_ARGUMENT;
+  if (B == 0 || ntiles == 0) return GBU_OK;
+  if (!desc || !pstart || !seg || !results || ntiles > c->max_states) return GBU_BAD_ARGUMENT;
+  gbu::SegParams q;
+  memset(&q, 0, sizeof(q));
+  q.desc = desc;
+  q.pstart = pstart;
+  q.B = B;
+  q.ntiles = ntiles;
+  q.seg = seg;
+  q.results = results;
+  q.ws = c->ws;
+  q.states = c->states;
+  q.max_states = c->max_states;
+  q.wait_limit = c->wait_limit;
+  const int d = op == K_C8 ? 0 : 1;
+  DeviceGuard g(c->device);
+  uint64_t grid = (uint64_t)c->num_sms * (uint64_t)c->seg_blocks_per_sm[d];
+  if (ntiles < grid) grid = ntiles;
+  void *args[] = {(void *)&q};
+  cudaError_t e = cudaLaunchKernel(
+      d == 0 ? gbu::utf8_to_utf16_segments_kernel_ptr() : gbu::utf16_to_utf8_segments_kernel_ptr(), dim3((unsigned)grid),
+      dim3(gbu::XT), args, d == 0 ? gbu::utf8_to_utf16_smem_bytes() : gbu::utf16_to_utf8_smem_bytes(),
+      (cudaStream_t)stream);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return GBU_CUDA_ERROR;
+  }
+  c->launches.fetch_add(1);
+  return GBU_OK;
 }

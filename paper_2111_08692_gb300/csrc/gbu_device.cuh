@@ -100,6 +100,28 @@ struct BatchParams {
   uint32_t long_bytes;       // strings of at least this many input bytes go to a whole CTA
 };
 
+// Several strings transcoded by one launch, each split into partitions with its own look-back
+// chain (gbu_xcode.cuh, transcode_segments).
+struct SegState {            // per string; starts {NO_ERROR, 0, 0}, left so by the launch
+  unsigned long long errkey; // smallest erroring chunk start of the string
+  unsigned long long total;  // output units (set by the CTA of the string's last partition)
+  uint32_t done;             // partitions finished
+  uint32_t pad;
+};
+
+struct SegParams {
+  const StringDesc *desc;    // B strings, each n >= 1
+  const uint32_t *pstart;    // B+1: first partition of each string in the launch's numbering
+  uint32_t B;
+  uint32_t ntiles;           // pstart[B]
+  SegState *seg;             // B entries
+  gbu_result *results;       // B results
+  WsHeader *ws;              // claim counter, completion counter, epoch, timeout flag
+  uint64_t *states;          // ntiles look-back states (pstart[s] onwards for string s)
+  uint32_t max_states;
+  uint32_t wait_limit;
+};
+
 struct ScanParams {
   const uint64_t *in;
   uint64_t *out;             // count + 1 entries

@@ -17,6 +17,9 @@ const void *utf8_to_utf16_kernel_ptr();
 const void *utf16_to_utf8_kernel_ptr();
 size_t utf8_to_utf16_smem_bytes();
 size_t utf16_to_utf8_smem_bytes();
+// the same transcoders over several strings per launch (SegParams; same shared memory)
+const void *utf8_to_utf16_segments_kernel_ptr();
+const void *utf16_to_utf8_segments_kernel_ptr();
 
 // batched kernels (mode: BatchMode; nwarps: 4, 8 or 16 warps per CTA) and the u64 scan
 const void *batch_kernel_ptr(int mode, int nwarps);

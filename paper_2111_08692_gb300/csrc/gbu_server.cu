@@ -137,6 +137,9 @@ struct Slot {
   gbu_result *res_h;        // pinned, mapped
   gbu::StringDesc *desc_d;  // the device's address of desc_h
   gbu_result *res_d;        // the device's address of res_h
+  uint32_t *pstart_h;       // pinned, mapped: first launch partition of each large request
+  uint32_t *pstart_d;
+  gbu::SegState *seg_d;     // device: per-request error minimum / length / partitions done
   std::vector<Req> reqs;
   bool busy;
 };
@@ -285,7 +288,25 @@ Slot *free_slot(gbu_server *s) {
 void launch_group(gbu_server *s, Slot &sl, bool large) {
   const size_t B = sl.reqs.size();
   int rc = GBU_OK;
-  if (large) {
+  const int op0 = sl.reqs[0].r.op;
+  if (large && (op0 == GBU_OP_CONVERT_UTF8_TO_UTF16LE || op0 == GBU_OP_CONVERT_UTF16LE_TO_UTF8)) {
+    // large transcodings of one direction: one launch over all their partitions, each
+    // request with its own look-back chain
+    uint32_t ntiles = 0;
+    for (size_t k = 0; k < B; ++k) {
+      const Req &q = sl.reqs[k];
+      sl.desc_h[k].src = q.r.src;
+      sl.desc_h[k].n = q.r.n;
+      sl.desc_h[k].dst = (void *)(s->arena_base + q.out_off);
+      sl.desc_h[k].cap = out_cap(op0, q.r.n);
+      sl.pstart_h[k] = ntiles;
+      ntiles += (uint32_t)gbu_internal_partitions(op0, q.r.src, q.r.n);
+    }
+    sl.pstart_h[B] = ntiles;
+    rc = gbu_internal_convert_segments(sl.ctx, op0, sl.desc_d, sl.pstart_d, (uint32_t)B, ntiles, sl.seg_d, sl.res_d,
+                                       sl.stream);
+    s->stats.launches++;
+  } else if (large) {
     for (size_t k = 0; k < B && rc == GBU_OK; ++k) {
       const Req &q = sl.reqs[k];
       const int op = q.r.op;
@@ -336,10 +357,17 @@ bool dispatch(gbu_server *s, std::deque<Req> &small_q, std::deque<Req> &large_q)
     Slot *sl = free_slot(s);
     if (!sl) break;
     if (!large_q.empty()) {
-      const uint32_t lim = s->cfg.max_large_group;
-      while (!large_q.empty() && sl->reqs.size() < lim) {
-        sl->reqs.push_back(large_q.front());
-        large_q.pop_front();
+      // transcodings of the head's direction share one launch; validations run two per group
+      const int op = large_q.front().r.op;
+      const bool conv = op == GBU_OP_CONVERT_UTF8_TO_UTF16LE || op == GBU_OP_CONVERT_UTF16LE_TO_UTF8;
+      const uint32_t lim = conv ? s->cfg.max_large_group : 2u;
+      for (auto it = large_q.begin(); it != large_q.end() && sl->reqs.size() < lim;) {
+        if (it->r.op == op) {
+          sl->reqs.push_back(*it);
+          it = large_q.erase(it);
+        } else {
+          ++it;
+        }
       }
       launch_group(s, *sl, true);
     } else {
@@ -380,6 +408,8 @@ void destroy_resources(gbu_server *s) {
     if (sl.done) cudaEventDestroy(sl.done);
     if (sl.desc_h) cudaFreeHost(sl.desc_h);
     if (sl.res_h) cudaFreeHost(sl.res_h);
+    if (sl.pstart_h) cudaFreeHost(sl.pstart_h);
+    if (sl.seg_d) cudaFree(sl.seg_d);
   }
   for (gbu_ctx *c : s->ctxs) gbu_destroy(c);
   for (cudaStream_t st : s->streams) cudaStreamDestroy(st);
@@ -392,12 +422,12 @@ extern "C" void gbu_server_default_config(gbu_server_config *cfg) {
   if (!cfg) return;
   memset(cfg, 0, sizeof(*cfg));
   cfg->budget_bytes = 8ull << 30;
-  // 16 streams x 8 groups x 2 single-buffer launches per group: the best of a sweep on GB300
-  // (enough launches in flight that mid-sized requests, a few partitions each, fill the SMs)
+  // 16 streams x 8 groups in flight; large transcodings of one direction share a launch (up
+  // to 32 requests), large validations run two per group
   cfg->streams = 16;
   cfg->groups_per_stream = 8;
   cfg->max_group = 4096;
-  cfg->max_large_group = 2;
+  cfg->max_large_group = 32;
   cfg->large_bytes = 64 << 10;
   cfg->max_request_units = 16ull << 20;
   cfg->max_inflight = 1u << 16;
@@ -430,7 +460,8 @@ extern "C" gbu_server *gbu_server_create(int device, const gbu_server_config *cf
     ok = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) == cudaSuccess;
     if (!ok) break;
     s->streams.push_back(st);
-    gbu_ctx *c = gbu_create(device, 2 * cfg.max_request_units + 64);
+    // look-back states for a whole group of large requests (max_large_group x the largest)
+    gbu_ctx *c = gbu_create(device, (uint64_t)cfg.max_large_group * (cfg.max_request_units + 2 * gbu::PART_BYTES));
     ok = c != nullptr;
     if (ok) s->ctxs.push_back(c);
   }
@@ -444,6 +475,9 @@ extern "C" gbu_server *gbu_server_create(int device, const gbu_server_config *cf
     sl.res_h = nullptr;
     sl.desc_d = nullptr;
     sl.res_d = nullptr;
+    sl.pstart_h = nullptr;
+    sl.pstart_d = nullptr;
+    sl.seg_d = nullptr;
     sl.stream = s->streams[i / cfg.groups_per_stream];
     sl.ctx = s->ctxs[i / cfg.groups_per_stream];
     sl.busy = false;
@@ -451,7 +485,15 @@ extern "C" gbu_server *gbu_server_create(int device, const gbu_server_config *cf
          cudaHostAlloc(&sl.desc_h, G * sizeof(gbu::StringDesc), cudaHostAllocMapped) == cudaSuccess &&
          cudaHostAlloc(&sl.res_h, G * sizeof(gbu_result), cudaHostAllocMapped) == cudaSuccess &&
          cudaHostGetDevicePointer((void **)&sl.desc_d, sl.desc_h, 0) == cudaSuccess &&
-         cudaHostGetDevicePointer((void **)&sl.res_d, sl.res_h, 0) == cudaSuccess;
+         cudaHostGetDevicePointer((void **)&sl.res_d, sl.res_h, 0) == cudaSuccess &&
+         cudaHostAlloc(&sl.pstart_h, (G + 1) * sizeof(uint32_t), cudaHostAllocMapped) == cudaSuccess &&
+         cudaHostGetDevicePointer((void **)&sl.pstart_d, sl.pstart_h, 0) == cudaSuccess &&
+         cudaMalloc(&sl.seg_d, G * sizeof(gbu::SegState)) == cudaSuccess;
+    if (ok) {  // per-request states start {no error, 0, 0}
+      std::vector<gbu::SegState> init(G);
+      for (auto &e : init) e = gbu::SegState{gbu::NO_ERROR, 0ull, 0u, 0u};
+      ok = cudaMemcpy(sl.seg_d, init.data(), G * sizeof(gbu::SegState), cudaMemcpyHostToDevice) == cudaSuccess;
+    }
   }
   if (!ok) {
     cudaGetLastError();

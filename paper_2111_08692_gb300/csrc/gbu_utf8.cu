@@ -24,7 +24,30 @@ __global__ void __launch_bounds__(XT, 2) utf8_to_utf16_kernel(const Params p) {
   });
 }
 
+// Several strings per launch (the serving loop's large requests): one result per string.
+__global__ void __launch_bounds__(XT, 2) utf8_to_utf16_segments_kernel(const SegParams q) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];  // sizeof(XSmem), set at launch
+  XSmem<Utf8ToUtf16> &sm = *reinterpret_cast<XSmem<Utf8ToUtf16> *>(smem_raw);
+  transcode_segments<Utf8ToUtf16>(q, sm, [&](const Params &p, const SegState &st, uint32_t) {
+    const uint32_t status = *(volatile uint32_t *)&p.ws->status;
+    const unsigned long long key = *(volatile const unsigned long long *)&st.errkey;
+    const unsigned long long tot = *(volatile const unsigned long long *)&st.total;
+    if (status) {
+      write_result(p.result, GBU_TIMEOUT, 0);
+    } else if (key != NO_ERROR) {
+      int32_t kind;
+      uint64_t off;
+      resolve_utf8_error(p.base + p.off0, p.n, (long long)key - (long long)p.off0, &kind, &off);
+      write_result(p.result, kind, off);
+    } else {
+      write_result(p.result, tot > p.cap ? GBU_OUTPUT_TOO_SMALL : GBU_OK, tot);
+    }
+  });
+}
+
 const void *utf8_to_utf16_kernel_ptr() { return (const void *)utf8_to_utf16_kernel; }
 size_t utf8_to_utf16_smem_bytes() { return sizeof(XSmem<Utf8ToUtf16>); }
+
+const void *utf8_to_utf16_segments_kernel_ptr() { return (const void *)utf8_to_utf16_segments_kernel; }
 
 }  // namespace gbu

@@ -75,6 +75,8 @@ struct __align__(128) XSmem {
   unsigned long long red[XWARPS];
   uint32_t ticket;
   int is_last;
+  Params prm[2];   // several-string launches: the string of counts[0] / counts[1]
+  uint32_t sid[2];
 };
 
 // Virtual position of lane `lane`'s chunk in region r of warp w's slice of partition part.
@@ -219,6 +221,64 @@ __device__ __forceinline__ Region convert_counted(const Params &p, uint4 v, uint
 
 // The whole transcoder kernel body.  finalize(status, key, total) runs in thread 0 of the
 // last CTA and writes the result.
+// Step 3 for partition `part` of the buffer that p describes (all threads; each warp on its
+// slice): transcodes the partition, whose output starts at unit S0, with the region offsets,
+// lane offsets and flags of its count pass in pc.
+template <class Codec>
+__device__ __forceinline__ void convert_partition(const Params &p, uint32_t part, const PartCounts &pc, uint64_t S0,
+                                                  XSmem<Codec> &sm, uint32_t &use, unsigned long long &err_pos) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const long long lo = p.off0, hi = (long long)p.vbytes;
+  // this warp's slice: the words just before and after it, and its first chunk
+  const long long s0 = chunk_pos(part, warp, 0, 0);
+  const bool slice_inside = s0 - 4 >= lo && s0 + (long long)SLICE_BYTES + 4 <= hi;
+  const uint32_t before = slice_inside ? ldg_word(p.base + s0 - 4) : load_word_checked(p, s0 - 4);
+  const uint32_t after =
+      slice_inside ? ldg_word(p.base + s0 + SLICE_BYTES) : load_word_checked(p, s0 + SLICE_BYTES);
+  const uint64_t last_use = l2_policy_last_use();
+  // two regions in flight ahead of the one being converted (the convert pass reads from L2)
+  uint4 v_next = load_chunk_hint(p, s0 + CHUNK * lane, slice_inside, last_use);
+  uint4 v_next2 = load_chunk_hint(p, s0 + REGION_BYTES + CHUNK * lane, slice_inside, last_use);
+  uint32_t prev_last = before;  // last word of the previous region (lane 31's), for lane 0
+#pragma unroll 1
+  for (int r = 0; r < PART_ROUNDS; ++r) {
+    const long long c = s0 + (long long)r * REGION_BYTES + CHUNK * lane;
+    const bool edge = c < lo || c + 16 > hi;
+    const uint4 v = v_next;
+    v_next = v_next2;
+    if (r + 2 < PART_ROUNDS) v_next2 = load_chunk_hint(p, c + 2 * REGION_BYTES, slice_inside, last_use);
+    uint32_t prev = __shfl_up_sync(0xffffffffu, v.w, 1);
+    uint32_t next = __shfl_down_sync(0xffffffffu, v.x, 1);
+    const uint32_t next_first = __shfl_sync(0xffffffffu, v_next.x, 0);  // next region's first word
+    if (lane == 0) prev = prev_last;
+    if (lane == 31) next = r + 1 < PART_ROUNDS ? next_first : after;
+    prev_last = __shfl_sync(0xffffffffu, v.w, 31);
+
+    const int ri = warp * PART_ROUNDS + r;
+    const uint64_t S = S0 + pc.off[ri];
+    const uint32_t rtot = pc.rtot[ri];
+    const uint32_t rflags = pc.flags[ri];
+    const long long rc = s0 + (long long)r * REGION_BYTES;
+    const bool rin = rc >= lo && rc + (long long)REGION_BYTES <= hi;  // uniform over the warp
+    if (rin && Codec::ascii_region(rtot, rflags) && ((p.dshift + S) & (Codec::DIRECT_ALIGN - 1)) == 0 &&
+        S + Codec::REGION_UNITS <= p.cap) {
+      Codec::ascii_direct(p, v, prev, c, S, err_pos);
+      continue;
+    }
+    typename Codec::Out *st = sm.staging[warp][use & 1];
+    ++use;
+    const uint32_t x0 = pc.lane_off[ri][lane];
+    constexpr uint32_t V = 16 / sizeof(typename Codec::Out);
+    const uint32_t h = (uint32_t)(p.dshift + S) & (V - 1);
+    if (lane == 0) bulk_wait_read<1>();  // the store of two regions ago has read this buffer
+    __syncwarp();
+    const Region g = Codec::convert(p, v, prev, next, c, edge, rin, st, h, x0, rtot, rflags, err_pos);
+    fence_proxy_async_smem();
+    __syncwarp();
+    store_region(p, st, S, g.skip, g.total, g.extra);
+  }
+}
+
 template <class Codec, class Final>
 __device__ __forceinline__ void transcode(const Params &p, XSmem<Codec> &sm, Final finalize) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -252,55 +312,7 @@ __device__ __forceinline__ void transcode(const Params &p, XSmem<Codec> &sm, Fin
     }
     const uint64_t S0 = lookback_cta<XT>(p, cur, sm.counts[cb].total, epoch, sm.scratch, sm.sums);
 
-    // this warp's slice: the words just before and after it, and its first chunk
-    const long long s0 = chunk_pos(cur, warp, 0, 0);
-    const bool slice_inside = s0 - 4 >= lo && s0 + (long long)SLICE_BYTES + 4 <= hi;
-    const uint32_t before = slice_inside ? ldg_word(p.base + s0 - 4) : load_word_checked(p, s0 - 4);
-    const uint32_t after =
-        slice_inside ? ldg_word(p.base + s0 + SLICE_BYTES) : load_word_checked(p, s0 + SLICE_BYTES);
-    const uint64_t last_use = l2_policy_last_use();
-    // two regions in flight ahead of the one being converted (the convert pass reads from L2)
-    uint4 v_next = load_chunk_hint(p, s0 + CHUNK * lane, slice_inside, last_use);
-    uint4 v_next2 = load_chunk_hint(p, s0 + REGION_BYTES + CHUNK * lane, slice_inside, last_use);
-    uint32_t prev_last = before;  // last word of the previous region (lane 31's), for lane 0
-#pragma unroll 1
-    for (int r = 0; r < PART_ROUNDS; ++r) {
-      const long long c = s0 + (long long)r * REGION_BYTES + CHUNK * lane;
-      const bool edge = c < lo || c + 16 > hi;
-      const uint4 v = v_next;
-      v_next = v_next2;
-      if (r + 2 < PART_ROUNDS) v_next2 = load_chunk_hint(p, c + 2 * REGION_BYTES, slice_inside, last_use);
-      uint32_t prev = __shfl_up_sync(0xffffffffu, v.w, 1);
-      uint32_t next = __shfl_down_sync(0xffffffffu, v.x, 1);
-      const uint32_t next_first = __shfl_sync(0xffffffffu, v_next.x, 0);  // next region's first word
-      if (lane == 0) prev = prev_last;
-      if (lane == 31) next = r + 1 < PART_ROUNDS ? next_first : after;
-      prev_last = __shfl_sync(0xffffffffu, v.w, 31);
-
-      const PartCounts &pc = sm.counts[cb];
-      const int ri = warp * PART_ROUNDS + r;
-      const uint64_t S = S0 + pc.off[ri];
-      const uint32_t rtot = pc.rtot[ri];
-      const uint32_t rflags = pc.flags[ri];
-      const long long rc = s0 + (long long)r * REGION_BYTES;
-      const bool rin = rc >= lo && rc + (long long)REGION_BYTES <= hi;  // uniform over the warp
-      if (rin && Codec::ascii_region(rtot, rflags) && ((p.dshift + S) & (Codec::DIRECT_ALIGN - 1)) == 0 &&
-          S + Codec::REGION_UNITS <= p.cap) {
-        Codec::ascii_direct(p, v, prev, c, S, err_pos);
-        continue;
-      }
-      typename Codec::Out *st = sm.staging[warp][use & 1];
-      ++use;
-      const uint32_t x0 = pc.lane_off[ri][lane];
-      constexpr uint32_t V = 16 / sizeof(typename Codec::Out);
-      const uint32_t h = (uint32_t)(p.dshift + S) & (V - 1);
-      if (lane == 0) bulk_wait_read<1>();  // the store of two regions ago has read this buffer
-      __syncwarp();
-      const Region g = Codec::convert(p, v, prev, next, c, edge, rin, st, h, x0, rtot, rflags, err_pos);
-      fence_proxy_async_smem();
-      __syncwarp();
-      store_region(p, st, S, g.skip, g.total, g.extra);
-    }
+    convert_partition<Codec>(p, cur, sm.counts[cb], S0, sm, use, err_pos);
     cur = nxt;
     cb ^= 1;
     __syncthreads();  // counts[cb ^ 1] is rewritten by the next count pass
@@ -316,6 +328,139 @@ __device__ __forceinline__ void transcode(const Params &p, XSmem<Codec> &sm, Fin
     finalize(status, key, tot);
   }
   reset_workspace(p);
+}
+
+// ---- several strings in one launch -----------------------------------------------------------
+//
+// Long strings (the serving loop's large requests) are transcoded together: their partitions
+// are numbered one after the other (string s owns partitions pstart[s] .. pstart[s+1]-1),
+// CTAs claim them from one ticket counter, and each string has its own look-back chain (its
+// Params point at its own run of states, so its first partition publishes an inclusive
+// prefix at once).  A thread that flags an error adds it to its string's minimum; the CTA
+// that finishes a string's last outstanding partition writes that string's result.
+
+// The string that owns launch partition t: the last s with pstart[s] <= t.
+__device__ __forceinline__ uint32_t seg_of(const SegParams &q, uint32_t t) {
+  uint32_t lo = 0, hi = q.B;  // pstart[lo] <= t < pstart[hi]
+  while (hi - lo > 1) {
+    const uint32_t mid = (lo + hi) >> 1;
+    if (q.pstart[mid] <= t) lo = mid;
+    else hi = mid;
+  }
+  return lo;
+}
+
+// The single-buffer parameters of string s.
+template <class Codec>
+__device__ __forceinline__ void seg_params(const SegParams &q, uint32_t s, Params &p) {
+  constexpr uint32_t OUT_UNIT = sizeof(typename Codec::Out);
+  constexpr uint32_t IN_UNIT = OUT_UNIT == 2 ? 1u : 2u;
+  const StringDesc d = q.desc[s];
+  const uintptr_t a = (uintptr_t)d.src, da = (uintptr_t)d.dst;
+  p.base = (const uint8_t *)(a & ~(uintptr_t)15);
+  p.off0 = (uint32_t)(a & 15);
+  p.n = d.n;
+  p.vbytes = p.off0 + d.n * IN_UNIT;
+  p.dbase = (uint8_t *)(da & ~(uintptr_t)15);
+  p.dshift = (uint32_t)((da & 15) / OUT_UNIT);
+  p.cap = d.cap;
+  p.ntiles = q.pstart[s + 1] - q.pstart[s];
+  p.result = q.results + s;
+  p.len_out = nullptr;
+  p.ws = q.ws;
+  p.states = q.states + q.pstart[s];
+  p.max_states = q.max_states;
+  p.wait_limit = q.wait_limit;
+  p.skip_tile = -1;
+}
+
+// The kernel body.  finalize(p, st, s) runs in one thread once string s is finished (p: its
+// parameters, st: its error minimum and output length) and writes its result.
+template <class Codec, class Final>
+__device__ __forceinline__ void transcode_segments(const SegParams &q, XSmem<Codec> &sm, Final finalize) {
+  const int tid = threadIdx.x, lane = tid & 31;
+  const uint32_t epoch = q.ws->epoch;
+  unsigned long long err_pos = NO_ERROR;
+  uint32_t use = 0;  // regions staged by this warp (picks the staging buffer)
+  int cb = 0;        // which counts[] / prm[] hold the current partition
+
+  if (tid == 0) {
+    const uint32_t t = atomicAdd(&q.ws->ticket, 1u);
+    sm.ticket = t;
+    if (t < q.ntiles) {
+      sm.sid[0] = seg_of(q, t);
+      seg_params<Codec>(q, sm.sid[0], sm.prm[0]);
+    }
+  }
+  __syncthreads();
+  uint32_t cur = sm.ticket;
+  if (cur < q.ntiles) {
+    const uint32_t lc = cur - q.pstart[sm.sid[0]];
+    count_partition<Codec>(sm.prm[0], lc, sm.counts[0]);
+    if (tid == 0) publish_aggregate(sm.prm[0], lc, sm.counts[0].total, epoch);
+  }
+  while (cur < q.ntiles) {
+    // claim and count the next partition, so that its aggregate is out a partition early
+    if (tid == 0) {
+      const uint32_t t = atomicAdd(&q.ws->ticket, 1u);
+      sm.ticket = t;
+      if (t < q.ntiles) {
+        sm.sid[cb ^ 1] = seg_of(q, t);
+        seg_params<Codec>(q, sm.sid[cb ^ 1], sm.prm[cb ^ 1]);
+      }
+    }
+    __syncthreads();
+    const uint32_t nxt = sm.ticket;
+    if (nxt < q.ntiles) {
+      const uint32_t ln = nxt - q.pstart[sm.sid[cb ^ 1]];
+      count_partition<Codec>(sm.prm[cb ^ 1], ln, sm.counts[cb ^ 1]);
+      if (tid == 0) publish_aggregate(sm.prm[cb ^ 1], ln, sm.counts[cb ^ 1].total, epoch);
+    }
+    const Params &p = sm.prm[cb];
+    const uint32_t s = sm.sid[cb];
+    const uint32_t lc = cur - q.pstart[s];
+    const uint64_t S0 = lookback_cta<XT>(p, lc, sm.counts[cb].total, epoch, sm.scratch, sm.sums);
+    convert_partition<Codec>(p, lc, sm.counts[cb], S0, sm, use, err_pos);
+    if (err_pos != NO_ERROR) {  // rare: this thread saw an error in the partition
+      atomicMin(&q.seg[s].errkey, err_pos);
+      __threadfence();
+      err_pos = NO_ERROR;
+    }
+    __syncthreads();  // every warp is done with the partition
+    if (tid == 0) {
+      if (lc + 1 == p.ntiles) *(volatile unsigned long long *)&q.seg[s].total = S0 + sm.counts[cb].total;
+      __threadfence();
+      const uint32_t prev = atomicAdd(&q.seg[s].done, 1u);
+      if (prev + 1 == p.ntiles) {
+        __threadfence();
+        finalize(p, q.seg[s], s);
+        q.seg[s].errkey = NO_ERROR;  // ready for the next launch
+        q.seg[s].total = 0;
+        q.seg[s].done = 0;
+      }
+    }
+    cur = nxt;
+    cb ^= 1;
+    __syncthreads();  // counts[cb ^ 1] and prm[cb ^ 1] are rewritten by the next claim
+  }
+  if (lane == 0) bulk_wait_all<0>();
+
+  // the last CTA to finish resets the launch's workspace
+  __syncthreads();
+  if (tid == 0) {
+    __threadfence();
+    const uint32_t prev = atomicAdd(&q.ws->done, 1u);
+    sm.is_last = prev == gridDim.x - 1;
+    if (sm.is_last) __threadfence();
+  }
+  __syncthreads();
+  if (sm.is_last) {
+    Params r;
+    r.ws = q.ws;
+    r.states = q.states;
+    r.max_states = q.max_states;
+    reset_workspace(r);
+  }
 }
 
 }  // namespace gbu

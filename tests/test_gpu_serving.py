@@ -190,3 +190,28 @@ def test_cancel_and_refusals(torch, lib, pools):
         assert _collect(srv, [rid])[rid]["status"] == "OK"
     finally:
         srv.close()
+
+
+def test_large_transcodings_share_partitioned_launches(torch, lib, pools):
+    """Requests of 70 KiB to 1 MiB in both directions (clean and with injected errors) are
+    grouped into one partitioned launch per direction; each result equals the oracle's."""
+    host, dev = pools
+    trace = W.serving_trace(40, 1e6, host, seed=3200, min_bytes=70 << 10, max_bytes=1 << 20, p_validate=0.0,
+                            p_bad=0.3)
+    srv = lib.Server(0, budget_bytes=1 << 30)
+    try:
+        reqs = [(OPS[trace["op"][i]], _request_tensor(dev, trace, i), 0, i) for i in range(len(trace["op"]))]
+        first = srv.submit(reqs)
+        got = _collect(srv, list(range(first, first + len(reqs))))
+        for k in range(len(reqs)):
+            c = got[first + k]
+            op = reqs[k][0]
+            want, wdst = _expected(_request_host(host, trace, k), op)
+            assert (c["status"], c["count"]) == want, (k, op, c["status"], c["count"], want)
+            out = _output(srv, c, op)
+            if wdst is not None:
+                assert np.array_equal(out, wdst), k
+        st = srv.stats()
+        assert st["launches"] < len(reqs)  # requests of one direction shared launches
+    finally:
+        srv.close()
