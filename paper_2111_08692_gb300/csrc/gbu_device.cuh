@@ -240,26 +240,40 @@ __device__ __forceinline__ unsigned long long warp_min_u64(unsigned long long v)
 // Records a failed wait: the launch reports GBU_TIMEOUT.
 __device__ __forceinline__ void note_timeout(WsHeader *ws) { atomicOr(&ws->status, 1u); }
 
-// A 32-bit word at virtual position v, bytes outside [off0, vbytes) read as zero.
-__device__ __forceinline__ uint32_t load_word_checked(const Params &p, long long v) {
-  uint32_t w = 0;
-#pragma unroll
-  for (int j = 0; j < 4; ++j) {
-    const long long q = v + j;
-    if (q >= (long long)p.off0 && q < (long long)p.vbytes) w |= (uint32_t)p.base[q] << (8 * j);
-  }
-  return w;
+// Mask keeping the bytes of a 32-bit word at virtual position w whose positions lie in
+// [lo, hi) (bytes outside read as zero).
+__device__ __forceinline__ uint32_t word_keep_mask(long long w, long long lo, long long hi) {
+  const long long a = lo - w, b = hi - w;  // data bytes of the word: [a, b) clamped to [0, 4)
+  const uint32_t la = a <= 0 ? 0u : (a >= 4 ? 4u : (uint32_t)a);
+  const uint32_t hb = b <= 0 ? 0u : (b >= 4 ? 4u : (uint32_t)b);
+  if (hb <= la) return 0u;
+  const uint32_t upto = hb == 4 ? 0xFFFFFFFFu : (1u << (8 * hb)) - 1u;  // bytes below hb
+  const uint32_t from = ~((1u << (8 * la)) - 1u);                        // bytes from la (la < 4)
+  return upto & from;
 }
 
-// A 16-byte chunk at virtual position c: a streaming load when it lies inside the data,
-// else byte by byte with bytes outside [off0, vbytes) read as zero.
+// A 32-bit word at virtual position v (a multiple of 4), bytes outside [off0, vbytes) read as
+// zero.  A word holding a data byte is read whole: an aligned word never crosses a page, so
+// the bytes next to the data are readable (they are then cleared).
+__device__ __forceinline__ uint32_t load_word_checked(const Params &p, long long v) {
+  const long long lo = p.off0, hi = (long long)p.vbytes;
+  if (v + 4 <= lo || v >= hi) return 0u;
+  const uint32_t w = ldg_word(p.base + v);
+  return (v >= lo && v + 4 <= hi) ? w : w & word_keep_mask(v, lo, hi);
+}
+
+// A 16-byte chunk at virtual position c (a multiple of 16): a streaming load when it lies
+// inside the data; else, if it holds a data byte, the aligned chunk is read whole (it cannot
+// cross a page) and the bytes outside [off0, vbytes) are cleared; else zeros.
 __device__ __forceinline__ uint4 load_chunk(const Params &p, long long c, bool inside) {
   if (inside) return ldg_stream(p.base + c);
-  uint4 v;
-  v.x = load_word_checked(p, c);
-  v.y = load_word_checked(p, c + 4);
-  v.z = load_word_checked(p, c + 8);
-  v.w = load_word_checked(p, c + 12);
+  const long long lo = p.off0, hi = (long long)p.vbytes;
+  if (c + 16 <= lo || c >= hi) return make_uint4(0u, 0u, 0u, 0u);
+  uint4 v = ldg_stream(p.base + c);
+  v.x &= word_keep_mask(c, lo, hi);
+  v.y &= word_keep_mask(c + 4, lo, hi);
+  v.z &= word_keep_mask(c + 8, lo, hi);
+  v.w &= word_keep_mask(c + 12, lo, hi);
   return v;
 }
 
@@ -267,12 +281,7 @@ __device__ __forceinline__ uint4 load_chunk(const Params &p, long long c, bool i
 __device__ __forceinline__ uint4 load_chunk_hint(const Params &p, long long c, bool inside,
                                                  uint64_t pol) {
   if (inside) return ldg_stream_hint(p.base + c, pol);
-  uint4 v;
-  v.x = load_word_checked(p, c);
-  v.y = load_word_checked(p, c + 4);
-  v.z = load_word_checked(p, c + 8);
-  v.w = load_word_checked(p, c + 12);
-  return v;
+  return load_chunk(p, c, false);
 }
 
 // ---- CTA-wide scan -----------------------------------------------------------------------
