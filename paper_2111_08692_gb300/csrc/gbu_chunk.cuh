@@ -11,10 +11,10 @@
 //     three back): the three flag words are funnel-shifted by 1, 2 and 3 bytes and compared
 //     with the continuation flags (bytes past the end of the input read as zero, so a cut
 //     sequence fails there);
-//   * values (rules 4-6, and rule 1 for F8-FF): each position is decoded as if it were a
-//     leading byte, two positions per 32-bit register (16-bit lanes), and the decoded value
-//     is range-checked for its class: two-byte >= U+80, three-byte >= U+800 and outside
-//     D800-DFFF, four-byte in U+10000-10FFFF (tested on the high surrogate it produces).
+//   * values (rules 4-6, and rule 1 for F8-FF): given a correct structure, only six leading
+//     bytes with particular second bytes can encode an out-of-range value; they are found by
+//     zero-byte tests on whole words (utf8_special_errors).  The transcoder, which decodes
+//     every position anyway, range-checks the decoded 16-bit values instead.
 // UTF-16 (Section 3): a word in D800-DBFF must be followed by one in DC00-DFFF and a word
 // in DC00-DFFF must follow one in D800-DBFF.
 #pragma once
@@ -65,73 +65,6 @@ __device__ __forceinline__ uint32_t utf8_structure_errors(const Flags8 f[5]) {
     err |= req ^ f[k + 1].isC;
   }
   return err;
-}
-
-// Rules 4-6 (and rule 1 for F8-FF) on the values the 16 positions of W[1..4] would decode
-// to, with W[5] the word after.  Must be called by all 32 lanes of a warp (the classes that
-// occur are agreed warp-wide so that absent classes cost nothing).  Nonzero = error.  When
-// UNITS, R[i] receives the UTF-16 word of positions 2i, 2i+1 (low, high lane: the byte
-// itself for ASCII, the decoded value for 2- and 3-byte leads, the high surrogate for
-// 4-byte leads) and L4[i] the low surrogate of 4-byte leads.
-template <bool UNITS>
-__device__ __forceinline__ uint32_t utf8_value_errors(const uint32_t W[6], const Flags8 f[5],
-                                                      uint32_t R[8], uint32_t L4[8]) {
-  uint32_t c2 = 0, c3 = 0, c4 = 0;
-#pragma unroll
-  for (int k = 0; k < 4; ++k) {
-    c2 |= f[k + 1].geC0 & ~f[k + 1].geE0;
-    c3 |= f[k + 1].geE0 & ~f[k + 1].geF0;
-    c4 |= f[k + 1].geF0;
-  }
-  const bool has2 = __any_sync(0xffffffffu, c2 != 0);
-  const bool has3 = __any_sync(0xffffffffu, c3 != 0);
-  const bool has4 = __any_sync(0xffffffffu, c4 != 0);
-  if (!UNITS && !(has2 || has3 || has4)) return 0;
-  // pair i covers positions 2i, 2i+1; E[i] = bytes (2i, 2i+1), O[i] = bytes (2i+1, 2i+2)
-  uint32_t E[9], O[9];
-#pragma unroll
-  for (int i = 0; i < 9; ++i) {
-    const int k = i >> 1, h = i & 1;
-    E[i] = __byte_perm(W[k + 1], W[k + 2 <= 5 ? k + 2 : 5], selE(h));
-    O[i] = __byte_perm(W[k + 1], W[k + 2 <= 5 ? k + 2 : 5], selO(h));
-  }
-  uint32_t bad = 0;
-#pragma unroll
-  for (int i = 0; i < 8; ++i) {
-    const int k = i >> 1, h = i & 1;
-    uint32_t r = E[i] & 0x00FF00FFu;
-    if (UNITS) L4[i] = 0;
-    if (has2 || has3 || has4) {
-      const uint32_t U2 = ((E[i] << 6) & 0x07C007C0u) | (O[i] & 0x003F003Fu);
-      if (has2) {
-        const uint32_t M2 = prmt(f[k + 1].geC0 & ~f[k + 1].geE0, 0, selM(h));
-        const uint32_t t = E[i] & 0x001E001Eu;  // U2 < 0x80 exactly when the lead is C0/C1
-        bad |= ~(t + 0x7FFF7FFFu) & M2 & 0x80008000u;
-        if (UNITS) r = (U2 & M2) | (r & ~M2);
-      }
-      if (has3) {
-        const uint32_t M3 = prmt(f[k + 1].geE0 & ~f[k + 1].geF0, 0, selM(h));
-        const uint32_t U3 = ((U2 << 6) & 0xFFC0FFC0u) | (E[i + 1] & 0x003F003Fu);
-        const uint32_t t = (U3 >> 11) & 0x001F001Fu;  // 0: below U+800; 0x1B: D800-DFFF
-        const uint32_t nz0 = t + 0x7FFF7FFFu;
-        const uint32_t nzS = (t ^ 0x001B001Bu) + 0x7FFF7FFFu;
-        bad |= ~(nz0 & nzS) & M3 & 0x80008000u;
-        if (UNITS) r = (U3 & M3) | (r & ~M3);
-      }
-      if (has4) {
-        const uint32_t M4 = prmt(f[k + 1].geF0, 0, selM(h));
-        const uint32_t hi = (U2 << 2) + ((E[i + 1] >> 4) & 0x00030003u) + 0xC7C0C7C0u;
-        const uint32_t t = ((hi ^ 0xD800D800u) >> 10) & 0x003F003Fu;  // 0 iff U+10000-10FFFF
-        bad |= (t + 0x7FFF7FFFu) & M4 & 0x80008000u;
-        if (UNITS) {
-          r = (hi & M4) | (r & ~M4);
-          L4[i] = ((E[i + 1] << 6) & 0x03C003C0u) | (O[i + 1] & 0x003F003Fu) | 0xDC00DC00u;
-        }
-      }
-    }
-    if (UNITS) R[i] = r;
-  }
-  return bad;
 }
 
 // Bit 7 of each byte set where that byte is zero (exact per byte).

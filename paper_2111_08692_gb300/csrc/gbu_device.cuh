@@ -284,55 +284,6 @@ __device__ __forceinline__ uint4 load_chunk_hint(const Params &p, long long c, b
   return load_chunk(p, c, false);
 }
 
-// ---- CTA-wide scan -----------------------------------------------------------------------
-
-// Exclusive scan over the CTA's threads (NTH threads).  Returns this thread's exclusive
-// prefix; *total receives the CTA-wide sum.  Two __syncthreads.
-template <int NTH>
-__device__ __forceinline__ uint32_t cta_exclusive_scan(uint32_t x, uint32_t *warp_sums,
-                                                       uint32_t *total) {
-  constexpr int NW = NTH / 32;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  uint32_t incl = x;
-#pragma unroll
-  for (int d = 1; d < 32; d <<= 1) {
-    const uint32_t y = __shfl_up_sync(0xffffffffu, incl, d);
-    if (lane >= d) incl += y;
-  }
-  if (lane == 31) warp_sums[warp] = incl;
-  __syncthreads();
-  if (warp == 0) {
-    const uint32_t s = lane < NW ? warp_sums[lane] : 0u;
-    uint32_t si = s;
-#pragma unroll
-    for (int d = 1; d < NW; d <<= 1) {
-      const uint32_t y = __shfl_up_sync(0xffffffffu, si, d);
-      if (lane >= d) si += y;
-    }
-    if (lane < NW) warp_sums[lane] = si - s;
-    if (lane == NW - 1) warp_sums[NW] = si;
-  }
-  __syncthreads();
-  *total = warp_sums[NW];
-  return warp_sums[warp] + incl - x;
-}
-
-// CTA-wide sum (NTH threads); every thread gets the total.  Two __syncthreads.
-template <int NTH>
-__device__ __forceinline__ uint32_t cta_sum(uint32_t x, uint32_t *warp_sums) {
-  constexpr int NW = NTH / 32;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-  for (int d = 16; d >= 1; d >>= 1) x += __shfl_xor_sync(0xffffffffu, x, d);
-  if (lane == 0) warp_sums[warp] = x;
-  __syncthreads();
-  uint32_t t = 0;
-#pragma unroll
-  for (int w = 0; w < NW; ++w) t += warp_sums[w];
-  __syncthreads();
-  return t;
-}
-
 // ---- decoupled look-back -----------------------------------------------------------------
 
 // Publishes partition `part`'s aggregate (the inclusive prefix at once for partition 0).
@@ -343,50 +294,9 @@ __device__ __forceinline__ void publish_aggregate(const Params &p, uint32_t part
   st_relaxed_u64(&p.states[part], (part == 0 ? ST_FLAG_INC : ST_FLAG_AGG) | tag | (agg & ST_VALUE_MASK));
 }
 
-// Exclusive prefix of partition `part` (one warp, all lanes): reads the 32 states before the
-// current position at once, waits (bounded) until each has an aggregate or an inclusive
-// prefix of this launch, sums back to the nearest inclusive prefix, and repeats 32 earlier
-// while none was found.  Then publishes the partition's inclusive prefix (excl + agg).
-__device__ __forceinline__ uint64_t lookback(const Params &p, uint32_t part, uint64_t agg,
-                                             uint32_t epoch) {
-  const int lane = threadIdx.x & 31;
-  uint64_t excl = 0;
-  if (part > 0) {
-    long long pred = (long long)part - 1;
-    uint32_t polls = 0;
-    while (true) {
-      const long long idx = pred - lane;
-      uint64_t s = ST_FLAG_INC;  // before partition 0: an inclusive prefix of 0
-      bool ok = true;
-      if (idx >= 0) {
-        s = ld_relaxed_u64(&p.states[idx]);
-        ok = (s >> 62) != 0 && (uint32_t)((s >> ST_EPOCH_SHIFT) & ST_EPOCH_MASK) == epoch;
-      }
-      if (!__all_sync(0xffffffffu, ok)) {
-        if (++polls >= p.wait_limit || ((polls & 63) == 0 && ld_relaxed_u32(&p.ws->status))) {
-          note_timeout(p.ws);
-          break;  // give up with the prefix collected so far
-        }
-        __nanosleep(64);
-        continue;
-      }
-      const uint32_t incmask = __ballot_sync(0xffffffffu, (s >> 62) == 2);
-      const int first_inc = incmask ? __ffs(incmask) - 1 : 32;
-      excl += warp_sum_u64(lane <= first_inc ? (s & ST_VALUE_MASK) : 0ull);
-      if (incmask) break;
-      pred -= 32;
-    }
-    if (lane == 0 && (long long)part != p.skip_tile) {
-      const uint64_t tag = (uint64_t)epoch << ST_EPOCH_SHIFT;
-      st_relaxed_u64(&p.states[part], ST_FLAG_INC | tag | ((excl + agg) & ST_VALUE_MASK));
-    }
-  }
-  return excl;
-}
-
-// CTA-wide form of the look-back (NTH threads): each poll reads NTH predecessor states at
-// once, so a look-back that has to sum many aggregates back to the nearest inclusive prefix
-// takes one round trip instead of one per 32.  Only the states between the partition and
+// Exclusive prefix of partition `part` by a CTA-wide look-back (NTH threads): each poll
+// reads NTH predecessor states at once, so a look-back that has to sum many aggregates back
+// to the nearest inclusive prefix takes one round trip per NTH states.  Only the states between the partition and
 // the nearest inclusive prefix must have been published.  scratch holds NTH/32 + 2 words.
 // Returns the exclusive prefix (in every thread) and publishes the inclusive prefix.
 template <int NTH>
