@@ -89,12 +89,16 @@ __device__ __forceinline__ uint32_t utf8_special_errors(const uint32_t W[6], boo
     const uint32_t n = __funnelshift_r(W[k], W[k + 1], 8);  // byte j: the byte after byte j
     if (has2) bad |= zero_bytes((w & 0xFEFEFEFEu) ^ 0xC0C0C0C0u);
     if (has3) {
-      bad |= zero_bytes((w ^ 0xE0E0E0E0u) | (n & 0x20202020u));
-      bad |= zero_bytes((w ^ 0xEDEDEDEDu) | (~n & 0x20202020u));
+      // E0 then 80-9F, or ED then A0-BF: with y = 1 where the next byte has bit 5 set
+      // (A0-BF), exactly the bytes equal to E0 ^ 0D*y (E0 when y = 0, ED when y = 1)
+      const uint32_t y = (n >> 5) & 0x01010101u;
+      bad |= zero_bytes(w ^ 0xE0E0E0E0u ^ (y * 0x0Du));
     }
     if (has4) {
-      bad |= zero_bytes((w ^ 0xF0F0F0F0u) | (n & 0x30303030u));
-      bad |= zero_bytes(w ^ 0xF4F4F4F4u) & ((n & 0x30303030u) + 0x70707070u);
+      // F0 then 80-8F, or F4 then 90-BF: with y4 = 4 where the next byte has bit 4 or 5 set
+      // (90-BF), exactly the bytes equal to F0 ^ y4
+      const uint32_t y4 = ((n >> 2) | (n >> 3)) & 0x04040404u;
+      bad |= zero_bytes(w ^ 0xF0F0F0F0u ^ y4);
       bad |= ((w & 0x7F7F7F7Fu) + 0x0B0B0B0Bu) & w & 0x80808080u;  // F5-FF
     }
   }

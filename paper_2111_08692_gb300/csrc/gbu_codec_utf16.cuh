@@ -65,12 +65,12 @@ struct Utf16ToUtf8 {
 
   __device__ __forceinline__ static bool ascii_region(uint32_t rtot, uint32_t) { return rtot == 256u; }
 
-  // An all-ASCII region inside the buffer, output 8-byte aligned: each lane narrows its 8
-  // words and stores them with one 8-byte store (Section 4's ASCII route).
-  __device__ __forceinline__ static void ascii_direct(const Params &p, uint4 v, uint32_t, long long,
-                                                      uint64_t S, unsigned long long &) {
+  // An all-ASCII region inside the buffer whose output starts at dst, 8-byte aligned: each
+  // lane narrows its 8 words and stores them with one 8-byte store (Section 4's ASCII route).
+  __device__ __forceinline__ static void ascii_direct(uint8_t *dst, uint4 v, uint32_t, long long,
+                                                      unsigned long long &) {
     const int lane = threadIdx.x & 31;
-    uint2 *d = reinterpret_cast<uint2 *>(p.dbase + p.dshift + S) + lane;
+    uint2 *d = reinterpret_cast<uint2 *>(dst) + lane;
     *d = make_uint2(__byte_perm(v.x, v.y, 0x6420), __byte_perm(v.z, v.w, 0x6420));
   }
 

@@ -55,12 +55,12 @@ struct Utf8ToUtf16 {
 
   __device__ __forceinline__ static bool ascii_region(uint32_t, uint32_t rflags) { return rflags == 0; }
 
-  // An all-ASCII region inside the buffer, output 16-byte aligned: each lane widens its 16
-  // bytes and stores them with two 16-byte stores (Section 4's ASCII path).  The only
+  // An all-ASCII region inside the buffer whose output starts at dst, 16-byte aligned: each
+  // lane widens its 16 bytes and stores them with two 16-byte stores (Section 4's ASCII path).  The only
   // possible error is a leading byte just before the region that wants continuation bytes
   // inside it (lane 0's chunk).
-  __device__ __forceinline__ static void ascii_direct(const Params &p, uint4 v, uint32_t prev, long long c,
-                                                      uint64_t S, unsigned long long &err_pos) {
+  __device__ __forceinline__ static void ascii_direct(uint16_t *dst, uint4 v, uint32_t prev, long long c,
+                                                      unsigned long long &err_pos) {
     const int lane = threadIdx.x & 31;
     if (lane == 0) {
       const Flags8 fp = classify8(prev);
@@ -68,7 +68,7 @@ struct Utf8ToUtf16 {
                            __funnelshift_l(fp.geF0, 0u, 24);
       if (req && (unsigned long long)c < err_pos) err_pos = (unsigned long long)c;
     }
-    uint4 *d = reinterpret_cast<uint4 *>(reinterpret_cast<uint16_t *>(p.dbase) + p.dshift + S) + 2 * lane;
+    uint4 *d = reinterpret_cast<uint4 *>(dst) + 2 * lane;
     d[0] = make_uint4(__byte_perm(v.x, 0, 0x4140), __byte_perm(v.x, 0, 0x4342), __byte_perm(v.y, 0, 0x4140),
                       __byte_perm(v.y, 0, 0x4342));
     d[1] = make_uint4(__byte_perm(v.z, 0, 0x4140), __byte_perm(v.z, 0, 0x4342), __byte_perm(v.w, 0, 0x4140),
@@ -94,6 +94,79 @@ struct Utf8ToUtf16 {
       acc = __dp4a(w & s1 & (w << 2) & (w << 3) & vm, 0x01010101u, acc);
     }
     return acc >> 7;
+  }
+
+  // Validates one chunk of a region that lies inside the buffer and whose output fits the
+  // staging buffer, and stages its words from index addr on; returns nonzero when the chunk
+  // breaks a rule.  H2 / H3 / H4: leading bytes C0-DF / E0-EF / F0-FF occur in the warp
+  // (the code for an absent class is left out).  Rules 1-3 by the funnel-shifted lead flags
+  // of the classes present; rules 4-5 for the two- and three-byte forms by the word-level
+  // tests of utf8_special_errors; the four-byte form by the range of the decoded first
+  // surrogate (D800-DBFF exactly when the code point is in 10000-10FFFF).  Each
+  // non-continuation byte stages one word (a four-byte sequence two), which is the count the
+  // count pass gave the chunk, so no store needs a bounds test.
+  template <bool H2, bool H3, bool H4>
+  __device__ __forceinline__ static uint32_t convert_fast(const uint32_t W[6], const Flags8 f[5], uint16_t *st,
+                                                          uint32_t addr) {
+    // with a single class present, every byte >= C0 is a leading byte of that class
+    constexpr bool ONE = (int)H2 + (int)H3 + (int)H4 == 1;
+    uint32_t bad = 0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const uint32_t a = f[k].geC0, b = f[k + 1].geC0;
+      uint32_t req = __funnelshift_l(a, b, 8);
+      if (H3 || H4) req |= ONE ? __funnelshift_l(a, b, 16) : __funnelshift_l(f[k].geE0, f[k + 1].geE0, 16);
+      if (H4) req |= ONE ? __funnelshift_l(a, b, 24) : __funnelshift_l(f[k].geF0, f[k + 1].geF0, 24);
+      bad |= req ^ f[k + 1].isC;
+    }
+    if (H2 || H3) bad |= utf8_special_errors(W, H2, H3, false);
+    // pair i covers positions 2i, 2i+1 (two 16-bit lanes): E = bytes (2i, 2i+1),
+    // O = bytes (2i+1, 2i+2); the next pair's E and O hold the third and fourth bytes
+    uint32_t E = __byte_perm(W[1], W[2], selE(0));
+    uint32_t O = __byte_perm(W[1], W[2], selO(0));
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const int k = i >> 1, h = i & 1;
+      const int kn = (i + 1) >> 1, hn = (i + 1) & 1;
+      const uint32_t En = __byte_perm(W[kn + 1], W[kn + 2 <= 5 ? kn + 2 : 5], selE(hn));
+      const uint32_t On = __byte_perm(W[kn + 1], W[kn + 2 <= 5 ? kn + 2 : 5], selO(hn));
+      const Flags8 &g = f[k + 1];
+      uint32_t r = E & 0x00FF00FFu;
+      uint32_t lo4 = 0;
+      if (H2) {
+        const uint32_t M2 = prmt(ONE ? g.geC0 : g.geC0 & ~g.geE0, 0, selM(h));
+        const uint32_t U2 = (E & 0x001F001Fu) * 64u + (O & 0x003F003Fu);
+        r = (U2 & M2) | (r & ~M2);
+      }
+      if (H3) {
+        const uint32_t M3 = prmt(ONE ? g.geC0 : g.geE0 & ~g.geF0, 0, selM(h));
+        const uint32_t U3 = ((E & 0x000F000Fu) * 64u + (O & 0x003F003Fu)) * 64u + (En & 0x003F003Fu);
+        r = (U3 & M3) | (r & ~M3);
+      }
+      if (H4) {
+        const uint32_t M4 = prmt(ONE ? g.geC0 : g.geF0, 0, selM(h));
+        // first surrogate: (code point >> 10) + D7C0, from bits of the first three bytes
+        const uint32_t hi = (E & 0x001F001Fu) * 256u + (O & 0x003F003Fu) * 4u + ((En >> 4) & 0x00030003u) +
+                            0xC7C0C7C0u;
+        const uint32_t t = ((hi ^ 0xD800D800u) >> 10) & 0x003F003Fu;  // 0 iff 10000-10FFFF
+        bad |= (t + 0x7FFF7FFFu) & M4 & 0x80008000u;
+        r = (hi & M4) | (r & ~M4);
+        lo4 = (En & 0x000F000Fu) * 64u + (On & 0x003F003Fu) + 0xDC00DC00u;
+      }
+      const uint32_t nc = ~g.isC;  // bit 7 of each byte: not a continuation byte
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        const int bit = 16 * h + 8 * q + 7;
+        if ((nc >> bit) & 1u) {
+          st[addr] = (uint16_t)(r >> (16 * q));
+          if (H4 && (((ONE ? g.geC0 : g.geF0) >> bit) & 1u)) st[++addr] = (uint16_t)(lo4 >> (16 * q));
+          ++addr;
+        }
+      }
+      E = En;
+      O = On;
+    }
+    return bad;
   }
 
   // Validates the chunk and stages its UTF-16 words.  The lane's offset x0 (inside the
@@ -129,12 +202,62 @@ struct Utf8ToUtf16 {
     Flags8 f[5];
 #pragma unroll
     for (int k = 0; k < 5; ++k) f[k] = classify8(W[k]);
+    if (inside && base + rtot <= STAGE) {
+      // the leading-byte classes present in the warp, the word before each chunk included
+      // (a sequence that starts there reaches into the chunk)
+      uint32_t c2 = 0, c3 = 0, c4 = 0;
+#pragma unroll
+      for (int k = 0; k < 5; ++k) {
+        c2 |= f[k].geC0 & ~f[k].geE0;
+        c3 |= f[k].geE0 & ~f[k].geF0;
+        c4 |= f[k].geF0;
+      }
+      const bool h2 = __any_sync(0xffffffffu, c2 != 0);
+      const bool h3 = __any_sync(0xffffffffu, c3 != 0);
+      const bool h4 = __any_sync(0xffffffffu, c4 != 0);
+      const uint32_t addr = base + x0;
+      uint32_t bad;
+      if (h4) {
+        bad = (h2 || h3) ? convert_fast<true, true, true>(W, f, st, addr)
+                         : convert_fast<false, false, true>(W, f, st, addr);
+      } else if (h3) {
+        bad = h2 ? convert_fast<true, true, false>(W, f, st, addr) : convert_fast<false, true, false>(W, f, st, addr);
+      } else {
+        bad = h2 ? convert_fast<true, false, false>(W, f, st, addr) : convert_fast<true, true, true>(W, f, st, addr);
+      }
+      if (bad && (unsigned long long)c < err_pos) err_pos = (unsigned long long)c;
+      return Region{rtot, 0u, 0u, rtot};
+    }
+    const General r = convert_general(p.off0, (long long)p.vbytes, v, prev, next, c, edge, st, base, x0, rtot, err_pos);
+    err_pos = r.err_pos;
+    return r.g;
+  }
+
+  struct General {
+    Region g;
+    unsigned long long err_pos;
+  };
+
+  // Any region (one at a buffer end, or one whose output would overflow the staging buffer,
+  // which only happens after an error): per-byte word counts with the buffer's bounds, and
+  // a bounds test before every store.  Kept out of line so that the hot loop does not carry
+  // its registers.
+  __device__ __noinline__ static General convert_general(long long lo, long long hi, uint4 v, uint32_t prev, uint32_t next,
+                                                          long long c, bool edge, uint16_t *st, uint32_t base,
+                                                          uint32_t x0, uint32_t rtot, unsigned long long err_pos) {
+    uint32_t W[6];
+    W[0] = prev;
+    W[1] = v.x; W[2] = v.y; W[3] = v.z; W[4] = v.w;
+    W[5] = next;
+    Flags8 f[5];
+#pragma unroll
+    for (int k = 0; k < 5; ++k) f[k] = classify8(W[k]);
     uint32_t uw[4];  // per byte: UTF-16 words produced at that position (0, 1 or 2)
     uint32_t cnt = 0;
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
       uint32_t vm = 0x80808080u;
-      if (edge) vm = byte_range_mask(c + 4 * k, p.off0, (long long)p.vbytes);
+      if (edge) vm = byte_range_mask(c + 4 * k, lo, hi);
       uw[k] = ((~f[k + 1].isC & vm) >> 7) + ((f[k + 1].geF0 & vm) >> 7);
       cnt = __dp4a(uw[k], 0x01010101u, cnt);
     }
@@ -206,7 +329,7 @@ struct Utf8ToUtf16 {
     }
     if (err && (unsigned long long)c < err_pos) err_pos = (unsigned long long)c;
     if (g.total > STAGE - base) g.total = STAGE - base;  // only after the first error
-    return g;
+    return General{g, err_pos};
   }
 };
 

@@ -25,8 +25,8 @@
 //                                      uint32_t base, uint32_t x0, uint32_t rtot, uint32_t rflags,
 //                                      unsigned long long& err_pos);
 //     __device__ static bool ascii_region(uint32_t rtot, uint32_t rflags);
-//     __device__ static void ascii_direct(const Params&, uint4 v, uint32_t prev, long long c,
-//                                         uint64_t S, unsigned long long& err_pos);
+//     __device__ static void ascii_direct(Out* dst, uint4 v, uint32_t prev, long long c,
+//                                         unsigned long long& err_pos);
 //   };
 // count() returns the units one chunk contributes to its region (the total that converting
 // the region stages) and sets codec-defined flag bits (the region's flags are the OR over its
@@ -88,12 +88,14 @@ __device__ __forceinline__ long long chunk_pos(uint32_t part, int w, int r, int 
 // Counts partition `part` into pc (all threads).  Warp w scans the lane counts of each of its
 // regions (two regions packed per register: a region has at most 32 x 48 units), keeping
 // every lane's exclusive offset; then warp 0 turns the 128 region totals into offsets.
-template <class Codec>
+// INSIDE: the partition lies inside the buffer with a word to spare at each end
+// (part_inside), so that no chunk needs a bounds test.
+template <class Codec, bool INSIDE>
 __device__ __forceinline__ void count_partition(const Params &p, uint32_t part, PartCounts &pc) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const long long p0 = (long long)part * PART_BYTES;
   const long long lo = p.off0, hi = (long long)p.vbytes;
-  const bool inside = p0 >= lo && p0 + (long long)PART_BYTES <= hi;
+  const bool inside = INSIDE || (p0 >= lo && p0 + (long long)PART_BYTES <= hi);
   // the partition is read again by its conversion one partition later: keep it in L2
   const uint64_t keep = l2_policy_keep();
   uint4 v[PART_ROUNDS];
@@ -162,22 +164,20 @@ __device__ __forceinline__ void count_partition(const Params &p, uint32_t part, 
   __syncthreads();
 }
 
-// Writes the region's staged units [skip, cnt + extra), which start at global unit S (one
-// warp).  Staged index h + k holds global unit S + k with h = (dshift + S) & (V - 1), so
-// staged chunk boundaries fall on 16-byte destination boundaries; units at or past cap are
-// not written.  Lane 0 issues the bulk store of the whole 16-byte chunks and commits it as
-// one bulk group; the lanes write the ragged ends.  Every lane that wrote the staging
-// buffer must have run fence_proxy_async_smem() before the __syncwarp preceding this call.
+// Writes a region's staged units [skip, cnt + extra) (one warp).  gdst is the 16-byte-aligned
+// destination of staged index 0 and h the staged index of the region's first unit, so that
+// staged chunk boundaries fall on 16-byte destination boundaries; units at or past `room`
+// (counted from the region's first unit) are not written.  Lane 0 issues the bulk store of
+// the whole 16-byte chunks and commits it as one bulk group; the lanes write the ragged
+// ends.  Every lane that wrote the staging buffer must have run fence_proxy_async_smem()
+// before the __syncwarp preceding this call.
 template <typename U>
-__device__ __forceinline__ void store_region(const Params &p, const U *staging, uint64_t S,
-                                             uint32_t skip, uint32_t cnt, uint32_t extra) {
+__device__ __forceinline__ void store_staged(U *gdst, const U *staging, uint32_t h, uint32_t room, uint32_t skip,
+                                             uint32_t cnt, uint32_t extra) {
   constexpr uint32_t V = 16 / sizeof(U);
   const uint32_t lane = threadIdx.x & 31;
-  const uint32_t h = (uint32_t)(p.dshift + S) & (V - 1);
   uint32_t lim = cnt + extra;
-  const uint64_t room = p.cap > S ? p.cap - S : 0;
-  if (room < lim) lim = (uint32_t)room;
-  U *gdst = reinterpret_cast<U *>(p.dbase) + ((p.dshift + S) - h);
+  if (room < lim) lim = room;
   const uint32_t beg = h + (skip < lim ? skip : lim);
   const uint32_t end = h + lim;
   const uint32_t head_end = (beg + V - 1) & ~(V - 1);  // first 16-byte boundary at or after beg
@@ -191,6 +191,17 @@ __device__ __forceinline__ void store_region(const Params &p, const U *staging, 
     gdst[beg + lane] = staging[beg + lane];
   }
   if (lane == 0) bulk_commit();
+}
+
+// store_staged for a region whose output starts at global unit S of the buffer p describes.
+template <typename U>
+__device__ __forceinline__ void store_region(const Params &p, const U *staging, uint64_t S, uint32_t skip,
+                                             uint32_t cnt, uint32_t extra) {
+  constexpr uint32_t V = 16 / sizeof(U);
+  const uint32_t h = (uint32_t)(p.dshift + S) & (V - 1);
+  const uint64_t room = p.cap > S ? p.cap - S : 0;
+  U *gdst = reinterpret_cast<U *>(p.dbase) + ((p.dshift + S) - h);
+  store_staged(gdst, staging, h, room < 0xFFFFFFFFull ? (uint32_t)room : 0xFFFFFFFFu, skip, cnt, extra);
 }
 
 // Warp-level exclusive scan of per-lane counts; *total receives the warp sum.
@@ -224,29 +235,40 @@ __device__ __forceinline__ Region convert_counted(const Params &p, uint4 v, uint
 // Step 3 for partition `part` of the buffer that p describes (all threads; each warp on its
 // slice): transcodes the partition, whose output starts at unit S0, with the region offsets,
 // lane offsets and flags of its count pass in pc.
-template <class Codec>
+template <class Codec, bool INSIDE>
 __device__ __forceinline__ void convert_partition(const Params &p, uint32_t part, const PartCounts &pc, uint64_t S0,
                                                   XSmem<Codec> &sm, uint32_t &use, unsigned long long &err_pos) {
+  using Out = typename Codec::Out;
+  constexpr uint32_t V = 16 / sizeof(Out);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const long long lo = p.off0, hi = (long long)p.vbytes;
   // this warp's slice: the words just before and after it, and its first chunk
   const long long s0 = chunk_pos(part, warp, 0, 0);
-  const bool slice_inside = s0 - 4 >= lo && s0 + (long long)SLICE_BYTES + 4 <= hi;
+  const bool slice_inside = INSIDE || (s0 - 4 >= lo && s0 + (long long)SLICE_BYTES + 4 <= hi);
   const uint32_t before = slice_inside ? ldg_word(p.base + s0 - 4) : load_word_checked(p, s0 - 4);
   const uint32_t after =
       slice_inside ? ldg_word(p.base + s0 + SLICE_BYTES) : load_word_checked(p, s0 + SLICE_BYTES);
   const uint64_t last_use = l2_policy_last_use();
   // two regions in flight ahead of the one being converted (the convert pass reads from L2)
+  const uint8_t *const src = p.base + s0 + CHUNK * lane;  // the lane's chunk of the first region
   uint4 v_next = load_chunk_hint(p, s0 + CHUNK * lane, slice_inside, last_use);
   uint4 v_next2 = load_chunk_hint(p, s0 + REGION_BYTES + CHUNK * lane, slice_inside, last_use);
   uint32_t prev_last = before;  // last word of the previous region (lane 31's), for lane 0
+  // the partition's output: its first unit counted from the 16-byte-rounded destination base,
+  // and the units the destination holds from there on (clamped to 32 bits)
+  const uint64_t D0 = p.dshift + S0;
+  const uint64_t room64 = p.cap > S0 ? p.cap - S0 : 0;
+  const uint32_t room0 = room64 < 0xFFFFFFFFull ? (uint32_t)room64 : 0xFFFFFFFFu;
+  Out *const dpart = reinterpret_cast<Out *>(p.dbase) + D0;
 #pragma unroll 1
   for (int r = 0; r < PART_ROUNDS; ++r) {
     const long long c = s0 + (long long)r * REGION_BYTES + CHUNK * lane;
-    const bool edge = c < lo || c + 16 > hi;
+    const bool edge = !INSIDE && (c < lo || c + 16 > hi);
     const uint4 v = v_next;
     v_next = v_next2;
-    if (r + 2 < PART_ROUNDS) v_next2 = load_chunk_hint(p, c + 2 * REGION_BYTES, slice_inside, last_use);
+    if (r + 2 < PART_ROUNDS)
+      v_next2 = INSIDE ? ldg_stream_hint(src + (r + 2) * REGION_BYTES, last_use)
+                       : load_chunk_hint(p, c + 2 * REGION_BYTES, slice_inside, last_use);
     uint32_t prev = __shfl_up_sync(0xffffffffu, v.w, 1);
     uint32_t next = __shfl_down_sync(0xffffffffu, v.x, 1);
     const uint32_t next_first = __shfl_sync(0xffffffffu, v_next.x, 0);  // next region's first word
@@ -255,28 +277,49 @@ __device__ __forceinline__ void convert_partition(const Params &p, uint32_t part
     prev_last = __shfl_sync(0xffffffffu, v.w, 31);
 
     const int ri = warp * PART_ROUNDS + r;
-    const uint64_t S = S0 + pc.off[ri];
+    const uint32_t off = pc.off[ri];  // the region's first unit inside the partition's output
     const uint32_t rtot = pc.rtot[ri];
     const uint32_t rflags = pc.flags[ri];
+    const uint32_t dlo = (uint32_t)D0 + off;  // low bits of its destination unit
+    const uint32_t room = room0 > off ? room0 - off : 0u;
     const long long rc = s0 + (long long)r * REGION_BYTES;
-    const bool rin = rc >= lo && rc + (long long)REGION_BYTES <= hi;  // uniform over the warp
-    if (rin && Codec::ascii_region(rtot, rflags) && ((p.dshift + S) & (Codec::DIRECT_ALIGN - 1)) == 0 &&
-        S + Codec::REGION_UNITS <= p.cap) {
-      Codec::ascii_direct(p, v, prev, c, S, err_pos);
+    const bool rin = INSIDE || (rc >= lo && rc + (long long)REGION_BYTES <= hi);  // uniform over the warp
+    if (rin && Codec::ascii_region(rtot, rflags) && (dlo & (Codec::DIRECT_ALIGN - 1)) == 0 &&
+        Codec::REGION_UNITS <= room) {
+      Codec::ascii_direct(dpart + off, v, prev, c, err_pos);
       continue;
     }
-    typename Codec::Out *st = sm.staging[warp][use & 1];
+    Out *st = sm.staging[warp][use & 1];
     ++use;
     const uint32_t x0 = pc.lane_off[ri][lane];
-    constexpr uint32_t V = 16 / sizeof(typename Codec::Out);
-    const uint32_t h = (uint32_t)(p.dshift + S) & (V - 1);
+    const uint32_t h = dlo & (V - 1);
     if (lane == 0) bulk_wait_read<1>();  // the store of two regions ago has read this buffer
     __syncwarp();
     const Region g = Codec::convert(p, v, prev, next, c, edge, rin, st, h, x0, rtot, rflags, err_pos);
     fence_proxy_async_smem();
     __syncwarp();
-    store_region(p, st, S, g.skip, g.total, g.extra);
+    store_staged(dpart + off - h, st, h, room, g.skip, g.total, g.extra);
   }
+}
+
+// Whether partition `part` lies inside the buffer with a word to spare at each end (then no
+// chunk of it, nor a neighbouring word, needs a bounds test).
+__device__ __forceinline__ bool part_inside(const Params &p, uint32_t part) {
+  const long long p0 = (long long)part * PART_BYTES;
+  return p0 - 4 >= (long long)p.off0 && p0 + (long long)PART_BYTES + 4 <= (long long)p.vbytes;
+}
+
+template <class Codec>
+__device__ __forceinline__ void count_part(const Params &p, uint32_t part, PartCounts &pc) {
+  if (part_inside(p, part)) count_partition<Codec, true>(p, part, pc);
+  else count_partition<Codec, false>(p, part, pc);
+}
+
+template <class Codec>
+__device__ __forceinline__ void convert_part(const Params &p, uint32_t part, const PartCounts &pc, uint64_t S0,
+                                             XSmem<Codec> &sm, uint32_t &use, unsigned long long &err_pos) {
+  if (part_inside(p, part)) convert_partition<Codec, true>(p, part, pc, S0, sm, use, err_pos);
+  else convert_partition<Codec, false>(p, part, pc, S0, sm, use, err_pos);
 }
 
 template <class Codec, class Final>
@@ -292,7 +335,7 @@ __device__ __forceinline__ void transcode(const Params &p, XSmem<Codec> &sm, Fin
   __syncthreads();
   uint32_t cur = sm.ticket;
   if (cur < p.ntiles) {
-    count_partition<Codec>(p, cur, sm.counts[cb]);
+    count_part<Codec>(p, cur, sm.counts[cb]);
     if (tid == 0) {
       publish_aggregate(p, cur, sm.counts[cb].total, epoch);
       atomicAdd(&p.ws->total, (unsigned long long)sm.counts[cb].total);
@@ -304,7 +347,7 @@ __device__ __forceinline__ void transcode(const Params &p, XSmem<Codec> &sm, Fin
     __syncthreads();
     const uint32_t nxt = sm.ticket;
     if (nxt < p.ntiles) {
-      count_partition<Codec>(p, nxt, sm.counts[cb ^ 1]);
+      count_part<Codec>(p, nxt, sm.counts[cb ^ 1]);
       if (tid == 0) {
         publish_aggregate(p, nxt, sm.counts[cb ^ 1].total, epoch);
         atomicAdd(&p.ws->total, (unsigned long long)sm.counts[cb ^ 1].total);
@@ -312,7 +355,7 @@ __device__ __forceinline__ void transcode(const Params &p, XSmem<Codec> &sm, Fin
     }
     const uint64_t S0 = lookback_cta<XT>(p, cur, sm.counts[cb].total, epoch, sm.scratch, sm.sums);
 
-    convert_partition<Codec>(p, cur, sm.counts[cb], S0, sm, use, err_pos);
+    convert_part<Codec>(p, cur, sm.counts[cb], S0, sm, use, err_pos);
     cur = nxt;
     cb ^= 1;
     __syncthreads();  // counts[cb ^ 1] is rewritten by the next count pass
@@ -396,7 +439,7 @@ __device__ __forceinline__ void transcode_segments(const SegParams &q, XSmem<Cod
   uint32_t cur = sm.ticket;
   if (cur < q.ntiles) {
     const uint32_t lc = cur - q.pstart[sm.sid[0]];
-    count_partition<Codec>(sm.prm[0], lc, sm.counts[0]);
+    count_part<Codec>(sm.prm[0], lc, sm.counts[0]);
     if (tid == 0) publish_aggregate(sm.prm[0], lc, sm.counts[0].total, epoch);
   }
   while (cur < q.ntiles) {
@@ -413,14 +456,14 @@ __device__ __forceinline__ void transcode_segments(const SegParams &q, XSmem<Cod
     const uint32_t nxt = sm.ticket;
     if (nxt < q.ntiles) {
       const uint32_t ln = nxt - q.pstart[sm.sid[cb ^ 1]];
-      count_partition<Codec>(sm.prm[cb ^ 1], ln, sm.counts[cb ^ 1]);
+      count_part<Codec>(sm.prm[cb ^ 1], ln, sm.counts[cb ^ 1]);
       if (tid == 0) publish_aggregate(sm.prm[cb ^ 1], ln, sm.counts[cb ^ 1].total, epoch);
     }
     const Params &p = sm.prm[cb];
     const uint32_t s = sm.sid[cb];
     const uint32_t lc = cur - q.pstart[s];
     const uint64_t S0 = lookback_cta<XT>(p, lc, sm.counts[cb].total, epoch, sm.scratch, sm.sums);
-    convert_partition<Codec>(p, lc, sm.counts[cb], S0, sm, use, err_pos);
+    convert_part<Codec>(p, lc, sm.counts[cb], S0, sm, use, err_pos);
     if (err_pos != NO_ERROR) {  // rare: this thread saw an error in the partition
       atomicMin(&q.seg[s].errkey, err_pos);
       __threadfence();

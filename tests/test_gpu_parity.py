@@ -119,6 +119,34 @@ def test_errors_near_tile_and_warp_boundaries(codec, torch):
             assert v[0] != "OK" and v[1] == i, (t, bad.hex(), v)
 
 
+STRADDLERS = ("\u00e9".encode(), "\u4e2d".encode(), "\U0001F600".encode())  # 2-, 3-, 4-byte
+
+
+@pytest.mark.parametrize("profile", ("latin", "cyrillic", "cjk", "emoji"))
+def test_single_class_regions(codec, torch, profile):
+    """Text whose regions hold one class of leading byte (two-, three- or four-byte), with a
+    character of another class cut by a region, round or partition boundary (so the region
+    after it starts with that character's continuation bytes), and with each invalid
+    sequence inside a region."""
+    base = W.profile_buffers(profile, 3 * PART, 0, 41, cache=False)[0]
+    starts = char_starts_utf8(base)
+    for b in (512, 1024, 4096, TTILE, PART, PART + 512, 2 * PART - 512):
+        s = int(starts[np.searchsorted(starts, b - 8)])
+        s = s if s <= b - 4 else int(starts[np.searchsorted(starts, b - 8) - 1])
+        for ch in STRADDLERS:
+            for d in range(1, len(ch)):
+                pad = np.full(b - d - s, 0x41, np.uint8)
+                data = np.concatenate([base[:s], pad, np.frombuffer(ch, np.uint8), base[s:]])
+                v, _ = check_utf8_input(codec, torch, data)
+                assert v[0] == "OK", (profile, b, ch, d, v)
+    for t in (700, 5000, PART - 300, PART + 4000):
+        i = int(starts[np.searchsorted(starts, t)])
+        for bad in INVALID_UTF8:
+            data = np.concatenate([base[:i], np.frombuffer(bad, np.uint8), base[i:]])
+            v, _ = check_utf8_input(codec, torch, data)
+            assert v[0] != "OK" and v[1] == i, (profile, t, bad.hex(), v)
+
+
 def test_error_at_the_last_byte_and_cut_at_the_end(codec, torch):
     base = _mixed(3 * TILE, 9)
     starts = char_starts_utf8(base)
