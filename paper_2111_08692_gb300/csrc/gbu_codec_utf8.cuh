@@ -49,6 +49,16 @@ struct Utf8ToUtf16 {
   static constexpr uint32_t STAGE = 512 + 16 + 16;
 
   static constexpr uint32_t F_NONASCII = 1;  // flag: a byte >= 0x80 (or a chunk at a buffer end)
+  static constexpr uint32_t F_C2 = 2;        // flag: a leading byte C0-DF
+  static constexpr uint32_t F_C3 = 4;        // flag: a leading byte E0-EF
+  static constexpr uint32_t F_C4 = 8;        // flag: a byte F0-FF
+
+  // F_C2 / F_C3 / F_C4 for the bytes of w selected by m (bit 7 of each byte).
+  __device__ __forceinline__ static uint32_t lead_classes(uint32_t w, uint32_t m) {
+    const uint32_t s2 = w << 2, s3 = w << 3;
+    const uint32_t ge = w & (w << 1) & m;  // >= C0
+    return ((ge & ~s2) ? F_C2 : 0u) | ((ge & s2 & ~s3) ? F_C3 : 0u) | ((ge & s2 & s3) ? F_C4 : 0u);
+  }
 
   static constexpr uint32_t REGION_UNITS = 512;  // words out of an all-ASCII region
   static constexpr uint32_t DIRECT_ALIGN = 8;    // its lanes store 16 words (32 bytes) each
@@ -68,11 +78,17 @@ struct Utf8ToUtf16 {
                            __funnelshift_l(fp.geF0, 0u, 24);
       if (req && (unsigned long long)c < err_pos) err_pos = (unsigned long long)c;
     }
+    const uint4 a = make_uint4(__byte_perm(v.x, 0, 0x4140), __byte_perm(v.x, 0, 0x4342),
+                               __byte_perm(v.y, 0, 0x4140), __byte_perm(v.y, 0, 0x4342));
+    const uint4 b = make_uint4(__byte_perm(v.z, 0, 0x4140), __byte_perm(v.z, 0, 0x4342),
+                               __byte_perm(v.w, 0, 0x4140), __byte_perm(v.w, 0, 0x4342));
     uint4 *d = reinterpret_cast<uint4 *>(dst) + 2 * lane;
-    d[0] = make_uint4(__byte_perm(v.x, 0, 0x4140), __byte_perm(v.x, 0, 0x4342), __byte_perm(v.y, 0, 0x4140),
-                      __byte_perm(v.y, 0, 0x4342));
-    d[1] = make_uint4(__byte_perm(v.z, 0, 0x4140), __byte_perm(v.z, 0, 0x4342), __byte_perm(v.w, 0, 0x4140),
-                      __byte_perm(v.w, 0, 0x4342));
+    if (((uintptr_t)dst & 31) == 0) {
+      st_global_32B(d, a, b);  // the warp writes its 1 KB in whole sectors
+    } else {
+      d[0] = a;
+      d[1] = b;
+    }
   }
 
   __device__ __forceinline__ static uint32_t count(const Params &p, uint4 v, long long c, bool edge,
@@ -84,15 +100,22 @@ struct Utf8ToUtf16 {
       return 16;
     }
     // per byte, as bit 7: not a continuation byte (10xxxxxx), and >= F0; a byte dot product
-    // with 0x01 weights adds 0x80 per flag (FMA pipe rather than the XU pipe of popc)
-    uint32_t acc = 0;
+    // with 0x01 weights adds 0x80 per flag (FMA pipe rather than the XU pipe of popc).  The
+    // classes of the leading bytes go to the flags.
+    uint32_t acc = 0, c2 = 0, c3 = 0, c4 = 0;
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-      const uint32_t w = W[k], s1 = w << 1;
+      const uint32_t w = W[k], s1 = w << 1, s2 = w << 2, s3 = w << 3;
       const uint32_t vm = edge ? byte_range_mask(c + 4 * k, p.off0, (long long)p.vbytes) : 0x80808080u;
+      const uint32_t ge = w & s1 & vm;  // >= C0
+      const uint32_t f0 = ge & s2 & s3;  // >= F0
       acc = __dp4a((~w | s1) & vm, 0x01010101u, acc);
-      acc = __dp4a(w & s1 & (w << 2) & (w << 3) & vm, 0x01010101u, acc);
+      acc = __dp4a(f0, 0x01010101u, acc);
+      c2 |= ge & ~s2;
+      c3 |= ge & s2 & ~s3;
+      c4 |= f0;
     }
+    flags = F_NONASCII | (c2 ? F_C2 : 0u) | (c3 ? F_C3 : 0u) | (c4 ? F_C4 : 0u);
     return acc >> 7;
   }
 
@@ -106,17 +129,25 @@ struct Utf8ToUtf16 {
   // non-continuation byte stages one word (a four-byte sequence two), which is the count the
   // count pass gave the chunk, so no store needs a bounds test.
   template <bool H2, bool H3, bool H4>
-  __device__ __forceinline__ static uint32_t convert_fast(const uint32_t W[6], const Flags8 f[5], uint16_t *st,
-                                                          uint32_t addr) {
-    // with a single class present, every byte >= C0 is a leading byte of that class
+  __device__ __forceinline__ static uint32_t convert_fast(const uint32_t W[6], uint16_t *st, uint32_t addr) {
+    // with a single class present, every byte >= C0 is a leading byte of that class; without
+    // H4 there is no byte >= F0
     constexpr bool ONE = (int)H2 + (int)H3 + (int)H4 == 1;
+    Flags8 f[5];  // isC for W[1..4]; geC0, and geE0 / geF0 where the variant needs them
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+      const uint32_t w = W[k], s1 = w << 1;
+      f[k].geC0 = w & s1 & 0x80808080u;
+      f[k].isC = w & ~s1 & 0x80808080u;
+      f[k].geE0 = ONE ? f[k].geC0 : f[k].geC0 & (w << 2);
+      f[k].geF0 = ONE ? f[k].geC0 : (H4 ? f[k].geE0 & (w << 3) : 0u);
+    }
     uint32_t bad = 0;
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-      const uint32_t a = f[k].geC0, b = f[k + 1].geC0;
-      uint32_t req = __funnelshift_l(a, b, 8);
-      if (H3 || H4) req |= ONE ? __funnelshift_l(a, b, 16) : __funnelshift_l(f[k].geE0, f[k + 1].geE0, 16);
-      if (H4) req |= ONE ? __funnelshift_l(a, b, 24) : __funnelshift_l(f[k].geF0, f[k + 1].geF0, 24);
+      uint32_t req = __funnelshift_l(f[k].geC0, f[k + 1].geC0, 8);
+      if (H3 || H4) req |= __funnelshift_l(f[k].geE0, f[k + 1].geE0, 16);
+      if (H4) req |= __funnelshift_l(f[k].geF0, f[k + 1].geF0, 24);
       bad |= req ^ f[k + 1].isC;
     }
     if (H2 || H3) bad |= utf8_special_errors(W, H2, H3, false);
@@ -134,17 +165,17 @@ struct Utf8ToUtf16 {
       uint32_t r = E & 0x00FF00FFu;
       uint32_t lo4 = 0;
       if (H2) {
-        const uint32_t M2 = prmt(ONE ? g.geC0 : g.geC0 & ~g.geE0, 0, selM(h));
+        const uint32_t M2 = prmt(ONE ? g.geC0 : g.geC0 & ~g.geE0, 0, selM(h));  // C0-DF
         const uint32_t U2 = (E & 0x001F001Fu) * 64u + (O & 0x003F003Fu);
         r = (U2 & M2) | (r & ~M2);
       }
       if (H3) {
-        const uint32_t M3 = prmt(ONE ? g.geC0 : g.geE0 & ~g.geF0, 0, selM(h));
+        const uint32_t M3 = prmt(H4 && !ONE ? g.geE0 & ~g.geF0 : g.geE0, 0, selM(h));  // E0-EF
         const uint32_t U3 = ((E & 0x000F000Fu) * 64u + (O & 0x003F003Fu)) * 64u + (En & 0x003F003Fu);
         r = (U3 & M3) | (r & ~M3);
       }
       if (H4) {
-        const uint32_t M4 = prmt(ONE ? g.geC0 : g.geF0, 0, selM(h));
+        const uint32_t M4 = prmt(g.geF0, 0, selM(h));  // F0-FF
         // first surrogate: (code point >> 10) + D7C0, from bits of the first three bytes
         const uint32_t hi = (E & 0x001F001Fu) * 256u + (O & 0x003F003Fu) * 4u + ((En >> 4) & 0x00030003u) +
                             0xC7C0C7C0u;
@@ -159,7 +190,7 @@ struct Utf8ToUtf16 {
         const int bit = 16 * h + 8 * q + 7;
         if ((nc >> bit) & 1u) {
           st[addr] = (uint16_t)(r >> (16 * q));
-          if (H4 && (((ONE ? g.geC0 : g.geF0) >> bit) & 1u)) st[++addr] = (uint16_t)(lo4 >> (16 * q));
+          if (H4 && ((g.geF0 >> bit) & 1u)) st[++addr] = (uint16_t)(lo4 >> (16 * q));
           ++addr;
         }
       }
@@ -195,35 +226,22 @@ struct Utf8ToUtf16 {
       stage16(st, base + 16 * lane, u);
       return Region{512u, 0u, 0u, 512u};
     }
-    uint32_t W[6];
-    W[0] = prev;
-    W[1] = v.x; W[2] = v.y; W[3] = v.z; W[4] = v.w;
-    W[5] = next;
-    Flags8 f[5];
-#pragma unroll
-    for (int k = 0; k < 5; ++k) f[k] = classify8(W[k]);
     if (inside && base + rtot <= STAGE) {
-      // the leading-byte classes present in the warp, the word before each chunk included
-      // (a sequence that starts there reaches into the chunk)
-      uint32_t c2 = 0, c3 = 0, c4 = 0;
-#pragma unroll
-      for (int k = 0; k < 5; ++k) {
-        c2 |= f[k].geC0 & ~f[k].geE0;
-        c3 |= f[k].geE0 & ~f[k].geF0;
-        c4 |= f[k].geF0;
-      }
-      const bool h2 = __any_sync(0xffffffffu, c2 != 0);
-      const bool h3 = __any_sync(0xffffffffu, c3 != 0);
-      const bool h4 = __any_sync(0xffffffffu, c4 != 0);
+      const uint32_t W[6] = {prev, v.x, v.y, v.z, v.w, next};
+      // the leading-byte classes: the region's own (from the count pass) and those of bytes
+      // 1-3 of the word before it (a sequence starting there reaches into the region, and the
+      // structure test reads those bytes)
+      const uint32_t pc = lane == 0 ? lead_classes(prev, 0x80808000u) : 0u;
+      const uint32_t cls = rflags | __shfl_sync(0xffffffffu, pc, 0);
+      const bool h2 = cls & F_C2, h3 = cls & F_C3, h4 = cls & F_C4;
       const uint32_t addr = base + x0;
       uint32_t bad;
       if (h4) {
-        bad = (h2 || h3) ? convert_fast<true, true, true>(W, f, st, addr)
-                         : convert_fast<false, false, true>(W, f, st, addr);
+        bad = (h2 || h3) ? convert_fast<true, true, true>(W, st, addr) : convert_fast<false, false, true>(W, st, addr);
       } else if (h3) {
-        bad = h2 ? convert_fast<true, true, false>(W, f, st, addr) : convert_fast<false, true, false>(W, f, st, addr);
+        bad = h2 ? convert_fast<true, true, false>(W, st, addr) : convert_fast<false, true, false>(W, st, addr);
       } else {
-        bad = h2 ? convert_fast<true, false, false>(W, f, st, addr) : convert_fast<true, true, true>(W, f, st, addr);
+        bad = h2 ? convert_fast<true, false, false>(W, st, addr) : convert_fast<true, true, true>(W, st, addr);
       }
       if (bad && (unsigned long long)c < err_pos) err_pos = (unsigned long long)c;
       return Region{rtot, 0u, 0u, rtot};

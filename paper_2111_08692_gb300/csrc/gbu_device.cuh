@@ -205,6 +205,14 @@ __device__ __forceinline__ uint64_t l2_policy_last_use() {
   return pol;
 }
 
+// One 32-byte store (p 32-byte aligned): a warp storing 32 consecutive such blocks writes whole
+// 32-byte sectors in a single instruction.
+__device__ __forceinline__ void st_global_32B(void *p, uint4 a, uint4 b) {
+  asm volatile("st.global.v8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"l"(p), "r"(a.x), "r"(a.y), "r"(a.z),
+               "r"(a.w), "r"(b.x), "r"(b.y), "r"(b.z), "r"(b.w)
+               : "memory");
+}
+
 // 16-byte streaming load with an L2 cache policy
 __device__ __forceinline__ uint4 ldg_stream_hint(const uint8_t *p, uint64_t pol) {
   uint4 v;
