@@ -210,7 +210,7 @@ void gbu_graph_destroy(gbu_graph *graph);
  * outputs come from a device arena of budget_bytes allocated at creation.  Admitted small
  * requests of one operation share ONE batched launch (device descriptors); transcodings of
  * at least large_bytes of one direction share one partitioned launch (each request split into
- * 64 KiB partitions with its own look-back chain, so all SMs work on the group); large
+ * 16 KiB partitions with its own look-back chain, so all SMs work on the group); large
  * validations get single-buffer launches.  Launch groups are spread over `streams`
  * CUDA streams, `groups_per_stream` in flight on each, so newly admitted work overlaps with
  * running work.  Each request's result is the one the single-buffer call gives on it.
@@ -300,7 +300,7 @@ void gbu_arena_destroy(gbu_arena *arena);
  * another allocator already owns the device's memory.  The paper has no counterpart: it is
  * a deployment form of the same Section 3 / Section 5 transcoding, with identical results.
  *
- * The workspace is a static device array of the library (128 B + 8 B per 64 KiB partition),
+ * The workspace is a static device array of the library (128 B + 8 B per 16 KiB partition),
  * sized for n <= GBU_NOALLOC_MAX_UNITS bytes; a larger n returns GBU_NOALLOC_TOO_LARGE and
  * enqueues nothing.  Runs on the CURRENT device.  The first call on each device does a
  * one-time setup there (looks up the array's device address, queries the occupancy, clears
@@ -318,10 +318,13 @@ int gbu_convert_utf8_to_utf16le_noalloc(const uint8_t *src, uint64_t n, uint16_t
 /* Number of kernel launches the library made through this context so far (for accounting). */
 uint64_t gbu_launch_count(const gbu_ctx *ctx);
 
-/* Launch geometry, for diagnostics: writes up to n values into out (host memory): the SM
- * count, then the CTAs per SM of the kernels behind validate_utf8, utf16_length_from_utf8,
+/* Launch geometry, for diagnostics and tests: writes up to n values into out (host memory):
+ * the SM count; the CTAs per SM of the kernels behind validate_utf8, utf16_length_from_utf8,
  * convert_utf8_to_utf16le, validate_utf16le, utf8_length_from_utf16le and
- * convert_utf16le_to_utf8, then the threads per CTA.  Returns the number of values written. */
+ * convert_utf16le_to_utf8; the threads per CTA of the read-only kernels and of the
+ * transcoders; the input bytes per warp tile of the read-only kernels; the input bytes per
+ * transcoder partition (the unit of the look-back).  Returns the number of values written
+ * (at most 11). */
 int gbu_launch_config(const gbu_ctx *ctx, int32_t *out, int n);
 
 #ifdef __cplusplus

@@ -362,7 +362,8 @@ class Codec:
         v = gbu_launch_config(self.ctx)
         names = ("validate_utf8", "utf16_length_from_utf8", "convert_utf8_to_utf16le",
                  "validate_utf16le", "utf8_length_from_utf16le", "convert_utf16le_to_utf8")
-        return {"sms": v[0], "ctas_per_sm": dict(zip(names, v[1:7])), "threads_per_cta": v[7]}
+        return {"sms": v[0], "ctas_per_sm": dict(zip(names, v[1:7])), "threads_per_cta": v[7],
+                "transcoder_threads_per_cta": v[8], "stream_tile_bytes": v[9], "partition_bytes": v[10]}
 
     def set_wait_limit(self, rounds: int):
         gbu_set_wait_limit(self.ctx, rounds)

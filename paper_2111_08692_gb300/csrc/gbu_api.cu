@@ -195,12 +195,15 @@ extern "C" uint64_t gbu_launch_count(const gbu_ctx *c) { return c ? c->launches.
 
 extern "C" int gbu_launch_config(const gbu_ctx *c, int32_t *out, int n) {
   if (!c || !out) return 0;
-  int32_t v[K_COUNT + 3];
+  constexpr int NV = K_COUNT + 5;
+  int32_t v[NV];
   v[0] = c->num_sms;
   for (int k = 0; k < K_COUNT; ++k) v[1 + k] = c->blocks_per_sm[k];
   v[K_COUNT + 1] = gbu::STREAM_THREADS;
   v[K_COUNT + 2] = gbu::XT;
-  const int m = n < K_COUNT + 3 ? n : K_COUNT + 3;
+  v[K_COUNT + 3] = (int32_t)gbu::stream_tile_bytes();
+  v[K_COUNT + 4] = (int32_t)gbu::PART_BYTES;
+  const int m = n < NV ? n : NV;
   for (int i = 0; i < m; ++i) out[i] = v[i];
   return m;
 }

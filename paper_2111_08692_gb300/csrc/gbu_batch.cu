@@ -354,8 +354,7 @@ constexpr uint32_t SCAN_TILE = SCAN_THREADS * SCAN_ITEMS;
 // look-back; the last CTA writes the result {status, total} and resets the workspace.
 __global__ void __launch_bounds__(SCAN_THREADS) scan_u64_kernel(const ScanParams sp) {
   __shared__ unsigned long long warp_tot[SCAN_THREADS / 32 + 1];
-  __shared__ uint32_t scratch[2 * (SCAN_THREADS / 32) + 2];
-  __shared__ unsigned long long sums[SCAN_THREADS / 32];
+  __shared__ LookbackSmem<SCAN_THREADS> lb;
   __shared__ uint32_t ticket;
   __shared__ int is_last;
   const Params &p = sp.lb;
@@ -399,7 +398,7 @@ __global__ void __launch_bounds__(SCAN_THREADS) scan_u64_kernel(const ScanParams
       publish_aggregate(p, t, tile_total, epoch);
       atomicAdd(&p.ws->total, (unsigned long long)tile_total);
     }
-    run += lookback_cta<SCAN_THREADS>(p, t, tile_total, epoch, scratch, sums);
+    run += lookback_cta<SCAN_THREADS>(p, t, tile_total, epoch, lb);
 #pragma unroll
     for (int k = 0; k < SCAN_ITEMS; ++k) {
       if (b0 + k <= sp.count) sp.out[b0 + k] = run;

@@ -3,7 +3,7 @@
 // Two kernel shapes:
 //   * read-only kernels (validation, lengths; gbu_stream.cu) stream 4 KB warp tiles with
 //     16-byte loads, never waiting on another CTA;
-//   * transcoders (gbu_utf8.cu, gbu_utf16.cu) walk 64 KB partitions claimed from a ticket
+//   * transcoders (gbu_utf8.cu, gbu_utf16.cu) walk 16 KB partitions claimed from a ticket
 //     counter.  A CTA counts the output units of partition k+1 (a read from HBM) and
 //     publishes that aggregate before it transcodes partition k (a re-read, normally from
 //     L2).  Partition k's output offset comes from the single-pass decoupled look-back of
@@ -26,12 +26,15 @@
 namespace gbu {
 
 constexpr int STREAM_THREADS = 256;           // threads per CTA of the read-only kernels
-constexpr int XT = 512;                       // threads per CTA of the transcoders
+// Transcoders: small CTAs (4 warps, 8 resident per SM at 64 registers a thread), so that
+// the phases of many CTAs (count pass, look-back, conversion) overlap on each SM.
+constexpr int XT = 128;                       // threads per CTA of the transcoders
 constexpr int XWARPS = XT / 32;
+constexpr int XBLOCKS = 1024 / XT;            // transcoder CTAs resident per SM
 constexpr uint32_t CHUNK = 16;                // input bytes per thread per round
-constexpr uint32_t ROUND_BYTES = XT * CHUNK;  // 8 KB
+constexpr uint32_t ROUND_BYTES = XT * CHUNK;  // 2 KB
 constexpr int PART_ROUNDS = 8;
-constexpr uint32_t PART_BYTES = ROUND_BYTES * PART_ROUNDS;  // 64 KB per partition
+constexpr uint32_t PART_BYTES = ROUND_BYTES * PART_ROUNDS;  // 16 KB per partition
 
 // Scan state word: [63:62] flag, [61:44] epoch, [43:0] value.
 constexpr uint64_t ST_FLAG_AGG = 1ull << 62;
@@ -302,45 +305,75 @@ __device__ __forceinline__ void publish_aggregate(const Params &p, uint32_t part
   st_relaxed_u64(&p.states[part], (part == 0 ? ST_FLAG_INC : ST_FLAG_AGG) | tag | (agg & ST_VALUE_MASK));
 }
 
-// Exclusive prefix of partition `part` by a CTA-wide look-back (NTH threads): each poll
-// reads NTH predecessor states at once, so a look-back that has to sum many aggregates back
-// to the nearest inclusive prefix takes one round trip per NTH states.  Only the states between the partition and
-// the nearest inclusive prefix must have been published.  scratch holds NTH/32 + 2 words.
-// Returns the exclusive prefix (in every thread) and publishes the inclusive prefix.
+// Shared memory of lookback_cta: one record per warp and poll, in two buffers that
+// alternate between polls (so a poll needs a single barrier).
 template <int NTH>
+struct LookbackSmem {
+  uint32_t first[2][NTH / 32];          // first inclusive prefix (low 16 bits), first unpublished
+  unsigned long long sum[2][NTH / 32];  // the warp's states up to its first inclusive prefix
+};
+
+// Exclusive prefix of partition `part` by a CTA-wide look-back (NTH threads): each poll
+// reads NTH x K predecessor states at once (thread t the K states at distances tK+1 ..
+// tK+K), so a look-back that has to sum many aggregates back to the nearest inclusive prefix
+// takes one round trip per NTH x K states.  Only the states between the partition and the
+// nearest inclusive prefix must have been published.  Each lane sums its states up to its
+// first inclusive prefix and notes an unpublished state before it; each warp records its
+// first lane holding an inclusive prefix, its first lane with an unpublished state and the
+// sum of its lanes up to the former; after one barrier every thread combines the records
+// (the sum runs over the warps up to the first one that holds an inclusive prefix).
+// Returns the exclusive prefix (in every thread) and publishes the inclusive prefix.  The
+// caller must pass a barrier between two calls with the same ls.
+template <int NTH, int K = 1>
 __device__ __forceinline__ uint64_t lookback_cta(const Params &p, uint32_t part, uint64_t agg,
-                                                 uint32_t epoch, uint32_t *scratch,
-                                                 unsigned long long *sums) {
+                                                 uint32_t epoch, LookbackSmem<NTH> &ls) {
   constexpr int NW = NTH / 32;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   uint64_t excl = 0;
   if (part == 0) return 0;
   long long pred = (long long)part - 1;
   uint32_t polls = 0;
+  int buf = 0;
   while (true) {
-    const long long idx = pred - (long long)threadIdx.x;
-    uint64_t s = ST_FLAG_INC;  // before partition 0: an inclusive prefix of 0
-    bool ok = true;
-    if (idx >= 0) {
-      s = ld_relaxed_u64(&p.states[idx]);
-      ok = (s >> 62) != 0 && (uint32_t)((s >> ST_EPOCH_SHIFT) & ST_EPOCH_MASK) == epoch;
+    uint64_t s[K];
+#pragma unroll
+    for (int j = 0; j < K; ++j) {
+      const long long idx = pred - (long long)(threadIdx.x * K + j);
+      s[j] = idx >= 0 ? ld_relaxed_u64(&p.states[idx]) : ST_FLAG_INC;  // before partition 0: 0
     }
-    const bool inc = ok && (s >> 62) == 2;
-    // per warp: first thread with an inclusive prefix, first thread not yet published
-    const uint32_t incm = __ballot_sync(0xffffffffu, inc);
-    const uint32_t badm = __ballot_sync(0xffffffffu, !ok);
+    uint64_t lsum = 0;
+    bool linc = false, lbad = false;
+#pragma unroll
+    for (int j = 0; j < K; ++j) {
+      const bool before0 = pred < (long long)(threadIdx.x * K + j);
+      const bool ok = before0 || ((s[j] >> 62) != 0 && (uint32_t)((s[j] >> ST_EPOCH_SHIFT) & ST_EPOCH_MASK) == epoch);
+      if (!linc) {
+        lbad = lbad || !ok;
+        lsum += s[j] & ST_VALUE_MASK;
+        linc = ok && (s[j] >> 62) == 2;
+      }
+    }
+    const uint32_t incm = __ballot_sync(0xffffffffu, linc);
+    const uint32_t badm = __ballot_sync(0xffffffffu, lbad);
+    const int li = incm ? __ffs(incm) - 1 : 32;  // the warp's first lane with an inclusive prefix
+    const uint64_t v = warp_sum_u64(lane <= li ? lsum : 0ull);
     if (lane == 0) {
-      scratch[warp] = incm ? (uint32_t)(warp * 32 + __ffs(incm) - 1) : 0xFFFFu;
-      scratch[NW + warp] = badm ? (uint32_t)(warp * 32 + __ffs(badm) - 1) : 0xFFFFu;
+      const uint32_t fi = incm ? (uint32_t)(warp * 32 + li) : 0xFFFFu;
+      const uint32_t fb = badm ? (uint32_t)(warp * 32 + __ffs(badm) - 1) : 0xFFFFu;
+      ls.first[buf][warp] = fi | (fb << 16);
+      ls.sum[buf][warp] = v;
     }
     __syncthreads();
     uint32_t first_inc = 0xFFFFu, first_bad = 0xFFFFu;
+    uint64_t t = 0;
 #pragma unroll
     for (int w = 0; w < NW; ++w) {
-      first_inc = scratch[w] < first_inc ? scratch[w] : first_inc;
-      first_bad = scratch[NW + w] < first_bad ? scratch[NW + w] : first_bad;
+      const uint32_t f = ls.first[buf][w];
+      if (first_inc == 0xFFFFu) t += ls.sum[buf][w];  // warps up to the first inclusive prefix
+      first_inc = (f & 0xFFFFu) < first_inc ? (f & 0xFFFFu) : first_inc;
+      first_bad = (f >> 16) < first_bad ? (f >> 16) : first_bad;
     }
-    __syncthreads();
+    buf ^= 1;
     if (first_bad <= first_inc && first_bad != 0xFFFFu) {
       // a state we need is not published yet: poll again (bounded; the count is the same in
       // every thread, so all of them leave together)
@@ -351,18 +384,9 @@ __device__ __forceinline__ uint64_t lookback_cta(const Params &p, uint32_t part,
       __nanosleep(64);
       continue;
     }
-    // sum the states up to and including the nearest inclusive prefix
-    uint64_t v = threadIdx.x <= first_inc ? (s & ST_VALUE_MASK) : 0ull;
-    v = warp_sum_u64(v);
-    if (lane == 0) sums[warp] = v;
-    __syncthreads();
-    uint64_t t = 0;
-#pragma unroll
-    for (int w = 0; w < NW; ++w) t += sums[w];
-    __syncthreads();
     excl += t;
     if (first_inc != 0xFFFFu) break;
-    pred -= NTH;
+    pred -= (long long)NTH * K;
   }
   if (threadIdx.x == 0 && (long long)part != p.skip_tile) {
     const uint64_t tag = (uint64_t)epoch << ST_EPOCH_SHIFT;

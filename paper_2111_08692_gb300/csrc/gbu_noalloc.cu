@@ -25,7 +25,7 @@
 
 namespace {
 
-// Partition states the workspace holds: one per 64 KiB partition of the input, the input's
+// Partition states the workspace holds: one per partition (PART_BYTES) of the input, the input's
 // first byte sitting anywhere in a 16-byte word and the three positions past its end being
 // judged too.
 constexpr uint32_t NOALLOC_STATES = (uint32_t)(GBU_NOALLOC_MAX_UNITS / gbu::PART_BYTES) + 1u;
@@ -36,7 +36,8 @@ static_assert(sizeof(gbu::WsHeader) % 8 == 0, "header must keep the states 8-byt
 
 constexpr size_t NOALLOC_WORDS = sizeof(gbu::WsHeader) / 8 + NOALLOC_STATES;
 
-// [WsHeader][NOALLOC_STATES tile states]: 128 B + 32 KiB.
+// [WsHeader][NOALLOC_STATES tile states]: 128 B + 8 B per partition (128 KiB for 16 KiB
+// partitions and 256 MiB of input).
 static __device__ __align__(256) uint64_t noalloc_scratch[NOALLOC_WORDS];
 
 constexpr int MAX_DEVICES = 64;

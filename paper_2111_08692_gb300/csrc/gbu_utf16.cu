@@ -7,7 +7,7 @@
 
 namespace gbu {
 
-__global__ void __launch_bounds__(XT, 2) utf16_to_utf8_kernel(const Params p) {
+__global__ void __launch_bounds__(XT, XBLOCKS) utf16_to_utf8_kernel(const Params p) {
   extern __shared__ __align__(128) unsigned char smem_raw[];  // sizeof(XSmem), set at launch
   XSmem<Utf16ToUtf8> &sm = *reinterpret_cast<XSmem<Utf16ToUtf8> *>(smem_raw);
   transcode<Utf16ToUtf8>(p, sm, [&](uint32_t status, unsigned long long key, unsigned long long tot) {
@@ -25,7 +25,7 @@ __global__ void __launch_bounds__(XT, 2) utf16_to_utf8_kernel(const Params p) {
 }
 
 // Several strings per launch (the serving loop's large requests): one result per string.
-__global__ void __launch_bounds__(XT, 2) utf16_to_utf8_segments_kernel(const SegParams q) {
+__global__ void __launch_bounds__(XT, XBLOCKS) utf16_to_utf8_segments_kernel(const SegParams q) {
   extern __shared__ __align__(128) unsigned char smem_raw[];  // sizeof(XSmem), set at launch
   XSmem<Utf16ToUtf8> &sm = *reinterpret_cast<XSmem<Utf16ToUtf8> *>(smem_raw);
   transcode_segments<Utf16ToUtf8>(q, sm, [&](const Params &p, const SegState &st, uint32_t) {

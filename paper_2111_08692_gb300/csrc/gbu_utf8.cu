@@ -7,7 +7,7 @@
 
 namespace gbu {
 
-__global__ void __launch_bounds__(XT, 2) utf8_to_utf16_kernel(const Params p) {
+__global__ void __launch_bounds__(XT, XBLOCKS) utf8_to_utf16_kernel(const Params p) {
   extern __shared__ __align__(128) unsigned char smem_raw[];  // sizeof(XSmem), set at launch
   XSmem<Utf8ToUtf16> &sm = *reinterpret_cast<XSmem<Utf8ToUtf16> *>(smem_raw);
   transcode<Utf8ToUtf16>(p, sm, [&](uint32_t status, unsigned long long key, unsigned long long tot) {
@@ -25,7 +25,7 @@ __global__ void __launch_bounds__(XT, 2) utf8_to_utf16_kernel(const Params p) {
 }
 
 // Several strings per launch (the serving loop's large requests): one result per string.
-__global__ void __launch_bounds__(XT, 2) utf8_to_utf16_segments_kernel(const SegParams q) {
+__global__ void __launch_bounds__(XT, XBLOCKS) utf8_to_utf16_segments_kernel(const SegParams q) {
   extern __shared__ __align__(128) unsigned char smem_raw[];  // sizeof(XSmem), set at launch
   XSmem<Utf8ToUtf16> &sm = *reinterpret_cast<XSmem<Utf8ToUtf16> *>(smem_raw);
   transcode_segments<Utf8ToUtf16>(q, sm, [&](const Params &p, const SegState &st, uint32_t) {

@@ -1,11 +1,11 @@
 // gbu_xcode.cuh -- the partition loop shared by both transcoders.
 //
-// A CTA of XT threads (XWARPS warps) claims 64 KB partitions from a ticket counter.  Warp w
+// A CTA of XT threads (XWARPS warps) claims 16 KB partitions from a ticket counter.  Warp w
 // owns the partition's w-th 4 KB slice and walks it in eight 512-byte regions (one 16-byte
 // chunk per lane per region), so a chunk's neighbouring words come from the adjacent lane,
 // or from the previous / next region's registers.  For every partition the CTA
 //   1. counts the output units of each region of the NEXT partition (a read from HBM), turns
-//      the 128 region counts into region offsets inside that partition, and publishes the
+//      the region counts (32 per partition) into region offsets inside it, and publishes the
 //      partition total as its aggregate -- a whole partition before any look-back needs it;
 //   2. gets the CURRENT partition's output offset from a CTA-wide decoupled look-back;
 //   3. transcodes the current partition (a re-read, normally from L2): every warp handles its
@@ -56,7 +56,7 @@ struct Region {
   uint32_t units;  // units counted for the region (unclamped: the region's output length)
 };
 
-constexpr int PART_REGIONS = PART_ROUNDS * XWARPS;  // 128 regions per partition
+constexpr int PART_REGIONS = PART_ROUNDS * XWARPS;  // 32 regions per partition
 
 struct __align__(16) PartCounts {
   uint32_t off[PART_REGIONS];           // region offsets inside the partition, in byte order
@@ -70,8 +70,7 @@ template <class Codec>
 struct __align__(128) XSmem {
   typename Codec::Out staging[XWARPS][2][Codec::STAGE];
   PartCounts counts[2];
-  uint32_t scratch[2 * XWARPS + 2];
-  unsigned long long sums[XWARPS];
+  LookbackSmem<XT> lb;
   unsigned long long red[XWARPS];
   uint32_t ticket;
   int is_last;
@@ -140,11 +139,14 @@ __device__ __forceinline__ void count_partition(const Params &p, uint32_t part, 
   }
   __syncthreads();
   if (warp == 0) {
-    constexpr int PER = PART_REGIONS / 32;  // consecutive values per lane
+    // consecutive values per lane (one per lane, and none past the last region, when the
+    // partition has at most 32 regions)
+    constexpr int PER = PART_REGIONS >= 32 ? PART_REGIONS / 32 : 1;
+    static_assert(PART_REGIONS < 32 || PART_REGIONS % 32 == 0, "regions per partition");
     uint32_t vals[PER], s = 0;
 #pragma unroll
     for (int i = 0; i < PER; ++i) {
-      vals[i] = pc.off[lane * PER + i];
+      vals[i] = lane * PER + i < PART_REGIONS ? pc.off[lane * PER + i] : 0u;
       s += vals[i];
     }
     uint32_t incl = s;
@@ -156,7 +158,7 @@ __device__ __forceinline__ void count_partition(const Params &p, uint32_t part, 
     uint32_t run = incl - s;
 #pragma unroll
     for (int i = 0; i < PER; ++i) {
-      pc.off[lane * PER + i] = run;
+      if (lane * PER + i < PART_REGIONS) pc.off[lane * PER + i] = run;
       run += vals[i];
     }
     if (lane == 31) pc.total = incl;
@@ -353,7 +355,7 @@ __device__ __forceinline__ void transcode(const Params &p, XSmem<Codec> &sm, Fin
         atomicAdd(&p.ws->total, (unsigned long long)sm.counts[cb ^ 1].total);
       }
     }
-    const uint64_t S0 = lookback_cta<XT>(p, cur, sm.counts[cb].total, epoch, sm.scratch, sm.sums);
+    const uint64_t S0 = lookback_cta<XT>(p, cur, sm.counts[cb].total, epoch, sm.lb);
 
     convert_part<Codec>(p, cur, sm.counts[cb], S0, sm, use, err_pos);
     cur = nxt;
@@ -462,7 +464,7 @@ __device__ __forceinline__ void transcode_segments(const SegParams &q, XSmem<Cod
     const Params &p = sm.prm[cb];
     const uint32_t s = sm.sid[cb];
     const uint32_t lc = cur - q.pstart[s];
-    const uint64_t S0 = lookback_cta<XT>(p, lc, sm.counts[cb].total, epoch, sm.scratch, sm.sums);
+    const uint64_t S0 = lookback_cta<XT>(p, lc, sm.counts[cb].total, epoch, sm.lb);
     convert_part<Codec>(p, lc, sm.counts[cb], S0, sm, use, err_pos);
     if (err_pos != NO_ERROR) {  // rare: this thread saw an error in the partition
       atomicMin(&q.seg[s].errkey, err_pos);

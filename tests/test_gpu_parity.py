@@ -13,9 +13,10 @@ from gpu_helpers import char_starts_utf8, check_utf16_input, check_utf8_input
 
 pytestmark = pytest.mark.gpu
 
-TILE = 4096    # bytes per streaming warp tile
-TTILE = 8192   # bytes per transcoder round (512-byte regions per warp)
-PART = 65536   # bytes per transcoder partition (the unit of the look-back)
+# The kernels' geometry, read from the library by the `geometry` fixture: bytes per streaming
+# warp tile (TILE), per transcoder round (one 512-byte region per warp, TTILE) and per
+# transcoder partition (the unit of the look-back, PART).
+TILE = TTILE = PART = None
 
 
 @pytest.fixture(scope="module")
@@ -32,6 +33,11 @@ def codec(torch):
     from paper_2111_08692_gb300.build import build
     build()
     c = Codec(0, max_units=(1 << 30) + 4096)
+    g = c.launch_config()
+    global TILE, TTILE, PART
+    TILE = g["stream_tile_bytes"]
+    TTILE = g["transcoder_threads_per_cta"] * 16
+    PART = g["partition_bytes"]
     yield c
     c.close()
 
@@ -104,11 +110,11 @@ INVALID_UTF8 = [bytes.fromhex(h) for h in (
 
 
 def test_errors_near_tile_and_warp_boundaries(codec, torch):
-    base = _mixed(PART + 2 * TILE, 3)
+    base = _mixed(max(3 * PART, 5 * TILE) + 2 * TILE, 3)
     starts = char_starts_utf8(base)
     targets = []
     for b in (TILE, 2 * TILE, 3 * TILE, 512, 1024 + 512, 5 * TILE, TTILE + 16, 2 * TTILE - 16,
-              PART, PART + 512):
+              PART, PART + 512, 2 * PART, 3 * PART - 512):
         targets += [b - 5, b - 4, b - 3, b - 2, b - 1, b, b + 1, b + 2, b + 3]
     targets += [0, 1, 2, 15, 16, 17]
     for t in targets:
