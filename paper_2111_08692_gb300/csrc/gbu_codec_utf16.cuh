@@ -40,26 +40,24 @@ struct Utf16ToUtf8 {
   // (0x80 per flag), which run on the FMA pipe.
   __device__ __forceinline__ static uint32_t count_inside(const uint32_t W[4], uint32_t *sur_any,
                                                          uint32_t *ge800_any) {
-    uint32_t acc = 0, sub = 0, sa = 0, g3 = 0;
+    uint32_t a80 = 0, a800 = 0, sub = 0;
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-      const uint32_t sr = lanes16_sur(W[k]);
-      const uint32_t t = lanes16_ge800(W[k]);
-      acc = __dp4a(lanes16_ge80(W[k]), 0x01000100u, acc);
-      acc = __dp4a(t, 0x01000100u, acc);
-      sub = __dp4a(sr, 0x01000100u, sub);
-      sa |= sr;
-      g3 |= t;
+      a80 = __dp4a(lanes16_ge80(W[k]), 0x01000100u, a80);
+      a800 = __dp4a(lanes16_ge800(W[k]), 0x01000100u, a800);
+      sub = __dp4a(lanes16_sur(W[k]), 0x01000100u, sub);
     }
-    *sur_any = sa;
-    *ge800_any = g3;
-    return 8u + ((acc - sub) >> 7);
+    *sur_any = sub;  // the sums double as the "any" flags
+    *ge800_any = a800;
+    return 8u + ((a80 + a800 - sub) >> 7);
   }
 
   // Flag bits of a chunk (and, ORed over the lanes, of a region).
   static constexpr uint32_t F_SUR = 1;     // a surrogate word (or a chunk at a buffer end)
   static constexpr uint32_t F_THREE = 2;   // a word of three UTF-8 bytes (>= 0x800)
 
+  static constexpr uint32_t ASCII_MASK = 0xFF80FF80u;  // nonzero in a word: a word >= 0x80
+  static constexpr uint32_t CHUNK_UNITS = 8;            // bytes out of an all-ASCII chunk
   static constexpr uint32_t REGION_UNITS = 256;  // bytes out of an all-ASCII region
   static constexpr uint32_t DIRECT_ALIGN = 8;    // its lanes store 8 bytes each
 

@@ -60,6 +60,8 @@ struct Utf8ToUtf16 {
     return ((ge & ~s2) ? F_C2 : 0u) | ((ge & s2 & ~s3) ? F_C3 : 0u) | ((ge & s2 & s3) ? F_C4 : 0u);
   }
 
+  static constexpr uint32_t ASCII_MASK = 0x80808080u;  // nonzero in a word: a byte >= 0x80
+  static constexpr uint32_t CHUNK_UNITS = 16;           // words out of an all-ASCII chunk
   static constexpr uint32_t REGION_UNITS = 512;  // words out of an all-ASCII region
   static constexpr uint32_t DIRECT_ALIGN = 8;    // its lanes store 16 words (32 bytes) each
 

@@ -149,11 +149,31 @@ __device__ __forceinline__ void bulk_store(void *dst_gmem, const void *src_smem,
 __device__ __forceinline__ void bulk_commit() {
   asm volatile("cp.async.bulk.commit_group;" ::: "memory");
 }
+// The same three operations issued only where `pred` holds, as predicated instructions (no
+// branch around them).
+__device__ __forceinline__ void bulk_store_if(bool pred, void *dst_gmem, const void *src_smem, uint32_t bytes) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %3, 0;\n\t"
+      "@p cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;\n\t}" ::"l"(dst_gmem),
+      "r"(smem_addr(src_smem)), "r"(bytes), "r"((uint32_t)pred)
+      : "memory");
+}
+__device__ __forceinline__ void bulk_commit_if(bool pred) {
+  asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %0, 0;\n\t@p cp.async.bulk.commit_group;\n\t}" ::"r"(
+                   (uint32_t)pred)
+               : "memory");
+}
 
 // wait until at most N committed bulk groups still read shared memory
 template <int N>
 __device__ __forceinline__ void bulk_wait_read() {
   asm volatile("cp.async.bulk.wait_group.read %0;" ::"n"(N) : "memory");
+}
+template <int N>
+__device__ __forceinline__ void bulk_wait_read_if(bool pred) {
+  asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %1, 0;\n\t@p cp.async.bulk.wait_group.read %0;\n\t}" ::"n"(N),
+               "r"((uint32_t)pred)
+               : "memory");
 }
 
 template <int N>

@@ -64,6 +64,7 @@ struct __align__(16) PartCounts {
   uint16_t rtot[PART_REGIONS];          // region totals
   uint8_t flags[PART_REGIONS];          // OR of the codec flags of the region's lanes
   uint32_t total;
+  uint32_t all_ascii;                   // the partition lies inside the buffer and is all ASCII
 };
 
 template <class Codec>
@@ -101,40 +102,59 @@ __device__ __forceinline__ void count_partition(const Params &p, uint32_t part, 
 #pragma unroll
   for (int r = 0; r < PART_ROUNDS; ++r)
     v[r] = load_chunk_hint(p, chunk_pos(part, warp, r, lane), inside, keep);
+  bool slice_ascii = false;
+  if (INSIDE) {
+    uint32_t any = 0;
 #pragma unroll
-  for (int r = 0; r < PART_ROUNDS; r += 2) {
-    uint32_t a[2], f[2];
+    for (int r = 0; r < PART_ROUNDS; ++r) any |= v[r].x | v[r].y | v[r].z | v[r].w;
+    slice_ascii = __all_sync(0xffffffffu, (any & Codec::ASCII_MASK) == 0);
+  }
+  if (slice_ascii) {
+    // an all-ASCII slice: every chunk gives CHUNK_UNITS units, no scan needed
 #pragma unroll
-    for (int q = 0; q < 2; ++q) {
-      const long long c = chunk_pos(part, warp, r + q, lane);
-      const bool edge = !inside && (c < lo || c + 16 > hi);
-      a[q] = Codec::count(p, v[r + q], c, edge, f[q]);
+    for (int r = 0; r < PART_ROUNDS; ++r)
+      pc.lane_off[warp * PART_ROUNDS + r][lane] = (uint16_t)(lane * Codec::CHUNK_UNITS);
+    if (lane < PART_ROUNDS) {
+      pc.off[warp * PART_ROUNDS + lane] = Codec::REGION_UNITS;
+      pc.rtot[warp * PART_ROUNDS + lane] = (uint16_t)Codec::REGION_UNITS;
+      pc.flags[warp * PART_ROUNDS + lane] = 0;
     }
-    const uint32_t x = a[0] | (a[1] << 16);
-    uint32_t incl;
-    const uint32_t x_first = __shfl_sync(0xffffffffu, x, 0);
-    if (__all_sync(0xffffffffu, x == x_first)) {
-      incl = x * (uint32_t)(lane + 1);  // equal counts (all-ASCII regions): no scan needed
-    } else {
-      incl = x;
+  } else {
 #pragma unroll
-      for (int d = 1; d < 32; d <<= 1) {
-        const uint32_t y = __shfl_up_sync(0xffffffffu, incl, d);
-        if (lane >= d) incl += y;
+    for (int r = 0; r < PART_ROUNDS; r += 2) {
+      uint32_t a[2], f[2];
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        const long long c = chunk_pos(part, warp, r + q, lane);
+        const bool edge = !inside && (c < lo || c + 16 > hi);
+        a[q] = Codec::count(p, v[r + q], c, edge, f[q]);
       }
-    }
-    const uint32_t ex = incl - x;
-    const int ri = warp * PART_ROUNDS + r;
-    pc.lane_off[ri][lane] = (uint16_t)(ex & 0xFFFFu);
-    pc.lane_off[ri + 1][lane] = (uint16_t)(ex >> 16);
-    const uint32_t fr0 = __reduce_or_sync(0xffffffffu, f[0]), fr1 = __reduce_or_sync(0xffffffffu, f[1]);
-    if (lane == 31) {
-      pc.off[ri] = incl & 0xFFFFu;
-      pc.off[ri + 1] = incl >> 16;
-      pc.rtot[ri] = (uint16_t)(incl & 0xFFFFu);
-      pc.rtot[ri + 1] = (uint16_t)(incl >> 16);
-      pc.flags[ri] = (uint8_t)fr0;
-      pc.flags[ri + 1] = (uint8_t)fr1;
+      const uint32_t x = a[0] | (a[1] << 16);
+      uint32_t incl;
+      const uint32_t x_first = __shfl_sync(0xffffffffu, x, 0);
+      if (__all_sync(0xffffffffu, x == x_first)) {
+        incl = x * (uint32_t)(lane + 1);  // equal counts (all-ASCII regions): no scan needed
+      } else {
+        incl = x;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+          const uint32_t y = __shfl_up_sync(0xffffffffu, incl, d);
+          if (lane >= d) incl += y;
+        }
+      }
+      const uint32_t ex = incl - x;
+      const int ri = warp * PART_ROUNDS + r;
+      pc.lane_off[ri][lane] = (uint16_t)(ex & 0xFFFFu);
+      pc.lane_off[ri + 1][lane] = (uint16_t)(ex >> 16);
+      const uint32_t fr0 = __reduce_or_sync(0xffffffffu, f[0]), fr1 = __reduce_or_sync(0xffffffffu, f[1]);
+      if (lane == 31) {
+        pc.off[ri] = incl & 0xFFFFu;
+        pc.off[ri + 1] = incl >> 16;
+        pc.rtot[ri] = (uint16_t)(incl & 0xFFFFu);
+        pc.rtot[ri + 1] = (uint16_t)(incl >> 16);
+        pc.flags[ri] = (uint8_t)fr0;
+        pc.flags[ri + 1] = (uint8_t)fr1;
+      }
     }
   }
   __syncthreads();
@@ -156,12 +176,21 @@ __device__ __forceinline__ void count_partition(const Params &p, uint32_t part, 
       if (lane >= d) incl += y;
     }
     uint32_t run = incl - s;
+    bool ascii = INSIDE;
 #pragma unroll
     for (int i = 0; i < PER; ++i) {
-      if (lane * PER + i < PART_REGIONS) pc.off[lane * PER + i] = run;
+      const int ri = lane * PER + i;
+      if (ri < PART_REGIONS) {
+        pc.off[ri] = run;
+        ascii = ascii && Codec::ascii_region(vals[i], pc.flags[ri]);
+      }
       run += vals[i];
     }
-    if (lane == 31) pc.total = incl;
+    ascii = __all_sync(0xffffffffu, ascii);
+    if (lane == 31) {
+      pc.total = incl;
+      pc.all_ascii = ascii ? 1u : 0u;
+    }
   }
   __syncthreads();
 }
@@ -185,14 +214,14 @@ __device__ __forceinline__ void store_staged(U *gdst, const U *staging, uint32_t
   const uint32_t head_end = (beg + V - 1) & ~(V - 1);  // first 16-byte boundary at or after beg
   const uint32_t tail_beg = end & ~(V - 1);            // last 16-byte boundary at or before end
   if (head_end < tail_beg) {
-    if (lane == 0) bulk_store(gdst + head_end, staging + head_end, (tail_beg - head_end) * 16u / V);
+    bulk_store_if(lane == 0, gdst + head_end, staging + head_end, (tail_beg - head_end) * 16u / V);
     // the ragged ends hold fewer than V <= 16 units each
     if (beg + lane < head_end) gdst[beg + lane] = staging[beg + lane];
     if (tail_beg + lane < end) gdst[tail_beg + lane] = staging[tail_beg + lane];
   } else if (beg + lane < end) {  // fewer than 2V <= 32 units
     gdst[beg + lane] = staging[beg + lane];
   }
-  if (lane == 0) bulk_commit();
+  bulk_commit_if(lane == 0);
 }
 
 // store_staged for a region whose output starts at global unit S of the buffer p describes.
@@ -251,17 +280,31 @@ __device__ __forceinline__ void convert_partition(const Params &p, uint32_t part
   const uint32_t after =
       slice_inside ? ldg_word(p.base + s0 + SLICE_BYTES) : load_word_checked(p, s0 + SLICE_BYTES);
   const uint64_t last_use = l2_policy_last_use();
-  // two regions in flight ahead of the one being converted (the convert pass reads from L2)
   const uint8_t *const src = p.base + s0 + CHUNK * lane;  // the lane's chunk of the first region
-  uint4 v_next = load_chunk_hint(p, s0 + CHUNK * lane, slice_inside, last_use);
-  uint4 v_next2 = load_chunk_hint(p, s0 + REGION_BYTES + CHUNK * lane, slice_inside, last_use);
-  uint32_t prev_last = before;  // last word of the previous region (lane 31's), for lane 0
   // the partition's output: its first unit counted from the 16-byte-rounded destination base,
   // and the units the destination holds from there on (clamped to 32 bits)
   const uint64_t D0 = p.dshift + S0;
   const uint64_t room64 = p.cap > S0 ? p.cap - S0 : 0;
   const uint32_t room0 = room64 < 0xFFFFFFFFull ? (uint32_t)room64 : 0xFFFFFFFFu;
   Out *const dpart = reinterpret_cast<Out *>(p.dbase) + D0;
+  if (INSIDE && pc.all_ascii && ((uint32_t)D0 & (Codec::DIRECT_ALIGN - 1)) == 0 &&
+      room0 >= (uint32_t)PART_REGIONS * Codec::REGION_UNITS) {
+    // an all-ASCII partition whose output is aligned and fits: every region goes straight
+    // to global memory (no offsets, shuffles or staging); only the word before the slice
+    // can hold a leading byte that wants continuation bytes in it
+    uint4 w[PART_ROUNDS];
+#pragma unroll
+    for (int r = 0; r < PART_ROUNDS; ++r) w[r] = ldg_stream_hint(src + r * REGION_BYTES, last_use);
+#pragma unroll
+    for (int r = 0; r < PART_ROUNDS; ++r)
+      Codec::ascii_direct(dpart + (warp * PART_ROUNDS + r) * Codec::REGION_UNITS, w[r], r == 0 ? before : 0u,
+                          s0 + (long long)r * REGION_BYTES + CHUNK * lane, err_pos);
+    return;
+  }
+  // two regions in flight ahead of the one being converted (the convert pass reads from L2)
+  uint4 v_next = load_chunk_hint(p, s0 + CHUNK * lane, slice_inside, last_use);
+  uint4 v_next2 = load_chunk_hint(p, s0 + REGION_BYTES + CHUNK * lane, slice_inside, last_use);
+  uint32_t prev_last = before;  // last word of the previous region (lane 31's), for lane 0
 #pragma unroll 1
   for (int r = 0; r < PART_ROUNDS; ++r) {
     const long long c = s0 + (long long)r * REGION_BYTES + CHUNK * lane;
@@ -295,7 +338,7 @@ __device__ __forceinline__ void convert_partition(const Params &p, uint32_t part
     ++use;
     const uint32_t x0 = pc.lane_off[ri][lane];
     const uint32_t h = dlo & (V - 1);
-    if (lane == 0) bulk_wait_read<1>();  // the store of two regions ago has read this buffer
+    bulk_wait_read_if<1>(lane == 0);  // the store of two regions ago has read this buffer
     __syncwarp();
     const Region g = Codec::convert(p, v, prev, next, c, edge, rin, st, h, x0, rtot, rflags, err_pos);
     fence_proxy_async_smem();
