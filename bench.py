@@ -49,6 +49,9 @@ def parse():
     ap.add_argument("--batched-steps", type=int, default=10)
     ap.add_argument("--loop-sample", type=int, default=3000,
                     help="strings timed through the per-string launch loop")
+    ap.add_argument("--no-sweep", action="store_true")
+    ap.add_argument("--sweep-size", type=int, default=256 << 20, help="UTF-8 bytes per invalid-input sweep buffer")
+    ap.add_argument("--sweep-reps", type=int, default=5)
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--serving-loads", default="1e4,3e4,1e5,3e5,1e6", help="offered loads, requests/s")
     ap.add_argument("--serving-requests", type=int, default=20000, help="requests per offered load (at most)")
@@ -200,6 +203,8 @@ def run_ours(args):
     import workloads as W
     if local_rank == 0:
         W.prepare_single_buffers(profiles, args.size)  # spawn pool, before any CUDA work
+        if not args.no_sweep:
+            W.prepare_sweeps(args.sweep_size)
     import numpy as np
     import torch
     dist = None
@@ -342,6 +347,8 @@ def run_ours(args):
         line["e2e"] = run_e2e(args, codec, bufs, stream, dist, world, call)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(bufs, args.cpu_sample)
+    if not args.no_sweep:
+        line["sweep"] = run_sweep(args, codec, dev)
     if not args.no_batched and args.batched_strings > 0:
         line["batched"] = run_batched(args, codec, dev, dist, world)
     if not args.no_serving:
@@ -351,6 +358,58 @@ def run_ours(args):
     codec.close()
     if dist:
         dist.destroy_process_group()
+
+
+def run_sweep(args, codec, dev):
+    """The invalid-input sweep: Cyrillic and CJK buffers (sweep_size UTF-8 bytes, half as many
+    UTF-16 words) with errors at per-character rates 1e-6, 1e-4 and 1e-2.  Each validating
+    operation is timed (CUDA events, mean of sweep_reps launches after one untimed) with early
+    exit on -- the default, which stops work past the first flagged chunk -- and off (a full
+    scan); both give the same first error, which is reported."""
+    import numpy as np
+    import torch
+    import workloads as W
+    from paper_2111_08692_gb300 import result_tuple
+    stream = torch.cuda.current_stream(dev)
+    out = {"buffer_bytes": args.sweep_size, "reps": args.sweep_reps, "unit": "ms per launch",
+           "ops": {}}
+    for prof in W.SWEEP_PROFILES:
+        for rate in W.SWEEP_RATES:
+            d = W.sweep_buffers(prof, rate, args.sweep_size)
+            s8 = torch.from_numpy(np.asarray(d["u8"])).to(dev)
+            s16 = torch.from_numpy(np.asarray(d["u16"]).view(np.int16)).to(dev)
+            d16 = torch.empty(s8.numel() + 8, dtype=torch.int16, device=dev)
+            d8 = torch.empty(3 * s16.numel() + 8, dtype=torch.uint8, device=dev)
+            res = torch.empty(2, dtype=torch.int64, device=dev)
+            calls = {"validate_utf8": lambda: codec.validate_utf8(s8, result=res),
+                     "convert_utf8_to_utf16le": lambda: codec.convert_utf8_to_utf16le(s8, d16, result=res),
+                     "validate_utf16le": lambda: codec.validate_utf16le(s16, result=res),
+                     "convert_utf16le_to_utf8": lambda: codec.convert_utf16le_to_utf8(s16, d8, result=res)}
+            for op, fn in calls.items():
+                rec = {}
+                for mode in ("early_exit", "full_scan"):
+                    codec.set_early_exit(mode == "early_exit")
+                    fn()
+                    torch.cuda.synchronize()
+                    first = result_tuple(res)
+                    e0 = torch.cuda.Event(enable_timing=True)
+                    e1 = torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    for _ in range(args.sweep_reps):
+                        fn()
+                    e1.record(stream)
+                    torch.cuda.synchronize()
+                    assert result_tuple(res) == first
+                    rec[mode + "_ms"] = round(e0.elapsed_time(e1) / args.sweep_reps, 4)
+                    rec[mode + "_result"] = list(first)
+                assert rec["early_exit_result"] == rec["full_scan_result"], (prof, rate, op, rec)
+                rec["first_error"] = rec.pop("early_exit_result")
+                del rec["full_scan_result"]
+                out["ops"].setdefault(op, {}).setdefault(prof, {})[f"{rate:g}"] = rec
+            codec.set_early_exit(True)
+            del s8, s16, d16, d8
+            torch.cuda.empty_cache()
+    return out
 
 
 def run_batched(args, codec, dev, dist, world):
@@ -650,9 +709,47 @@ def cpu_baseline(bufs, sample):
         o.convert_utf16le_to_utf8(a16)
         nbytes += 3 * a8.size + 3 * 2 * a16.size
     dt = time.perf_counter() - t
-    return {"value": round(nbytes / dt / 1e9, 3), "unit": "GB/s", "cores": 1, "kind": "oracle",
-            "sample": f"first {sample >> 20} MiB of each profile's UTF-8 and UTF-16 buffer, the same six "
-                      f"operations, single thread ({dt:.1f} s)"}
+    out = {"value": round(nbytes / dt / 1e9, 3), "unit": "GB/s", "cores": 1, "kind": "oracle",
+           "sample": f"first {sample >> 20} MiB of each profile's UTF-8 and UTF-16 buffer, the same six "
+                     f"operations, single thread ({dt:.1f} s)"}
+    out["all_cores"] = cpu_baseline_all_cores(o, work)
+    return out
+
+
+def cpu_baseline_all_cores(o, work):
+    """The same work on every host core: each buffer is split into as many shards as cores at
+    character boundaries (the library's host cut function), the reference codec runs on the
+    shards in parallel threads (its calls release the interpreter lock), and the shards'
+    results are combined with gbu_combine_shards."""
+    import concurrent.futures as cf
+    from paper_2111_08692_gb300 import combine_shards, shard_cuts_host
+    cores = os.cpu_count() or 1
+    jobs = []
+    for a8, a16 in work:
+        c8, c16 = shard_cuts_host(a8, cores), shard_cuts_host(a16, cores)
+        jobs.append((a8, c8, [a8[int(c8[k]):int(c8[k + 1])] for k in range(cores)],
+                     a16, c16, [a16[int(c16[k]):int(c16[k + 1])] for k in range(cores)]))
+
+    def shard8(s):
+        return (o.validate_utf8(s), o.utf16_length_from_utf8(s), o.convert_utf8_to_utf16le(s)[0])
+
+    def shard16(s):
+        return (o.validate_utf16le(s), o.utf8_length_from_utf16le(s), o.convert_utf16le_to_utf8(s)[0])
+
+    with cf.ThreadPoolExecutor(max_workers=cores) as ex:
+        t = time.perf_counter()
+        nbytes = 0
+        for a8, c8, s8, a16, c16, s16 in jobs:
+            r8 = list(ex.map(shard8, s8))
+            r16 = list(ex.map(shard16, s16))
+            for r, c in ((r8, c8), (r16, c16)):
+                combine_shards(c, [x[0] for x in r])
+                combine_shards(c, [x[2] for x in r])
+            nbytes += 3 * a8.size + 6 * a16.size
+        dt = time.perf_counter() - t
+    return {"value": round(nbytes / dt / 1e9, 3), "unit": "GB/s", "cores": cores,
+            "sample": f"the same sample split into {cores} shards per buffer at character boundaries, "
+                      f"one thread per shard ({dt:.2f} s)"}
 
 
 # ---- the reference arm ----------------------------------------------------------------------

@@ -88,6 +88,15 @@ void gbu_set_wait_limit(gbu_ctx *ctx, uint32_t rounds);
 /* Test hook: the tile with this index never publishes its scan state, so the tiles after it
  * wait until the limit and the call reports GBU_TIMEOUT.  -1 (default) disables the hook. */
 void gbu_debug_skip_publish(gbu_ctx *ctx, int64_t tile);
+/* Early exit on invalid input (on by default).  The single-buffer validation calls and
+ * transcoders publish the position of a flagged chunk as soon as a thread finds one; work
+ * that lies wholly past it is skipped (validation stops reading, a transcoder still counts
+ * and chains such a partition but does not convert it).  Results are identical either way,
+ * since the first error and the output of the valid prefix never lie past a flagged chunk;
+ * only the time to reach them changes.  enable = 0 scans every input to the end (used to
+ * time full scans).  Not in the paper, whose kernels process blocks in order and can stop at
+ * once. */
+void gbu_set_early_exit(gbu_ctx *ctx, int enable);
 
 /* UTF-8 validation (Section 3, rules 1-6). */
 int gbu_validate_utf8(gbu_ctx *ctx, const uint8_t *src, uint64_t n, gbu_result *result,
@@ -314,6 +323,44 @@ void gbu_arena_destroy(gbu_arena *arena);
 #define GBU_NOALLOC_MAX_UNITS ((uint64_t)1 << 28) /* 256 MiB of UTF-8 input */
 int gbu_convert_utf8_to_utf16le_noalloc(const uint8_t *src, uint64_t n, uint16_t *dst, uint64_t cap,
                                         gbu_result *result, gbu_stream stream);
+
+/* ---- Sharded form --------------------------------------------------------------------------
+ * One buffer split into P shards at character boundaries, so that each shard can be handled by
+ * an ordinary single-buffer call (on its own stream and context, or on its own GPU), and the
+ * shards' results combined into the result of the whole buffer.  Not in the paper, which
+ * processes one buffer on one core: this is the data-parallel split of the same Section 3
+ * validation and transcoding.
+ *
+ * Cuts: cuts[0] = 0, cuts[P] = n, and cuts[k] (0 < k < P) is the nominal start
+ * floor(k n / P) (balanced) moved forward to a character start: UTF-8, the first position in
+ * [c, c+3) whose byte is not a continuation byte (10xxxxxx), else c+3; UTF-16LE, c+1 when the
+ * word at c is a second surrogate (DC00-DFFF), else c.  The cuts never decrease (a shard may be
+ * empty).  Inside a valid prefix every cut is a character start, and a sequence that a cut
+ * splits fails in its shard with the kind and offset it has in the whole buffer, so:
+ *   - validation/transcoding: the first shard (in order) with an input error holds the
+ *     buffer's first error, at cuts[k] + its offset, and the shards before it are valid;
+ *   - lengths: the buffer's length is the sum of the shards' lengths (the formulas are per
+ *     position);
+ *   - transcoding: shard k writes to dst + off[k] with capacity off[k+1] - off[k], where off is
+ *     the exclusive scan of the shards' output lengths (gbu_exclusive_scan_u64) clipped to the
+ *     buffer's cap; then dst[0:L] of the valid prefix is exactly the single call's output.
+ * P is 1 .. GBU_MAX_SHARDS.  cuts has P + 1 entries (8-byte aligned). */
+#define GBU_MAX_SHARDS 65536u
+/* Cuts of a DEVICE buffer, written to the DEVICE array cuts by one small launch on `stream`. */
+int gbu_shard_cuts_utf8(gbu_ctx *ctx, const uint8_t *src, uint64_t n, uint32_t P, uint64_t *cuts,
+                        gbu_stream stream);
+int gbu_shard_cuts_utf16le(gbu_ctx *ctx, const uint16_t *src, uint64_t n, uint32_t P, uint64_t *cuts,
+                           gbu_stream stream);
+/* The same cuts of a HOST buffer, computed on the host (a loader that splits text before
+ * sending each shard to its GPU). */
+int gbu_shard_cuts_utf8_host(const uint8_t *src, uint64_t n, uint32_t P, uint64_t *cuts);
+int gbu_shard_cuts_utf16le_host(const uint16_t *src, uint64_t n, uint32_t P, uint64_t *cuts);
+/* Host: combines the P shards' validation or transcoding results (host arrays; cuts as above)
+ * into *out.  A shard that reported GBU_TIMEOUT (or another call failure) makes that the
+ * result; else the first shard with an input error gives {kind, cuts[k] + count}; else
+ * {GBU_OK, sum of counts}, or {GBU_OUTPUT_TOO_SMALL, sum of counts} if any shard ran out of
+ * room.  GBU_BAD_ARGUMENT for NULL arrays, P out of range or decreasing cuts. */
+int gbu_combine_shards(const uint64_t *cuts, const gbu_result *parts, uint32_t P, gbu_result *out);
 
 /* Number of kernel launches the library made through this context so far (for accounting). */
 uint64_t gbu_launch_count(const gbu_ctx *ctx);

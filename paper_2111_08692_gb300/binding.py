@@ -97,6 +97,16 @@ def lib() -> ctypes.CDLL:
             L.gbu_set_wait_limit.argtypes = [vp, u32]
             L.gbu_debug_skip_publish.restype = None
             L.gbu_debug_skip_publish.argtypes = [vp, i64]
+            L.gbu_set_early_exit.restype = None
+            L.gbu_set_early_exit.argtypes = [vp, i32]
+            for name in ("gbu_shard_cuts_utf8", "gbu_shard_cuts_utf16le"):
+                getattr(L, name).restype = i32
+                getattr(L, name).argtypes = [vp, vp, u64, u32, vp, vp]
+            for name in ("gbu_shard_cuts_utf8_host", "gbu_shard_cuts_utf16le_host"):
+                getattr(L, name).restype = i32
+                getattr(L, name).argtypes = [vp, u64, u32, vp]
+            L.gbu_combine_shards.restype = i32
+            L.gbu_combine_shards.argtypes = [vp, vp, u32, vp]
             L.gbu_launch_count.restype = u64
             L.gbu_launch_count.argtypes = [vp]
             L.gbu_launch_config.restype = i32
@@ -195,6 +205,10 @@ def gbu_set_wait_limit(ctx: int, rounds: int) -> None:
 
 def gbu_debug_skip_publish(ctx: int, tile: int) -> None:
     lib().gbu_debug_skip_publish(ctx, tile)
+
+
+def gbu_set_early_exit(ctx: int, enable: bool) -> None:
+    lib().gbu_set_early_exit(ctx, 1 if enable else 0)
 
 
 def gbu_launch_count(ctx: int) -> int:
@@ -371,6 +385,18 @@ class Codec:
     def debug_skip_publish(self, tile: int):
         gbu_debug_skip_publish(self.ctx, tile)
 
+    def set_early_exit(self, enable: bool):
+        gbu_set_early_exit(self.ctx, enable)
+
+    def shard_cuts(self, src, P: int, out=None, stream=None):
+        """Cuts (P + 1 int64 values, on this device) of a device buffer: uint8 (UTF-8) or
+        int16 (UTF-16LE), split into P shards at character boundaries."""
+        out = self.torch.empty(P + 1, dtype=self.torch.int64, device=f"cuda:{self.device}") if out is None else out
+        fn = lib().gbu_shard_cuts_utf16le if src.dtype == self.torch.int16 else lib().gbu_shard_cuts_utf8
+        _check(fn(self.ctx, self._ptr(src), src.numel(), P, out.data_ptr(), self._stream(stream)),
+               "gbu_shard_cuts")
+        return out
+
     def reset(self):
         _check(gbu_reset(self.ctx), "gbu_reset")
 
@@ -491,6 +517,31 @@ class Codec:
                                            result.data_ptr(), self._stream(stream)),
                "gbu_convert_utf16le_to_utf8")
         return result
+
+
+def shard_cuts_host(data, P: int):
+    """Cuts (P + 1 uint64 values) of a host buffer: a uint8 numpy array (UTF-8) or a uint16
+    one (UTF-16LE), split into P shards at character boundaries (gbu_shard_cuts_*_host)."""
+    import numpy as np
+    data = np.ascontiguousarray(data)
+    cuts = np.empty(P + 1, dtype=np.uint64)
+    fn = lib().gbu_shard_cuts_utf16le_host if data.dtype == np.uint16 else lib().gbu_shard_cuts_utf8_host
+    _check(fn(data.ctypes.data if data.size else None, data.size, P, cuts.ctypes.data), "gbu_shard_cuts_host")
+    return cuts
+
+
+def combine_shards(cuts, parts) -> tuple[str, int]:
+    """The whole buffer's (status name, count) from its shards' results (gbu_combine_shards);
+    parts: P (status name, count) pairs."""
+    import numpy as np
+    cuts = np.ascontiguousarray(cuts, dtype=np.uint64)
+    P = len(parts)
+    arr = (GbuResult * P)()
+    for k, (name, count) in enumerate(parts):
+        arr[k] = GbuResult(STATUS_CODE[name], 0, int(count))
+    out = GbuResult()
+    _check(lib().gbu_combine_shards(cuts.ctypes.data, arr, P, ctypes.byref(out)), "gbu_combine_shards")
+    return STATUS.get(out.status, out.status), int(out.count)
 
 
 def convert_utf8_to_utf16le_noalloc(src, dst, result, stream=None, cap=None):

@@ -62,6 +62,7 @@ struct gbu_ctx {
   uint32_t max_states;
   uint32_t wait_limit;
   long long skip_tile;
+  uint32_t early_exit;
   int blocks_per_sm[K_COUNT];
   int batch_blocks_per_sm[K_COUNT][3];  // per batched mode and warps per CTA (4, 8, 16)
   int scan_blocks_per_sm;
@@ -80,6 +81,7 @@ static int init_workspace(gbu_ctx *c) {
   memset(&h, 0, sizeof(h));
   h.epoch = 1;
   h.errkey = gbu::NO_ERROR;
+  h.stop_tile = 0xFFFFFFFFu;
   if (cudaMemcpy(c->ws, &h, sizeof(h), cudaMemcpyHostToDevice) != cudaSuccess) return GBU_CUDA_ERROR;
   if (cudaMemset(c->states, 0, (size_t)c->max_states * sizeof(uint64_t)) != cudaSuccess)
     return GBU_CUDA_ERROR;
@@ -94,6 +96,7 @@ extern "C" gbu_ctx *gbu_create(int device, uint64_t max_units) {
   c->max_units = max_units;
   c->wait_limit = 1u << 22;
   c->skip_tile = -1;
+  c->early_exit = 1;
   c->launches = 0;
   if (cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) {
     delete c;
@@ -191,6 +194,10 @@ extern "C" void gbu_debug_skip_publish(gbu_ctx *c, int64_t tile) {
   if (c) c->skip_tile = tile;
 }
 
+extern "C" void gbu_set_early_exit(gbu_ctx *c, int enable) {
+  if (c) c->early_exit = enable ? 1u : 0u;
+}
+
 extern "C" uint64_t gbu_launch_count(const gbu_ctx *c) { return c ? c->launches.load() : 0; }
 
 extern "C" int gbu_launch_config(const gbu_ctx *c, int32_t *out, int n) {
@@ -232,6 +239,7 @@ static int make_params(gbu_ctx *c, int k, const void *src, uint64_t n, uint32_t 
   p->max_states = c->max_states;
   p->wait_limit = c->wait_limit;
   p->skip_tile = c->skip_tile;
+  p->early_exit = c->early_exit;
   return GBU_OK;
 }
 
@@ -594,6 +602,9 @@ extern "C" void gbu_graph_destroy(gbu_graph *gr) {
 }
 
 // ---- library-internal entry points (gbu_internal.h) ---------------------------------------
+
+int gbu_internal_device(const gbu_ctx *c) { return c->device; }
+void gbu_internal_count_launch(gbu_ctx *c) { c->launches.fetch_add(1); }
 
 int gbu_internal_batch_desc(gbu_ctx *c, int op, const gbu::StringDesc *desc, uint64_t B, gbu_result *results,
                             gbu_stream stream) {

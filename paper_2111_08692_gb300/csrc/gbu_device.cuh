@@ -55,7 +55,8 @@ struct WsHeader {
   uint32_t status;                // sticky: 1 = a wait gave up (GBU_TIMEOUT)
   unsigned long long errkey;      // smallest input position of a thread chunk with an error
   unsigned long long total;       // sum of partition aggregates (output length)
-  uint32_t pad[24];
+  uint32_t stop_tile;             // validation early exit: smallest warp tile with a flagged chunk
+  uint32_t pad[23];
 };
 static_assert(sizeof(WsHeader) == 128, "header is one 128-byte line");
 
@@ -75,6 +76,8 @@ struct Params {
   uint32_t max_states;     // entries in states[]
   uint32_t wait_limit;     // look-back polls before a wait gives up
   long long skip_tile;     // test hook: this partition never publishes (-1: off)
+  uint32_t early_exit;     // validation and single-buffer transcoders: skip work past a known error
+  uint32_t pad_;
 };
 
 // Batched operations (gbu_batch.cu), in the order of the single-buffer kernels.
@@ -487,6 +490,7 @@ __device__ __forceinline__ void reset_workspace(const Params &p) {
     ws->errkey = NO_ERROR;
     ws->total = 0;
     ws->status = 0;
+    ws->stop_tile = 0xFFFFFFFFu;
     const uint32_t e = ws->epoch + 1;
     wrap = e > ST_EPOCH_MASK;
     ws->epoch = wrap ? 1u : e;

@@ -26,3 +26,7 @@ int gbu_internal_partitions(int op, const void *src, uint64_t n);
 int gbu_internal_convert_segments(gbu_ctx *ctx, int op, const gbu::StringDesc *desc, const uint32_t *pstart,
                                   uint32_t B, uint32_t ntiles, gbu::SegState *seg, gbu_result *results,
                                   gbu_stream stream);
+
+// The context's device, and the launch counter (for launches made outside gbu_api.cu).
+int gbu_internal_device(const gbu_ctx *ctx);
+void gbu_internal_count_launch(gbu_ctx *ctx);

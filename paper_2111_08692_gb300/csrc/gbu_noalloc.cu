@@ -75,6 +75,7 @@ void setup_device(DeviceSetup &s, int device) {
   memset(&h, 0, sizeof(h));
   h.epoch = 1;
   h.errkey = gbu::NO_ERROR;
+  h.stop_tile = 0xFFFFFFFFu;
   if (cudaMemset(addr, 0, NOALLOC_WORDS * sizeof(uint64_t)) != cudaSuccess ||
       cudaMemcpy(addr, &h, sizeof(h), cudaMemcpyHostToDevice) != cudaSuccess ||
       cudaDeviceSynchronize() != cudaSuccess) {

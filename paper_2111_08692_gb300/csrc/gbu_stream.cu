@@ -32,9 +32,31 @@ __global__ void __launch_bounds__(STREAM_THREADS) stream_kernel(const Params p) 
   const long long nw = (long long)gridDim.x * ST_WARPS;
   const long long lo = p.off0, hi = (long long)p.vbytes;
   unsigned long long err_pos = NO_ERROR, total = 0;
+  // Early exit (validation): a warp's tiles lie at increasing positions, so once a warp has
+  // flagged a chunk it stops, and no warp starts a tile past the smallest tile flagged so far
+  // (the workspace's stop tile, published at once; a snapshot is refreshed every 8th tile of
+  // the warp -- all warps read that one word, so reading it every tile would queue them on one
+  // L2 slice -- by a load that overlaps the tile's own loads).  The smallest flagged chunk is
+  // never skipped.
+  const bool early = (MODE == S_V8 || MODE == S_V16) && p.early_exit != 0;
+  uint32_t known = 0xFFFFFFFFu;
+  // after a tile: publish a flagged tile and stop, or take the refreshed snapshot
+  uint32_t it = 0;  // tiles this warp has started
+  auto stop_after_tile = [&](long long wt, uint32_t snap) -> bool {
+    if (__any_sync(0xffffffffu, err_pos != NO_ERROR)) {
+      if (lane == 0) atomicMin(&p.ws->stop_tile, (uint32_t)wt);
+      return true;
+    }
+    if ((it & 7u) == 1u) known = __shfl_sync(0xffffffffu, snap, 0);
+    return false;
+  };
 
   for (long long wt = gw; wt < (long long)p.ntiles; wt += nw) {
     const long long t0 = wt * WT_BYTES;
+    if (early && (uint32_t)wt > known) break;  // uniform over the warp
+    uint32_t snap = 0xFFFFFFFFu;
+    if (early && lane == 0 && (it & 7u) == 0) snap = ld_relaxed_u32(&p.ws->stop_tile);
+    ++it;
     const bool fast = t0 - 4 >= lo && t0 + (long long)WT_BYTES + 4 <= hi;
     uint4 v[ST_ROUNDS];
     uint32_t pre, post;
@@ -62,6 +84,7 @@ __global__ void __launch_bounds__(STREAM_THREADS) stream_kernel(const Params p) 
                                __funnelshift_l(fp.geF0, 0u, 24);
           if (req && (unsigned long long)t0 < err_pos) err_pos = (unsigned long long)t0;
         }
+        if (early && stop_after_tile(wt, snap)) break;
         continue;
       }
     }
@@ -118,6 +141,7 @@ __global__ void __launch_bounds__(STREAM_THREADS) stream_kernel(const Params p) 
         }
       }
     }
+    if (early && stop_after_tile(wt, snap)) break;
   }
 
   const bool want_err = MODE == S_V8 || MODE == S_V16;

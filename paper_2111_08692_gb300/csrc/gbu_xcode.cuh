@@ -75,6 +75,7 @@ struct __align__(128) XSmem {
   unsigned long long red[XWARPS];
   uint32_t ticket;
   int is_last;
+  unsigned long long known;  // snapshot of the error key (single-buffer early exit)
   Params prm[2];   // several-string launches: the string of counts[0] / counts[1]
   uint32_t sid[2];
 };
@@ -386,11 +387,21 @@ __device__ __forceinline__ void transcode(const Params &p, XSmem<Codec> &sm, Fin
       atomicAdd(&p.ws->total, (unsigned long long)sm.counts[cb].total);
     }
   }
+  // Early exit: output past the first error is unspecified, so a partition that starts past
+  // a chunk some thread already flagged (the error key, published at once) is counted and
+  // chained as usual -- later partitions still need its aggregate -- but not converted.  The
+  // first error lies at most 15 bytes past the smallest flagged chunk, so it is always
+  // converted up to its start.
+  unsigned long long published = NO_ERROR;
   while (cur < p.ntiles) {
     // claim and count the next partition, so that its aggregate is out a partition early
-    if (tid == 0) sm.ticket = atomicAdd(&p.ws->ticket, 1u);
+    if (tid == 0) {
+      sm.ticket = atomicAdd(&p.ws->ticket, 1u);
+      sm.known = p.early_exit ? ld_relaxed_u64(reinterpret_cast<const uint64_t *>(&p.ws->errkey)) : NO_ERROR;
+    }
     __syncthreads();
     const uint32_t nxt = sm.ticket;
+    const unsigned long long known = sm.known;
     if (nxt < p.ntiles) {
       count_part<Codec>(p, nxt, sm.counts[cb ^ 1]);
       if (tid == 0) {
@@ -400,7 +411,13 @@ __device__ __forceinline__ void transcode(const Params &p, XSmem<Codec> &sm, Fin
     }
     const uint64_t S0 = lookback_cta<XT>(p, cur, sm.counts[cb].total, epoch, sm.lb);
 
-    convert_part<Codec>(p, cur, sm.counts[cb], S0, sm, use, err_pos);
+    if ((unsigned long long)cur * PART_BYTES <= known) {  // uniform over the CTA
+      convert_part<Codec>(p, cur, sm.counts[cb], S0, sm, use, err_pos);
+      if (p.early_exit && err_pos < published) {  // rare: this thread flagged a new error
+        atomicMin(&p.ws->errkey, err_pos);
+        published = err_pos;
+      }
+    }
     cur = nxt;
     cb ^= 1;
     __syncthreads();  // counts[cb ^ 1] is rewritten by the next count pass
@@ -460,6 +477,7 @@ __device__ __forceinline__ void seg_params(const SegParams &q, uint32_t s, Param
   p.max_states = q.max_states;
   p.wait_limit = q.wait_limit;
   p.skip_tile = -1;
+  p.early_exit = 0;
 }
 
 // The kernel body.  finalize(p, st, s) runs in one thread once string s is finished (p: its

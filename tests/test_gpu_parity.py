@@ -226,6 +226,39 @@ def test_sweep_small(codec, torch):
             check_utf16_input(codec, torch, d["u16_cut_end"])
 
 
+def test_early_exit_gives_the_same_results(codec, torch):
+    """Early exit on invalid input changes no result: errors placed before, inside and after
+    the tiles and partitions other warps work on, several at once, with early exit on and off."""
+    from paper_2111_08692_gb300 import result_tuple
+    from gpu_helpers import as_torch_u16
+    u8, u16 = W.profile_buffers("cjk", 3 * PART + 777, (3 * PART + 777) // 2, 52, cache=False)
+    starts = char_starts_utf8(u8)
+    rng = np.random.default_rng(53)
+    cases8, cases16 = [], []
+    for k in range(24):
+        b = u8.copy()
+        for pos in rng.choice(starts[starts > 4], size=1 + k % 3, replace=False):
+            b[pos] = (0x80, 0xC0, 0xFF)[k % 3]
+        cases8.append(b)
+        w = u16.copy()
+        for pos in rng.integers(0, w.size, size=1 + k % 3):
+            w[pos] = 0xDC00 + k
+        cases16.append(w)
+    for b, w in zip(cases8, cases16):
+        s8 = torch.from_numpy(b).to("cuda")
+        s16 = as_torch_u16(torch, w).to("cuda")
+        d16 = torch.empty(b.size + 8, dtype=torch.int16, device="cuda")
+        d8 = torch.empty(3 * w.size + 8, dtype=torch.uint8, device="cuda")
+        want = (oracle.validate_utf8(b), oracle.convert_utf8_to_utf16le(b, b.size + 8)[0],
+                oracle.validate_utf16le(w), oracle.convert_utf16le_to_utf8(w, 3 * w.size + 8)[0])
+        for early in (True, False):
+            codec.set_early_exit(early)
+            got = (result_tuple(codec.validate_utf8(s8)), result_tuple(codec.convert_utf8_to_utf16le(s8, d16)),
+                   result_tuple(codec.validate_utf16le(s16)), result_tuple(codec.convert_utf16le_to_utf8(s16, d8)))
+            assert got == want, (early, got, want)
+    codec.set_early_exit(True)
+
+
 def test_repeated_runs_are_identical(codec, torch):
     from paper_2111_08692_gb300 import result_tuple
     u8, u16 = W.profile_buffers("emoji", 1 << 21, 1 << 20, 41, cache=False)

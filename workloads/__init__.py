@@ -358,6 +358,33 @@ def sweep_buffers(profile: str, rate: float, n_bytes: int = 256 << 20, seed: int
     return make()
 
 
+SWEEP_PROFILES = ("cyrillic", "cjk")
+SWEEP_RATES = (1e-6, 1e-4, 1e-2)
+
+
+def _make_sweep(args):
+    profile, rate, n_bytes = args
+    sweep_buffers(profile, rate, n_bytes)
+    return profile, rate
+
+
+def prepare_sweeps(n_bytes: int = 256 << 20, workers: int | None = None):
+    """Generates (into the on-disk cache) the six sweep workloads (two profiles x three error
+    rates) in parallel 'spawn' worker processes, like prepare_single_buffers."""
+    import concurrent.futures as cf
+    import multiprocessing as mp
+    todo = [(p, r, n_bytes) for p in SWEEP_PROFILES for r in SWEEP_RATES
+            if not os.path.exists(os.path.join(_cache_path(f"sweep:{p}:{r}:{n_bytes}:{SWEEP_SEEDS[(p, r)]}"),
+                                               "DONE"))]
+    if len(todo) <= 1 or (workers or os.cpu_count() or 1) <= 1 or n_bytes < (1 << 24):
+        for t in todo:
+            _make_sweep(t)
+        return
+    with cf.ProcessPoolExecutor(max_workers=min(len(todo), workers or os.cpu_count() or 1),
+                                mp_context=mp.get_context("spawn")) as ex:
+        list(ex.map(_make_sweep, todo))
+
+
 # ---- batched strings --------------------------------------------------------------------------
 
 def _char_sizes(cps: np.ndarray):
