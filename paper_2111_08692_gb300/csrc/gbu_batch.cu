@@ -150,7 +150,7 @@ __device__ __forceinline__ void region_read(const Params &sp, long long c, uint4
         c3 |= f[k].geE0 & ~f[k].geF0;
         c4 |= f[k].geF0;
       }
-      err |= utf8_special_errors(W, __any_sync(0xffffffffu, c2 != 0), __any_sync(0xffffffffu, c3 != 0),
+      err |= utf8_special_errors(W, f, __any_sync(0xffffffffu, c2 != 0), __any_sync(0xffffffffu, c3 != 0),
                                  __any_sync(0xffffffffu, c4 != 0));
       if (err && (unsigned long long)c < err_pos) err_pos = (unsigned long long)c;
     }

@@ -13,7 +13,7 @@
 //     sequence fails there);
 //   * values (rules 4-6, and rule 1 for F8-FF): given a correct structure, only six leading
 //     bytes with particular second bytes can encode an out-of-range value; they are found by
-//     zero-byte tests on whole words (utf8_special_errors).  The transcoder, which decodes
+//     byte tests on whole words (utf8_special_errors).  The transcoder, which decodes
 //     every position anyway, range-checks the decoded 16-bit values instead.
 // UTF-16 (Section 3): a word in D800-DBFF must be followed by one in DC00-DFFF and a word
 // in DC00-DFFF must follow one in D800-DBFF.
@@ -67,39 +67,39 @@ __device__ __forceinline__ uint32_t utf8_structure_errors(const Flags8 f[5]) {
   return err;
 }
 
-// Bit 7 of each byte set where that byte is zero (exact per byte).
-__device__ __forceinline__ uint32_t zero_bytes(uint32_t t) {
-  return ~(((t & 0x7F7F7F7Fu) + 0x7F7F7F7Fu) | t) & 0x80808080u;
-}
-
-// Rules 4-6 (and rule 1 for F8-FF) for the 16 bytes W[1..4], with W[5] the word after, as
-// byte tests on whole words.  With the structure (rules 1-3) already checked, the value of a
-// sequence can only be out of range for these leading bytes and second bytes: C0 or C1
-// (overlong), E0 then 80-9F (overlong), ED then A0-BF (D800-DFFF), F0 then 80-8F (overlong),
-// F4 then 90-BF or F5-FF (above U+10FFFF; F8-FF also break rule 1).  Each test looks at a
-// byte and the byte after it (N = the stream shifted by one byte).  Nonzero = some position
-// of the chunk starts such a sequence (the caller only needs to know that the chunk holds an
-// error; the kind and offset are resolved separately).  has2/has3/has4: whether the warp has
-// two-, three-, four-byte leading bytes at all (absent classes cost nothing).
-__device__ __forceinline__ uint32_t utf8_special_errors(const uint32_t W[6], bool has2, bool has3, bool has4) {
+// Rules 4-6 (and rule 1 for F8-FF) for the 16 bytes W[1..4], with W[5] the word after and
+// f[1..4] their classification, as byte tests on whole words.  With the structure (rules 1-3)
+// already checked, the value of a sequence can only be out of range for these leading bytes
+// and second bytes: C0 or C1 (overlong), E0 then 80-9F (overlong), ED then A0-BF (D800-DFFF),
+// F0 then 80-8F (overlong), F4 then 90-BF or F5-FF (above U+10FFFF; F8-FF also break rule
+// 1).  Each test looks at a byte's low bits and, for E0/ED and F0/F4, at the byte after it
+// (N = the stream shifted by one byte); the per-byte sums below never carry into the next
+// byte.  Nonzero = some position of the chunk starts such a sequence (the caller only needs
+// to know that the chunk holds an error; the kind and offset are resolved separately).
+// has2/has3/has4: whether the warp has two-, three-, four-byte leading bytes at all (absent
+// classes cost nothing).
+__device__ __forceinline__ uint32_t utf8_special_errors(const uint32_t W[6], const Flags8 f[5], bool has2, bool has3,
+                                                        bool has4) {
   uint32_t bad = 0;
 #pragma unroll
   for (int k = 1; k <= 4; ++k) {
     const uint32_t w = W[k];
     const uint32_t n = __funnelshift_r(W[k], W[k + 1], 8);  // byte j: the byte after byte j
-    if (has2) bad |= zero_bytes((w & 0xFEFEFEFEu) ^ 0xC0C0C0C0u);
+    // C0/C1: a leading byte >= C0 whose bits 5-1 are zero
+    if (has2) bad |= f[k].geC0 & ~((w & 0x3E3E3E3Eu) + 0x7F7F7F7Fu);
     if (has3) {
-      // E0 then 80-9F, or ED then A0-BF: with y = 1 where the next byte has bit 5 set
-      // (A0-BF), exactly the bytes equal to E0 ^ 0D*y (E0 when y = 0, ED when y = 1)
+      // E0-EF with low nibble 0 and next byte 80-9F, or low nibble D and next byte A0-BF:
+      // with y = 1 where the next byte has bit 5 set, exactly where (nibble ^ 0D*y) is zero
       const uint32_t y = (n >> 5) & 0x01010101u;
-      bad |= zero_bytes(w ^ 0xE0E0E0E0u ^ (y * 0x0Du));
+      const uint32_t q = (w & 0x0F0F0F0Fu) ^ (y * 0x0Du);
+      bad |= f[k].geE0 & ~f[k].geF0 & ~(q + 0x7F7F7F7Fu);
     }
     if (has4) {
-      // F0 then 80-8F, or F4 then 90-BF: with y4 = 4 where the next byte has bit 4 or 5 set
-      // (90-BF), exactly the bytes equal to F0 ^ y4
+      // F0-FF with low nibble 0 and next byte 80-8F, or nibble 4 and next byte 90-BF
+      // (y4 = 4 where the next byte has bit 4 or 5 set: (nibble ^ y4) is zero), or nibble >= 5
       const uint32_t y4 = ((n >> 2) | (n >> 3)) & 0x04040404u;
-      bad |= zero_bytes(w ^ 0xF0F0F0F0u ^ y4);
-      bad |= ((w & 0x7F7F7F7Fu) + 0x0B0B0B0Bu) & w & 0x80808080u;  // F5-FF
+      const uint32_t L = w & 0x0F0F0F0Fu;
+      bad |= f[k].geF0 & (~((L ^ y4) + 0x7F7F7F7Fu) | (L + 0x7B7B7B7Bu));
     }
   }
   return bad;

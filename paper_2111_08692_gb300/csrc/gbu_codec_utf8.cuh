@@ -142,7 +142,7 @@ struct Utf8ToUtf16 {
       f[k].geC0 = w & s1 & 0x80808080u;
       f[k].isC = w & ~s1 & 0x80808080u;
       f[k].geE0 = ONE ? f[k].geC0 : f[k].geC0 & (w << 2);
-      f[k].geF0 = ONE ? f[k].geC0 : (H4 ? f[k].geE0 & (w << 3) : 0u);
+      f[k].geF0 = H4 ? (ONE ? f[k].geC0 : f[k].geE0 & (w << 3)) : 0u;  // zero without H4 (the E0-EF test reads it)
     }
     uint32_t bad = 0;
 #pragma unroll
@@ -152,7 +152,7 @@ struct Utf8ToUtf16 {
       if (H4) req |= __funnelshift_l(f[k].geF0, f[k + 1].geF0, 24);
       bad |= req ^ f[k + 1].isC;
     }
-    if (H2 || H3) bad |= utf8_special_errors(W, H2, H3, false);
+    if (H2 || H3) bad |= utf8_special_errors(W, f, H2, H3, false);
     // pair i covers positions 2i, 2i+1 (two 16-bit lanes): E = bytes (2i, 2i+1),
     // O = bytes (2i+1, 2i+2); the next pair's E and O hold the third and fourth bytes
     uint32_t E = __byte_perm(W[1], W[2], selE(0));

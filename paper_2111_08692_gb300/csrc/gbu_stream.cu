@@ -102,6 +102,29 @@ __global__ void __launch_bounds__(STREAM_THREADS) stream_kernel(const Params p) 
       W[0] = lane == 0 ? before : up;
       W[5] = lane == 31 ? after : down;
 
+      if (MODE == S_V8) {
+        // Leading bytes >= E0 in the warp's region or in the word before it?  Without them
+        // (Latin, Cyrillic and other one- and two-byte text) a byte must be a continuation
+        // byte exactly when the byte before it is >= C0, and only C0/C1 can break rules 4-6.
+        uint32_t s1[5], geC0[5], hi3 = 0;
+#pragma unroll
+        for (int k = 0; k < 5; ++k) {
+          s1[k] = W[k] << 1;
+          geC0[k] = W[k] & s1[k] & 0x80808080u;
+          hi3 |= geC0[k] & (W[k] << 2);
+        }
+        if (!__any_sync(0xffffffffu, hi3 != 0)) {
+          uint32_t err = 0;
+#pragma unroll
+          for (int k = 1; k <= 4; ++k) {
+            const uint32_t isC = W[k] & ~s1[k] & 0x80808080u;
+            err |= __funnelshift_l(geC0[k - 1], geC0[k], 8) ^ isC;
+            err |= geC0[k] & ~((W[k] & 0x3E3E3E3Eu) + 0x7F7F7F7Fu);  // C0, C1
+          }
+          if (err && (unsigned long long)c < err_pos) err_pos = (unsigned long long)c;
+          continue;
+        }
+      }
       if (MODE == S_V8 || MODE == S_L16) {
         Flags8 f[5];
 #pragma unroll
@@ -117,7 +140,7 @@ __global__ void __launch_bounds__(STREAM_THREADS) stream_kernel(const Params p) 
             c3 |= f[k].geE0 & ~f[k].geF0;
             c4 |= f[k].geF0;
           }
-          err |= utf8_special_errors(W, __any_sync(0xffffffffu, c2 != 0), __any_sync(0xffffffffu, c3 != 0),
+          err |= utf8_special_errors(W, f, __any_sync(0xffffffffu, c2 != 0), __any_sync(0xffffffffu, c3 != 0),
                                      __any_sync(0xffffffffu, c4 != 0));
           if (err && (unsigned long long)c < err_pos) err_pos = (unsigned long long)c;
         }
