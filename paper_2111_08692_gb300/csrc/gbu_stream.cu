@@ -103,9 +103,11 @@ __global__ void __launch_bounds__(STREAM_THREADS) stream_kernel(const Params p) 
       W[5] = lane == 31 ? after : down;
 
       if (MODE == S_V8) {
-        // Leading bytes >= E0 in the warp's region or in the word before it?  Without them
-        // (Latin, Cyrillic and other one- and two-byte text) a byte must be a continuation
-        // byte exactly when the byte before it is >= C0, and only C0/C1 can break rules 4-6.
+        // Three routes, chosen per warp region by the leading bytes it holds (and the word
+        // before it): without bytes >= E0 (Latin, Cyrillic and other one- and two-byte text) a
+        // byte must be a continuation byte exactly when the byte before it is >= C0, and only
+        // C0/C1 can break rules 4-6; without bytes >= F0 (CJK) the >= F0 flags and tests drop
+        // out; else all three lead flags.
         uint32_t s1[5], geC0[5], hi3 = 0;
 #pragma unroll
         for (int k = 0; k < 5; ++k) {
@@ -124,27 +126,52 @@ __global__ void __launch_bounds__(STREAM_THREADS) stream_kernel(const Params p) 
           if (err && (unsigned long long)c < err_pos) err_pos = (unsigned long long)c;
           continue;
         }
+        // No leading byte >= F0 in the region (CJK and other text of one to three bytes):
+        // structure by the >= C0 and >= E0 flags only (the region holds bytes E0-EF).
+        Flags8 g[5];
+        uint32_t hi4 = 0;
+#pragma unroll
+        for (int k = 0; k < 5; ++k) {
+          g[k].geC0 = geC0[k];
+          g[k].geE0 = geC0[k] & (W[k] << 2);
+          g[k].geF0 = g[k].geE0 & (W[k] << 3);
+          g[k].isC = W[k] & ~s1[k] & 0x80808080u;
+          hi4 |= g[k].geF0;
+        }
+        if (!__any_sync(0xffffffffu, hi4 != 0)) {
+          uint32_t err = 0, c2 = 0;
+#pragma unroll
+          for (int k = 1; k <= 4; ++k) {
+            const uint32_t req = __funnelshift_l(g[k - 1].geC0, g[k].geC0, 8) |
+                                 __funnelshift_l(g[k - 1].geE0, g[k].geE0, 16);
+            err |= req ^ g[k].isC;
+            c2 |= g[k].geC0 & ~g[k].geE0;
+          }
+          err |= utf8_special_errors(W, g, __any_sync(0xffffffffu, c2 != 0), true, false);
+          if (err && (unsigned long long)c < err_pos) err_pos = (unsigned long long)c;
+          continue;
+        }
+        // leading bytes >= F0 occur in the region: all three flags
+        uint32_t err = 0, c2 = 0, c3 = 0;
+#pragma unroll
+        for (int k = 1; k <= 4; ++k) {
+          const uint32_t req = __funnelshift_l(g[k - 1].geC0, g[k].geC0, 8) |
+                               __funnelshift_l(g[k - 1].geE0, g[k].geE0, 16) |
+                               __funnelshift_l(g[k - 1].geF0, g[k].geF0, 24);
+          err |= req ^ g[k].isC;
+          c2 |= g[k].geC0 & ~g[k].geE0;
+          c3 |= g[k].geE0 & ~g[k].geF0;
+        }
+        err |= utf8_special_errors(W, g, __any_sync(0xffffffffu, c2 != 0), __any_sync(0xffffffffu, c3 != 0), true);
+        if (err && (unsigned long long)c < err_pos) err_pos = (unsigned long long)c;
+        continue;
       }
-      if (MODE == S_V8 || MODE == S_L16) {
+      if (MODE == S_L16) {
         Flags8 f[5];
 #pragma unroll
         for (int k = 0; k < 5; ++k) f[k] = classify8(W[k]);
-        if (MODE == S_L16) {
-          total += utf8_count_units(f, c, edge, lo, hi);
-        } else {
-          uint32_t err = utf8_structure_errors(f);
-          uint32_t c2 = 0, c3 = 0, c4 = 0;
-#pragma unroll
-          for (int k = 1; k <= 4; ++k) {
-            c2 |= f[k].geC0 & ~f[k].geE0;
-            c3 |= f[k].geE0 & ~f[k].geF0;
-            c4 |= f[k].geF0;
-          }
-          err |= utf8_special_errors(W, f, __any_sync(0xffffffffu, c2 != 0), __any_sync(0xffffffffu, c3 != 0),
-                                     __any_sync(0xffffffffu, c4 != 0));
-          if (err && (unsigned long long)c < err_pos) err_pos = (unsigned long long)c;
-        }
-      } else {
+        total += utf8_count_units(f, c, edge, lo, hi);
+      } else if (MODE == S_V16 || MODE == S_L8) {
         const uint32_t Wd[4] = {W[1], W[2], W[3], W[4]};
         if (MODE == S_L8) {
           uint32_t cnt = 0;
