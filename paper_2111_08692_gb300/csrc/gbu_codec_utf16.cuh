@@ -39,7 +39,7 @@ struct Utf16ToUtf8 {
   // (Section 3 sizes; a pair counts 2 + 2).  The flags are summed with byte dot products
   // (0x80 per flag), which run on the FMA pipe.
   __device__ __forceinline__ static uint32_t count_inside(const uint32_t W[4], uint32_t *sur_any,
-                                                         uint32_t *ge800_any) {
+                                                         uint32_t *ge800_any, uint32_t *wide_any) {
     uint32_t a80 = 0, a800 = 0, sub = 0;
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
@@ -49,12 +49,14 @@ struct Utf16ToUtf8 {
     }
     *sur_any = sub;  // the sums double as the "any" flags
     *ge800_any = a800;
+    *wide_any = a80 - sub;  // words >= 0x80 that are not surrogates (every surrogate is >= 0x80)
     return 8u + ((a80 + a800 - sub) >> 7);
   }
 
   // Flag bits of a chunk (and, ORed over the lanes, of a region).
   static constexpr uint32_t F_SUR = 1;     // a surrogate word (or a chunk at a buffer end)
-  static constexpr uint32_t F_THREE = 2;   // a word of three UTF-8 bytes (>= 0x800)
+  static constexpr uint32_t F_THREE = 2;   // a word >= 0x800 (three UTF-8 bytes, or a surrogate)
+  static constexpr uint32_t F_WIDE = 4;    // a word >= 0x80 that is not a surrogate
 
   static constexpr uint32_t ASCII_MASK = 0xFF80FF80u;  // nonzero in a word: a word >= 0x80
   static constexpr uint32_t CHUNK_UNITS = 8;            // bytes out of an all-ASCII chunk
@@ -75,13 +77,13 @@ struct Utf16ToUtf8 {
   __device__ __forceinline__ static uint32_t count(const Params &p, uint4 v, long long c, bool edge,
                                                    uint32_t &flags) {
     const uint32_t W[4] = {v.x, v.y, v.z, v.w};
-    flags = F_SUR | F_THREE;
+    flags = F_SUR | F_THREE | F_WIDE;
     if (!edge) {
       flags = 0;
       if (((W[0] | W[1] | W[2] | W[3]) & 0xFF80FF80u) == 0) return 8;  // all ASCII
-      uint32_t sa, g3;
-      const uint32_t n = count_inside(W, &sa, &g3);
-      flags = (sa != 0 ? F_SUR : 0u) | (g3 != 0 ? F_THREE : 0u);
+      uint32_t sa, g3, wd;
+      const uint32_t n = count_inside(W, &sa, &g3, &wd);
+      flags = (sa != 0 ? F_SUR : 0u) | (g3 != 0 ? F_THREE : 0u) | (wd != 0 ? F_WIDE : 0u);
       return n;
     }
     uint32_t cnt = 0;
@@ -143,7 +145,7 @@ struct Utf16ToUtf8 {
     }
     Region g{rtot, 0u, 0u, rtot};
     uint32_t o = base + x0;
-    if (rflags == 0) {
+    if (!(rflags & (F_SUR | F_THREE))) {
       // only words below 0x800 (Section 4's one-and-two-byte route)
 #pragma unroll
       for (int j = 0; j < 8; ++j) {
@@ -178,6 +180,33 @@ struct Utf16ToUtf8 {
       u[2 + 2 * k] = W[k] >> 16;
     }
     u[9] = next & 0xFFFFu;
+    const bool cut_start = is_low16(u[1]) && is_high16(u[0]);
+    const bool cut_end = is_high16(u[8]) && is_low16(u[9]);
+    g.skip = __shfl_sync(0xffffffffu, cut_start ? 2u : 0u, 0);
+    g.extra = __shfl_sync(0xffffffffu, cut_end ? 2u : 0u, 31);
+    if (!(rflags & F_WIDE)) {
+      // only ASCII words and surrogates (emoji-heavy text): an ASCII word writes its byte and
+      // every other word two slots' worth, all four bytes of a pair coming from its first
+      // word; the pair rules are checked on whole words (an unpaired surrogate is an error,
+      // and what it would write lies past the first error)
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const uint32_t w = u[j + 1], wn = u[j + 2];
+        const bool sur = (w & 0xF800u) == 0xD800u;
+        if (!sur) st[o] = (uint8_t)w;
+        if (is_high16(w) && is_low16(wn)) {
+          const uint32_t t = (w & 0x3FFu) + 0x40u;  // the code point >> 10
+          st[o] = (uint8_t)(0xF0u | (t >> 8));
+          st[o + 1] = (uint8_t)(0x80u | ((t >> 2) & 0x3Fu));
+          st[o + 2] = (uint8_t)(0x80u | ((t & 3u) << 4) | ((wn >> 6) & 0xFu));
+          st[o + 3] = (uint8_t)(0x80u | (wn & 0x3Fu));
+        }
+        o += sur ? 2u : 1u;
+      }
+      if (utf16_pair_errors_inside(W, prev, next) && (unsigned long long)c < err_pos)
+        err_pos = (unsigned long long)c;
+      return g;
+    }
     bool err = false;
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
@@ -200,10 +229,6 @@ struct Utf16ToUtf8 {
       o += (hs || ls) ? 2u : 1u + (g1 ? 1u : 0u) + (g2 ? 1u : 0u);
     }
     if (err && (unsigned long long)c < err_pos) err_pos = (unsigned long long)c;
-    const bool cut_start = is_low16(u[1]) && is_high16(u[0]);
-    const bool cut_end = is_high16(u[8]) && is_low16(u[9]);
-    g.skip = __shfl_sync(0xffffffffu, cut_start ? 2u : 0u, 0);
-    g.extra = __shfl_sync(0xffffffffu, cut_end ? 2u : 0u, 31);
     return g;
   }
 
