@@ -50,6 +50,8 @@ def parse():
     ap.add_argument("--loop-sample", type=int, default=3000,
                     help="strings timed through the per-string launch loop")
     ap.add_argument("--no-sweep", action="store_true")
+    ap.add_argument("--no-small", action="store_true", help="skip the L2-resident 1 MiB latency table")
+    ap.add_argument("--small-reps", type=int, default=200)
     ap.add_argument("--sweep-size", type=int, default=256 << 20, help="UTF-8 bytes per invalid-input sweep buffer")
     ap.add_argument("--sweep-reps", type=int, default=5)
     ap.add_argument("--no-serving", action="store_true")
@@ -318,7 +320,9 @@ def run_ours(args):
             ms = statistics.mean(per[op][b["profile"]])
             ab = algo_bytes(b, op)
             inb = b["s8"].numel() if op in UTF8_INPUT_OPS else 2 * b["s16"].numel()
-            breakdown[op][b["profile"]] = {"ms": round(ms, 4), "input_gbs": round(inb / ms / 1e6, 1),
+            breakdown[op][b["profile"]] = {"ms": round(ms, 4), "min_ms": round(min(per[op][b["profile"]]), 4),
+                                           "median_ms": round(statistics.median(per[op][b["profile"]]), 4),
+                                           "input_gbs": round(inb / ms / 1e6, 1),
                                            "traffic_gbs": round(ab / ms / 1e6, 1),
                                            "frac": round(ab / ms / 1e6 / peak, 3)}
             tot_ms += ms
@@ -349,6 +353,8 @@ def run_ours(args):
         line["cpu_baseline"] = cpu_baseline(bufs, args.cpu_sample)
     if not args.no_sweep:
         line["sweep"] = run_sweep(args, codec, dev)
+    if not args.no_small:
+        line["l2_resident_1mib"] = run_small(args, codec, dev)
     if not args.no_batched and args.batched_strings > 0:
         line["batched"] = run_batched(args, codec, dev, dist, world)
     if not args.no_serving:
@@ -358,6 +364,45 @@ def run_ours(args):
     codec.close()
     if dist:
         dist.destroy_process_group()
+
+
+def run_small(args, codec, dev):
+    """The 1 MiB mixed-profile buffer (50% U+0000-007F, 20% U+0080-07FF, 20% U+0800-FFFF, 10%
+    U+10000-10FFFF) and its UTF-16LE form: each of the six operations launched small_reps times
+    back to back, each launch timed by CUDA events.  The buffers stay in L2, so these are
+    L2-resident latencies (min and median per launch), not HBM-roofline numbers."""
+    import numpy as np
+    import torch
+    import workloads as W
+    stream = torch.cuda.current_stream(dev)
+    u8, u16, _, _ = W.mixed_1mib()
+    s8 = torch.from_numpy(np.ascontiguousarray(u8)).to(dev)
+    s16 = torch.from_numpy(np.ascontiguousarray(u16).view(np.int16)).to(dev)
+    d16 = torch.empty(s8.numel() + 8, dtype=torch.int16, device=dev)
+    d8 = torch.empty(3 * s16.numel() + 8, dtype=torch.uint8, device=dev)
+    res = torch.empty(2, dtype=torch.int64, device=dev)
+    ln = torch.empty(1, dtype=torch.int64, device=dev)
+    calls = {"validate_utf8": lambda: codec.validate_utf8(s8, result=res),
+             "utf16_length_from_utf8": lambda: codec.utf16_length_from_utf8(s8, out=ln),
+             "convert_utf8_to_utf16le": lambda: codec.convert_utf8_to_utf16le(s8, d16, result=res),
+             "validate_utf16le": lambda: codec.validate_utf16le(s16, result=res),
+             "utf8_length_from_utf16le": lambda: codec.utf8_length_from_utf16le(s16, out=ln),
+             "convert_utf16le_to_utf8": lambda: codec.convert_utf16le_to_utf8(s16, d8, result=res)}
+    out = {"utf8_bytes": int(s8.numel()), "utf16_words": int(s16.numel()), "reps": args.small_reps,
+           "unit": "us per launch", "ops": {}}
+    for op, fn in calls.items():
+        for _ in range(5):
+            fn()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(args.small_reps)]
+        for e0, e1 in ev:
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+        torch.cuda.synchronize()
+        t = [e0.elapsed_time(e1) * 1e3 for e0, e1 in ev]
+        out["ops"][op] = {"min_us": round(min(t), 2), "median_us": round(statistics.median(t), 2)}
+    return out
 
 
 def run_sweep(args, codec, dev):
@@ -636,8 +681,11 @@ def run_serving(args, dev, dist, world):
 
 
 def run_e2e(args, codec, bufs, stream, dist, world, call):
-    """Same workload through host memory: each step copies its inputs from pinned host
-    buffers, runs the 30 calls, and copies results and both transcoded outputs back."""
+    """Same workload through host memory: each step copies every profile's inputs from pinned
+    host buffers, runs the 30 calls, and copies results and both transcoded outputs back.
+    Three streams pipeline the profiles: the host-to-device copy of profile i+1 and the
+    device-to-host copy of profile i-1 overlap the kernels of profile i (the kernels stay on
+    the context's one stream), and events order each buffer's reuse across steps."""
     import numpy as np
     import torch
     host = []
@@ -651,25 +699,53 @@ def run_e2e(args, codec, bufs, stream, dist, world, call):
         hres = torch.empty((6, 2), dtype=torch.int64, pin_memory=True)
         hlen = torch.empty((2, 1), dtype=torch.int64, pin_memory=True)
         host.append((h8, h16, o16, o8, hres, hlen))
+    s_in = torch.cuda.Stream(device=stream.device)
+    s_out = torch.cuda.Stream(device=stream.device)
+    done_compute = [None] * len(bufs)  # previous step's kernels on buffer i (its inputs are free after)
+    done_out = [None] * len(bufs)      # previous step's read-back of buffer i (its outputs are free after)
 
     def step():
-        for b, (h8, h16, o16, o8, hres, hlen) in zip(bufs, host):
-            b["s8"].copy_(h8, non_blocking=True)
-            b["s16"].copy_(h16, non_blocking=True)
+        for i, (b, (h8, h16, o16, o8, hres, hlen)) in enumerate(zip(bufs, host)):
+            if done_compute[i] is not None:
+                s_in.wait_event(done_compute[i])
+            with torch.cuda.stream(s_in):
+                b["s8"].copy_(h8, non_blocking=True)
+                b["s16"].copy_(h16, non_blocking=True)
+            ev_in = torch.cuda.Event()
+            ev_in.record(s_in)
+            stream.wait_event(ev_in)
+            if done_out[i] is not None:
+                stream.wait_event(done_out[i])
             for op in OPS:
                 call(b, op)
-            hres.copy_(b["res"], non_blocking=True)
-            hlen.copy_(b["len"], non_blocking=True)
-            o16.copy_(b["d16"], non_blocking=True)
-            o8.copy_(b["d8"], non_blocking=True)
+            ev_c = torch.cuda.Event()
+            ev_c.record(stream)
+            done_compute[i] = ev_c
+            s_out.wait_event(ev_c)
+            with torch.cuda.stream(s_out):
+                hres.copy_(b["res"], non_blocking=True)
+                hlen.copy_(b["len"], non_blocking=True)
+                o16.copy_(b["d16"], non_blocking=True)
+                o8.copy_(b["d8"], non_blocking=True)
+            ev_o = torch.cuda.Event()
+            ev_o.record(s_out)
+            done_out[i] = ev_o
+        stream.wait_stream(s_out)  # the step ends when its last read-back has landed
+        stream.wait_stream(s_in)
 
     step()
     torch.cuda.synchronize()
+    # the pipelined step gives the same results as the device-resident run
+    for b, (_, _, o16, o8, hres, hlen) in zip(bufs, host):
+        r = hres.tolist()
+        assert r[2][1] == b["n16"] and r[5][1] == b["n8"] and r[2][0] == 0 and r[5][0] == 0, (b["profile"], r)
     if dist:
         dist.barrier()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
+    s_in.wait_stream(stream)  # no copy of the timed steps starts before e0
+    s_out.wait_stream(stream)
     for _ in range(args.e2e_steps):
         step()
     e1.record(stream)
@@ -681,7 +757,9 @@ def run_e2e(args, codec, bufs, stream, dist, world, call):
     d2h = sum(2 * b["n16"] + b["n8"] + 6 * 16 + 2 * 8 for b in bufs)
     return {"value": round(in_all * args.e2e_steps / (ms * 1e-3) / 1e9, 2), "unit": "GB/s",
             "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "steps": args.e2e_steps,
-            "ms_per_step": round(ms / args.e2e_steps, 3)}
+            "ms_per_step": round(ms / args.e2e_steps, 3),
+            "pipeline": "host-to-device copies, kernels and device-to-host copies of consecutive profiles "
+                        "overlap on three streams"}
 
 
 def cpu_baseline(bufs, sample):

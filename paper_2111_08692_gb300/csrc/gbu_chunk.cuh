@@ -130,9 +130,9 @@ __device__ __forceinline__ uint32_t len8_of_word(uint32_t w) {
 }
 
 // ---- two UTF-16 words per 32-bit register ------------------------------------------------
-// Bit 15 of each 16-bit lane of the result is set where that word is >= 0x80, >= 0x800, a
-// surrogate (D800-DFFF), a first surrogate (D800-DBFF) or a second one (DC00-DFFF).  No
-// addition carries out of a lane (bit 15 is masked off first and the sums stay below 0x10000).
+// Bit 15 of each 16-bit lane of the result is set where that word is >= 0x80, >= 0x800 or a
+// surrogate (D800-DFFF).  No addition carries out of a lane (bit 15 is masked off first and
+// the sums stay below 0x10000).
 __device__ __forceinline__ uint32_t lanes16_nonzero(uint32_t t) {
   return (((t & 0x7FFF7FFFu) + 0x7FFF7FFFu) | t) & 0x80008000u;
 }
@@ -144,23 +144,6 @@ __device__ __forceinline__ uint32_t lanes16_ge800(uint32_t X) {
 }
 __device__ __forceinline__ uint32_t lanes16_sur(uint32_t X) {
   return ~lanes16_nonzero((X & 0xF800F800u) ^ 0xD800D800u) & 0x80008000u;
-}
-__device__ __forceinline__ uint32_t lanes16_high(uint32_t X) {
-  return ~lanes16_nonzero((X & 0xFC00FC00u) ^ 0xD800D800u) & 0x80008000u;
-}
-__device__ __forceinline__ uint32_t lanes16_low(uint32_t X) {
-  return ~lanes16_nonzero((X & 0xFC00FC00u) ^ 0xDC00DC00u) & 0x80008000u;
-}
-// Whether any of the 8 words is a surrogate (a test for "some lane is zero": exact as a
-// whole, although the per-lane bits it computes may not be).
-__device__ __forceinline__ bool any_surrogate16(const uint32_t W[4]) {
-  uint32_t z = 0;
-#pragma unroll
-  for (int k = 0; k < 4; ++k) {
-    const uint32_t t = (W[k] & 0xF800F800u) ^ 0xD800D800u;
-    z |= (t - 0x00010001u) & ~t;
-  }
-  return (z & 0x80008000u) != 0;
 }
 
 // UTF-8 bytes of the 8 words of a chunk inside the buffer: one per word, one more per word
@@ -177,18 +160,35 @@ __device__ __forceinline__ uint32_t utf16_len8_inside(const uint32_t W[4]) {
   return 8u + ((acc - sub) >> 7);
 }
 
+// Whether any of the 8 words is a surrogate (a test for "some lane is zero": exact as a
+// whole, although the per-lane bits it computes may not be).  A chunk without surrogate words
+// has no error: its neighbours judge their own words.
+__device__ __forceinline__ bool any_surrogate16(const uint32_t W[4]) {
+  uint32_t z = 0;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const uint32_t t = (W[k] & 0xF800F800u) ^ 0xD800D800u;
+    z |= (t - 0x00010001u) & ~t;
+  }
+  return (z & 0x80008000u) != 0;
+}
+
 // Unpaired surrogates among the 8 words of a chunk inside the buffer, given the word before
 // (prevw's high half) and after (nextw's low half): a first surrogate whose next word is not
-// a second one, or a second surrogate whose previous word is not a first one.
+// a second one, or a second surrogate whose previous word is not a first one.  The surrogate
+// flags are computed once per word and split by bit 10 (clear: first surrogate D800-DBFF,
+// set: second DC00-DFFF).
 __device__ __forceinline__ bool utf16_pair_errors_inside(const uint32_t W[4], uint32_t prevw, uint32_t nextw) {
   uint32_t H[5], L[5];
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
-    H[k + 1] = lanes16_high(W[k]);
-    L[k] = lanes16_low(W[k]);
+    const uint32_t S = lanes16_sur(W[k]);
+    const uint32_t b10 = W[k] << 5;  // bit 10 of each word at bit 15
+    H[k + 1] = S & ~b10;
+    L[k] = S & b10;
   }
-  H[0] = lanes16_high(prevw);
-  L[4] = lanes16_low(nextw);
+  H[0] = lanes16_sur(prevw) & ~(prevw << 5);
+  L[4] = lanes16_sur(nextw) & (nextw << 5);
   uint32_t err = 0;
 #pragma unroll
   for (int k = 0; k < 4; ++k) {

@@ -23,8 +23,13 @@ constexpr int ST_WARPS = STREAM_THREADS / 32;
 constexpr int ST_ROUNDS = 8;                              // 16-byte chunks per lane per tile
 constexpr uint32_t WT_BYTES = 32u * 16u * ST_ROUNDS;      // 4096 bytes per warp tile
 
+// Resident CTAs per SM the register budget is held to: three for the validations (at most 80
+// registers), four for the lengths (64).
 template <int MODE>
-__global__ void __launch_bounds__(STREAM_THREADS) stream_kernel(const Params p) {
+constexpr int stream_min_blocks() { return (MODE == S_L16 || MODE == S_L8) ? 4 : 3; }
+
+template <int MODE>
+__global__ void __launch_bounds__(STREAM_THREADS, stream_min_blocks<MODE>()) stream_kernel(const Params p) {
   __shared__ unsigned long long red[ST_WARPS];
   __shared__ int is_last;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
