@@ -362,6 +362,39 @@ int gbu_shard_cuts_utf16le_host(const uint16_t *src, uint64_t n, uint32_t P, uin
  * room.  GBU_BAD_ARGUMENT for NULL arrays, P out of range or decreasing cuts. */
 int gbu_combine_shards(const uint64_t *cuts, const gbu_result *parts, uint32_t P, gbu_result *out);
 
+/* ---- Resumable (chunked) form ----------------------------------------------------------------
+ * One input that arrives in pieces (from a file or a socket, into host memory) validated or
+ * transcoded piece by piece, with the same results as one call on the whole input.  Not in the
+ * paper, which transcodes whole buffers; it serves the disk- and network-rate inputs its
+ * introduction motivates (Section 1).  Each push sees the characters the previous push held
+ * back followed by the new chunk; it holds back a trailing incomplete character (at most three
+ * bytes of a UTF-8 sequence whose leading byte is C2-F4, or one UTF-16 first surrogate) and runs
+ * the single-buffer call on the rest, which starts and ends at character starts.  A push with
+ * last != 0 holds nothing back, so an incomplete final character fails there (GBU_TOO_SHORT, or
+ * GBU_SURROGATE for a final first surrogate).
+ *
+ * gbu_chunked_create: op is GBU_OP_VALIDATE_UTF8, _VALIDATE_UTF16LE, _CONVERT_UTF8_TO_UTF16LE or
+ * _CONVERT_UTF16LE_TO_UTF8; max_chunk_units bounds n in each push.  Allocates its context,
+ * device buffers and a stream here (never on a push).  NULL on failure.
+ * gbu_chunked_push: chunk = n input code units in HOST memory (any host memory); out = HOST
+ * buffer of out_cap output units (transcoders; may be NULL for validation).  Synchronous.
+ *   *out_n  = output units written to out by this push (the outputs of consecutive pushes
+ *             concatenate to the output of the whole input);
+ *   *result = {GBU_OK, input units judged so far (validation) or output units written so far
+ *             (transcoding)}; or the first error {kind, offset in input units from the start of
+ *             the whole input} -- sticky: later pushes return it again and write nothing; or
+ *             {GBU_OUTPUT_TOO_SMALL, units needed} when out_cap is too small for this push's
+ *             output (nothing was consumed: repeat the push with a larger buffer); or GBU_TIMEOUT.
+ *   Return value: GBU_OK, GBU_BAD_ARGUMENT (n > max_chunk_units, NULL pointers, misaligned
+ *   UTF-16, a push after the last one) or GBU_CUDA_ERROR.
+ * gbu_chunked_reset starts a new input; gbu_chunked_destroy frees everything. */
+typedef struct gbu_chunked gbu_chunked;
+gbu_chunked *gbu_chunked_create(int device, int op, uint64_t max_chunk_units);
+int gbu_chunked_push(gbu_chunked *s, const void *chunk, uint64_t n, int last, void *out, uint64_t out_cap,
+                     uint64_t *out_n, gbu_result *result);
+int gbu_chunked_reset(gbu_chunked *s);
+void gbu_chunked_destroy(gbu_chunked *s);
+
 /* Number of kernel launches the library made through this context so far (for accounting). */
 uint64_t gbu_launch_count(const gbu_ctx *ctx);
 

@@ -107,6 +107,15 @@ def lib() -> ctypes.CDLL:
                 getattr(L, name).argtypes = [vp, u64, u32, vp]
             L.gbu_combine_shards.restype = i32
             L.gbu_combine_shards.argtypes = [vp, vp, u32, vp]
+            L.gbu_chunked_create.restype = vp
+            L.gbu_chunked_create.argtypes = [i32, i32, u64]
+            L.gbu_chunked_push.restype = i32
+            L.gbu_chunked_push.argtypes = [vp, vp, u64, i32, vp, u64, ctypes.POINTER(ctypes.c_uint64),
+                                           ctypes.POINTER(GbuResult)]
+            L.gbu_chunked_reset.restype = i32
+            L.gbu_chunked_reset.argtypes = [vp]
+            L.gbu_chunked_destroy.restype = None
+            L.gbu_chunked_destroy.argtypes = [vp]
             L.gbu_launch_count.restype = u64
             L.gbu_launch_count.argtypes = [vp]
             L.gbu_launch_config.restype = i32
@@ -560,6 +569,48 @@ def convert_utf8_to_utf16le_noalloc(src, dst, result, stream=None, cap=None):
                                                result.data_ptr(), s),
            "gbu_convert_utf8_to_utf16le_noalloc")
     return result
+
+
+class Chunked:
+    """The resumable form (gbu_chunked_*): push host chunks of one input (numpy uint8 for
+    UTF-8, uint16 for UTF-16LE); each push returns (output units as a numpy array, (status
+    name, count)) with the same meaning as the C call."""
+
+    def __init__(self, op: str, max_chunk_units: int, device: int = 0):
+        self.op = op
+        self.handle = lib().gbu_chunked_create(device, OP_CODE[op], max_chunk_units)
+        if not self.handle:
+            raise GbuError("gbu_chunked_create failed")
+        self.out_dtype = {"convert_utf8_to_utf16le": "uint16", "convert_utf16le_to_utf8": "uint8"}.get(op)
+        self.max_chunk = max_chunk_units
+
+    def push(self, chunk, last: bool = False, out_cap: int | None = None):
+        import numpy as np
+        chunk = np.ascontiguousarray(chunk)
+        n = chunk.size
+        if out_cap is None:
+            out_cap = (n + 4) * (3 if self.op == "convert_utf16le_to_utf8" else 1)
+        out = np.empty(out_cap if self.out_dtype else 0, dtype=self.out_dtype or "uint8")
+        out_n = ctypes.c_uint64(0)
+        res = GbuResult()
+        _check(lib().gbu_chunked_push(self.handle, chunk.ctypes.data if n else None, n, 1 if last else 0,
+                                      out.ctypes.data if out.size else None, out.size, ctypes.byref(out_n),
+                                      ctypes.byref(res)), "gbu_chunked_push")
+        return out[:out_n.value], (STATUS.get(res.status, res.status), int(res.count))
+
+    def reset(self):
+        _check(lib().gbu_chunked_reset(self.handle), "gbu_chunked_reset")
+
+    def close(self):
+        if self.handle:
+            lib().gbu_chunked_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Graph:
