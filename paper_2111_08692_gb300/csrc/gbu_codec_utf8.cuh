@@ -6,9 +6,9 @@
 // idiom; here a warp handles a 512-byte region, one 16-byte chunk per lane:
 //   * the chunk is classified and validated as in gbu_chunk.cuh;
 //   * output: one UTF-16 word per leading byte, two for a four-byte sequence, counted on the
-//     leading byte; word offsets are prefix sums of per-byte counts (bytes inside a word via
-//     a multiply by 0x01010101, lanes via a warp scan, regions via the partition count, and
-//     partitions via the look-back);
+//     leading byte; word offsets are prefix sums of per-byte counts (a lane's chunk by byte
+//     dot products in the count pass and a running index while staging, lanes via a warp
+//     scan, regions via the partition count, and partitions via the look-back);
 //   * an all-ASCII warp widens its bytes directly (Section 4's ASCII path).
 // A lane whose chunk breaks any check reports the chunk start; the last CTA turns the
 // smallest one into the exact offset and kind (resolve_utf8_error).
