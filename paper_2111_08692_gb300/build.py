@@ -63,14 +63,39 @@ KERNEL_SOURCES = {
 }
 
 
+def strip_comments(text: str) -> str:
+    """C/C++ source without its comments and blank lines (string and character literals are
+    kept as they are), so that editing a comment does not change a kernel's hash."""
+    out, i, n = [], 0, len(text)
+    while i < n:
+        c = text[i]
+        if c in "\"'":
+            j = i + 1
+            while j < n and text[j] != c:
+                j += 2 if text[j] == "\\" else 1
+            out.append(text[i:j + 1])
+            i = j + 1
+        elif text.startswith("//", i):
+            j = text.find("\n", i)
+            i = n if j < 0 else j
+        elif text.startswith("/*", i):
+            j = text.find("*/", i + 2)
+            i = n if j < 0 else j + 2
+        else:
+            out.append(c)
+            i += 1
+    lines = ["".join(ln.split()) for ln in "".join(out).splitlines()]
+    return "\n".join(ln for ln in lines if ln)
+
+
 def kernel_hash(op: str) -> str:
-    """Short hash of the sources of the kernel behind single-buffer operation `op` (ties an ncu
-    capture of that kernel to the code it measured)."""
+    """Short hash of the sources of the kernel behind single-buffer operation `op`, comments left
+    out (ties an ncu capture of that kernel to the code it measured)."""
     import hashlib
     h = hashlib.sha1()
     for name in KERNEL_SOURCES[op]:
         h.update(name.encode())
-        h.update(open(os.path.join(CSRC, name), "rb").read())
+        h.update(strip_comments(open(os.path.join(CSRC, name)).read()).encode())
     return h.hexdigest()[:12]
 
 
