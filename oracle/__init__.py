@@ -93,6 +93,13 @@ class Codec:
         for name in ("or_convert_utf8_to_utf16le", "or_convert_utf16le_to_utf8"):
             getattr(L, name).restype = Result
             getattr(L, name).argtypes = [vp, sz, vp, sz]
+        L.or_validate_utf16be.restype = Result
+        L.or_validate_utf16be.argtypes = [vp, sz]
+        L.or_utf8_length_from_utf16be.restype = ctypes.c_uint64
+        L.or_utf8_length_from_utf16be.argtypes = [vp, sz]
+        for name in ("or_convert_utf16be_to_utf8", "or_convert_utf8_to_utf16be"):
+            getattr(L, name).restype = Result
+            getattr(L, name).argtypes = [vp, sz, vp, sz]
         for name in ("or_validate_utf8_batched", "or_validate_utf16le_batched"):
             getattr(L, name).restype = None
             getattr(L, name).argtypes = [vp, vp, sz, vp]
@@ -133,6 +140,32 @@ class Codec:
             cap = self.utf8_length_from_utf16le(a)
         dst = np.zeros(cap, dtype=np.uint8)
         r = self.lib.or_convert_utf16le_to_utf8(_ptr(a), a.size, _ptr(dst), cap)
+        return r.as_tuple(), dst
+
+    # UTF-16BE: uint16 arrays holding the words as they lie in memory (big-endian bytes), e.g.
+    # a little-endian word array after .byteswap()
+    def validate_utf16be(self, src):
+        a = _u16(src)
+        return self.lib.or_validate_utf16be(_ptr(a), a.size).as_tuple()
+
+    def utf8_length_from_utf16be(self, src) -> int:
+        a = _u16(src)
+        return int(self.lib.or_utf8_length_from_utf16be(_ptr(a), a.size))
+
+    def convert_utf16be_to_utf8(self, src, cap=None):
+        a = _u16(src)
+        if cap is None:
+            cap = self.utf8_length_from_utf16be(a)
+        dst = np.zeros(cap, dtype=np.uint8)
+        r = self.lib.or_convert_utf16be_to_utf8(_ptr(a), a.size, _ptr(dst), cap)
+        return r.as_tuple(), dst
+
+    def convert_utf8_to_utf16be(self, src, cap=None):
+        a = _u8(src)
+        if cap is None:
+            cap = self.utf16_length_from_utf8(a)
+        dst = np.zeros(cap, dtype=np.uint16)
+        r = self.lib.or_convert_utf8_to_utf16be(_ptr(a), a.size, _ptr(dst), cap)
         return r.as_tuple(), dst
 
     def validate_utf8_batched(self, src, off):
@@ -215,3 +248,19 @@ def convert_utf8_to_utf16le_batched(src, off, dst_off):
 
 def convert_utf16le_to_utf8_batched(src, off, dst_off):
     return default().convert_utf16le_to_utf8_batched(src, off, dst_off)
+
+
+def validate_utf16be(src):
+    return default().validate_utf16be(src)
+
+
+def utf8_length_from_utf16be(src) -> int:
+    return default().utf8_length_from_utf16be(src)
+
+
+def convert_utf16be_to_utf8(src, cap=None):
+    return default().convert_utf16be_to_utf8(src, cap)
+
+
+def convert_utf8_to_utf16be(src, cap=None):
+    return default().convert_utf8_to_utf16be(src, cap)

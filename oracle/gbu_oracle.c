@@ -1,5 +1,5 @@
 /*
- * gbu_oracle.c -- scalar CPU reference codec for UTF-8 and UTF-16LE.
+ * gbu_oracle.c -- scalar CPU reference codec for UTF-8 and UTF-16 (LE and BE).
  *
  * TEST INFRASTRUCTURE ONLY: see gbu_oracle.h.  Plain C, one character at a time, no tables,
  * no blocking, no SIMD.  Nothing here is shared with the CUDA library.
@@ -20,7 +20,9 @@
  *     interval, and the sequence fails as soon as that whole interval breaks rule 4, 5 or 6;
  *     a missing continuation byte is rule 2 (TOO_SHORT), also at the end of the buffer;
  *   - rule 5's bound is "less than 1,114,112" (Section 1 prints "between 0 and 1,114,112");
- *   - the byte-order mark and noncharacters are ordinary characters; UTF-16 is little endian.
+ *   - the byte-order mark and noncharacters are ordinary characters; UTF-16 is little endian
+ *     (the UTF-16BE functions at the end take the same words with their bytes in big-endian
+ *     order, as RFC 2781 serialises them, and there is no byte-order-mark sniffing).
  *
  * Parity pins (tests/test_oracle_pins.py): boundary scalars and invalid sequences derived by
  * hand from Section 3 (tests/golden/), a round trip of all 1,112,064 scalar values against
@@ -31,6 +33,8 @@
  * completion of the bytes read).
  */
 #include "gbu_oracle.h"
+
+#include <stdlib.h>
 
 /* Section 3: payload bits carried by a leading byte, by sequence length 1..4. */
 static const uint8_t LEAD_PAYLOAD_MASK[5] = {0x00, 0x7F, 0x1F, 0x0F, 0x07};
@@ -239,4 +243,44 @@ void or_convert_utf16le_to_utf8_batched(const uint16_t *src, const uint64_t *off
   for (size_t s = 0; s < B; ++s)
     res[s] = or_convert_utf16le_to_utf8(src + off[s], off[s + 1] - off[s], dst + dst_off[s],
                                         dst_off[s + 1] - dst_off[s]);
+}
+
+/* UTF-16BE: the UTF-16 words of Section 3 with each word's most significant byte first (RFC
+ * 2781).  src and dst hold the words as they lie in memory, so each is read (written) with its
+ * two bytes exchanged; the scan is the UTF-16LE one on the exchanged words. */
+static uint16_t swap16(uint16_t w) { return (uint16_t)((w >> 8) | (w << 8)); }
+
+static uint16_t *swapped_copy(const uint16_t *src, size_t n) {
+  uint16_t *t = (uint16_t *)malloc((n ? n : 1) * sizeof(uint16_t));
+  if (!t) abort();
+  for (size_t i = 0; i < n; ++i) t[i] = swap16(src[i]);
+  return t;
+}
+
+or_result or_validate_utf16be(const uint16_t *src, size_t n) {
+  uint16_t *t = swapped_copy(src, n);
+  or_result r = or_validate_utf16le(t, n);
+  free(t);
+  return r;
+}
+
+uint64_t or_utf8_length_from_utf16be(const uint16_t *src, size_t n) {
+  uint16_t *t = swapped_copy(src, n);
+  uint64_t len = or_utf8_length_from_utf16le(t, n);
+  free(t);
+  return len;
+}
+
+or_result or_convert_utf16be_to_utf8(const uint16_t *src, size_t n, uint8_t *dst, size_t cap) {
+  uint16_t *t = swapped_copy(src, n);
+  or_result r = or_convert_utf16le_to_utf8(t, n, dst, cap);
+  free(t);
+  return r;
+}
+
+or_result or_convert_utf8_to_utf16be(const uint8_t *src, size_t n, uint16_t *dst, size_t cap) {
+  or_result r = or_convert_utf8_to_utf16le(src, n, dst, cap);
+  const uint64_t written = r.status == OR_OK ? r.count : cap;  /* every unit written (at most cap) */
+  for (uint64_t i = 0; i < written && i < cap; ++i) dst[i] = swap16(dst[i]);
+  return r;
 }

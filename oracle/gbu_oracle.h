@@ -1,5 +1,5 @@
 /*
- * gbu_oracle.h -- scalar CPU reference codec for UTF-8 and UTF-16LE.
+ * gbu_oracle.h -- scalar CPU reference codec for UTF-8 and UTF-16 (LE and BE).
  *
  * TEST INFRASTRUCTURE ONLY.  The test suite, the smoke check and the CPU-baseline leg of the
  * benchmark call this code; the CUDA library never includes, links or calls it, and this code
@@ -57,6 +57,13 @@ uint64_t or_utf8_length_from_utf16le(const uint16_t *src, size_t n);
  * prefix src[0:count] (clipped to cap). */
 or_result or_convert_utf8_to_utf16le(const uint8_t *src, size_t n, uint16_t *dst, size_t cap);
 or_result or_convert_utf16le_to_utf8(const uint16_t *src, size_t n, uint8_t *dst, size_t cap);
+
+/* UTF-16BE forms (RFC 2781 byte order: each word's most significant byte first in memory).
+ * src / dst hold the words as they lie in memory; results as for the UTF-16LE forms. */
+or_result or_validate_utf16be(const uint16_t *src, size_t n);
+uint64_t or_utf8_length_from_utf16be(const uint16_t *src, size_t n);
+or_result or_convert_utf16be_to_utf8(const uint16_t *src, size_t n, uint8_t *dst, size_t cap);
+or_result or_convert_utf8_to_utf16be(const uint8_t *src, size_t n, uint16_t *dst, size_t cap);
 
 /* Batched forms: a plain loop over B strings given as CSR offsets (B+1 entries, in input code
  * units).  Transcoders write string i at dst + dst_off[i] with capacity

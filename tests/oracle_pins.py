@@ -120,6 +120,36 @@ def check_all_scalars(codec):
     assert int(sizes.sum()) == u8.size
 
 
+def check_all_scalars_utf16be(codec):
+    """UTF-16BE (RFC 2781 byte order) against CPython's utf-16-be codec: every scalar value
+    round trips, and the first unpaired surrogate of random word strings is where CPython's
+    strict decoder reports it."""
+    cps = all_scalars()
+    s = cps.astype("<u4").tobytes().decode("utf-32-le")
+    u8 = np.frombuffer(s.encode("utf-8"), dtype=np.uint8)
+    be = np.frombuffer(s.encode("utf-16-be"), dtype=np.uint16)  # the words as they lie in memory
+    assert codec.validate_utf16be(be) == ("OK", be.size)
+    assert codec.utf8_length_from_utf16be(be) == u8.size
+    r, d = codec.convert_utf16be_to_utf8(be)
+    assert r == ("OK", u8.size) and np.array_equal(d, u8)
+    r, d = codec.convert_utf8_to_utf16be(u8)
+    assert r == ("OK", be.size) and d.tobytes() == s.encode("utf-16-be")
+    rng = np.random.default_rng(7)
+    words = np.array([0x41, 0x3B1, 0x4E2D, 0xD800, 0xDBFF, 0xDC00, 0xDFFF, 0xE000, 0xFFFD], dtype=">u2")
+    for _ in range(20000):
+        w = rng.choice(words, size=int(rng.integers(1, 9)))
+        raw = w.tobytes()  # big-endian bytes
+        mem = np.frombuffer(raw, dtype=np.uint16)
+        try:
+            raw.decode("utf-16-be")
+            want = ("OK", mem.size)
+        except UnicodeDecodeError as e:
+            want = ("SURROGATE", e.start // 2)
+        assert codec.validate_utf16be(mem) == want, (raw.hex(), want)
+        r, _ = codec.convert_utf16be_to_utf8(mem)
+        assert r == (want if want[0] != "OK" else ("OK", len(raw.decode("utf-16-be").encode("utf-8"))))
+
+
 def check_bruteforce(bf, max_len=3):
     """Every UTF-8 string of 1..max_len bytes against the second formulation."""
     assert bf.mixed_dead_prefixes() == 0
