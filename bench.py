@@ -51,6 +51,7 @@ def parse():
                     help="strings timed through the per-string launch loop")
     ap.add_argument("--no-sweep", action="store_true")
     ap.add_argument("--no-small", action="store_true", help="skip the L2-resident 1 MiB latency table")
+    ap.add_argument("--no-be", action="store_true", help="skip the UTF-16BE leg")
     ap.add_argument("--small-reps", type=int, default=200)
     ap.add_argument("--sweep-size", type=int, default=256 << 20, help="UTF-8 bytes per invalid-input sweep buffer")
     ap.add_argument("--sweep-reps", type=int, default=5)
@@ -355,6 +356,8 @@ def run_ours(args):
         line["sweep"] = run_sweep(args, codec, dev)
     if not args.no_small:
         line["l2_resident_1mib"] = run_small(args, codec, dev)
+    if not args.no_be:
+        line["utf16be"] = run_be(args, codec, bufs, stream, peak)
     if not args.no_batched and args.batched_strings > 0:
         line["batched"] = run_batched(args, codec, dev, dist, world)
     if not args.no_serving:
@@ -364,6 +367,48 @@ def run_ours(args):
     codec.close()
     if dist:
         dist.destroy_process_group()
+
+
+def run_be(args, codec, bufs, stream, peak, reps=3):
+    """The UTF-16BE calls on the same buffers: each profile's UTF-16 buffer with its words'
+    bytes exchanged (the same text in big-endian order), and its UTF-8 buffer transcoded to
+    UTF-16BE.  Mean of `reps` launches after one untimed, CUDA events on the launching stream;
+    the fraction counts input + output bytes against the measured copy bandwidth."""
+    import torch
+    from paper_2111_08692_gb300 import result_tuple
+    out = {"reps": reps, "ops": {}}
+    for b in bufs:
+        be = b["s16"].view(torch.uint8).view(-1, 2).flip(1).contiguous().view(torch.int16).view(-1)
+        res = torch.empty(2, dtype=torch.int64, device=be.device)
+        ln = torch.empty(1, dtype=torch.int64, device=be.device)
+        n16, n8 = b["n16"], b["n8"]
+        calls = {"validate_utf16be": (lambda: codec.validate_utf16be(be, result=res), 2 * be.numel(), 0),
+                 "utf8_length_from_utf16be": (lambda: codec.utf8_length_from_utf16be(be, out=ln), 2 * be.numel(), 0),
+                 "convert_utf16be_to_utf8": (lambda: codec.convert_utf16be_to_utf8(be, b["d8"], result=res),
+                                             2 * be.numel(), n8),
+                 "convert_utf8_to_utf16be": (lambda: codec.convert_utf8_to_utf16be(b["s8"], b["d16"], result=res),
+                                             b["s8"].numel(), 2 * n16)}
+        for op, (fn, inb, outb) in calls.items():
+            fn()
+            torch.cuda.synchronize()
+            if op.startswith("convert") or op.startswith("validate"):
+                r = result_tuple(res)
+                assert r[0] == "OK", (b["profile"], op, r)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(reps):
+                fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / reps
+            out["ops"].setdefault(op, {})[b["profile"]] = {
+                "ms": round(ms, 4), "input_gbs": round(inb / ms / 1e6, 1),
+                "frac": round((inb + outb) / ms / 1e6 / peak, 3)}
+        assert int(ln.item()) == n8
+        del be
+        torch.cuda.empty_cache()
+    return out
 
 
 def run_small(args, codec, dev):

@@ -122,6 +122,20 @@ int gbu_convert_utf8_to_utf16le(gbu_ctx *ctx, const uint8_t *src, uint64_t n, ui
 int gbu_convert_utf16le_to_utf8(gbu_ctx *ctx, const uint16_t *src, uint64_t n, uint8_t *dst,
                                 uint64_t cap, gbu_result *result, gbu_stream stream);
 
+/* UTF-16BE: the same words as UTF-16LE (Section 3) with each word's most significant byte first
+ * in memory (the byte order RFC 2781 names; no byte-order-mark sniffing).  src / dst are the
+ * words as they lie in memory (2-byte aligned).  Results, units, capacities, error offsets and
+ * return values are exactly those of the UTF-16LE calls on the byte-exchanged words; the UTF-16
+ * length of a UTF-8 input is gbu_utf16_length_from_utf8's. */
+int gbu_validate_utf16be(gbu_ctx *ctx, const uint16_t *src, uint64_t n, gbu_result *result,
+                         gbu_stream stream);
+int gbu_utf8_length_from_utf16be(gbu_ctx *ctx, const uint16_t *src, uint64_t n, uint64_t *len,
+                                 gbu_stream stream);
+int gbu_convert_utf16be_to_utf8(gbu_ctx *ctx, const uint16_t *src, uint64_t n, uint8_t *dst,
+                                uint64_t cap, gbu_result *result, gbu_stream stream);
+int gbu_convert_utf8_to_utf16be(gbu_ctx *ctx, const uint8_t *src, uint64_t n, uint16_t *dst,
+                                uint64_t cap, gbu_result *result, gbu_stream stream);
+
 /* ---- Batched forms ------------------------------------------------------------------------
  * The same six operations over B strings in ONE launch (a persistent grid; strings never wait
  * on one another).  The strings lie back to back in src; string i is src[off[i] : off[i+1]]

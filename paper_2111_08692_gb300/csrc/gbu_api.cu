@@ -14,8 +14,9 @@
 
 namespace {
 
-// The six kernels, in the order gbu_launch_config reports them.
-enum Kernel { K_V8 = 0, K_L8, K_C8, K_V16, K_L16, K_C16, K_COUNT };
+// The six kernels, in the order gbu_launch_config reports them (K_COUNT is also the number of
+// batched operations), then the UTF-16BE kernels.
+enum Kernel { K_V8 = 0, K_L8, K_C8, K_V16, K_L16, K_C16, K_COUNT, K_V16BE = K_COUNT, K_L16BE, K_C16BE, K_C8BE, K_ALL };
 
 const void *kernel_ptr(int k) {
   switch (k) {
@@ -24,13 +25,19 @@ const void *kernel_ptr(int k) {
     case K_V16: return gbu::stream_kernel_ptr(2);
     case K_L16: return gbu::stream_kernel_ptr(3);
     case K_C8: return gbu::utf8_to_utf16_kernel_ptr();
+    case K_V16BE: return gbu::stream_kernel_ptr(4);
+    case K_L16BE: return gbu::stream_kernel_ptr(5);
+    case K_C16BE: return gbu::utf16be_to_utf8_kernel_ptr();
+    case K_C8BE: return gbu::utf8_to_utf16be_kernel_ptr();
     default: return gbu::utf16_to_utf8_kernel_ptr();
   }
 }
-bool is_transcoder(int k) { return k == K_C8 || k == K_C16; }
+bool is_transcoder(int k) { return k == K_C8 || k == K_C16 || k == K_C16BE || k == K_C8BE; }
 size_t kernel_smem(int k) {
   if (k == K_C8) return gbu::utf8_to_utf16_smem_bytes();
   if (k == K_C16) return gbu::utf16_to_utf8_smem_bytes();
+  if (k == K_C16BE) return gbu::utf16be_to_utf8_smem_bytes();
+  if (k == K_C8BE) return gbu::utf8_to_utf16be_smem_bytes();
   return 0;
 }
 int kernel_threads(int k) { return is_transcoder(k) ? gbu::XT : gbu::STREAM_THREADS; }
@@ -63,7 +70,7 @@ struct gbu_ctx {
   uint32_t wait_limit;
   long long skip_tile;
   uint32_t early_exit;
-  int blocks_per_sm[K_COUNT];
+  int blocks_per_sm[K_ALL];
   int batch_blocks_per_sm[K_COUNT][3];  // per batched mode and warps per CTA (4, 8, 16)
   int scan_blocks_per_sm;
   int seg_blocks_per_sm[2];             // several-string transcoders: 8 -> 16, 16 -> 8
@@ -122,7 +129,7 @@ extern "C" gbu_ctx *gbu_create(int device, uint64_t max_units) {
     delete c;
     return nullptr;
   }
-  for (int k = 0; k < K_COUNT; ++k) {
+  for (int k = 0; k < K_ALL; ++k) {
     const void *f = kernel_ptr(k);
     const size_t smem = kernel_smem(k);
     int bps = 0;
@@ -332,6 +339,50 @@ extern "C" int gbu_convert_utf16le_to_utf8(gbu_ctx *c, const uint16_t *src, uint
   p.result = result;
   set_dst(&p, dst, cap, 1);
   return launch(c, K_C16, p, stream);
+}
+
+// ---- UTF-16BE ----------------------------------------------------------------------------
+
+extern "C" int gbu_validate_utf16be(gbu_ctx *c, const uint16_t *src, uint64_t n, gbu_result *result,
+                                    gbu_stream stream) {
+  gbu::Params p;
+  int rc = make_params(c, K_V16BE, src, n, 2, false, &p);
+  if (rc != GBU_OK) return rc;
+  if (!result) return GBU_BAD_ARGUMENT;
+  p.result = result;
+  return launch(c, K_V16BE, p, stream);
+}
+
+extern "C" int gbu_utf8_length_from_utf16be(gbu_ctx *c, const uint16_t *src, uint64_t n, uint64_t *len,
+                                            gbu_stream stream) {
+  gbu::Params p;
+  int rc = make_params(c, K_L16BE, src, n, 2, false, &p);
+  if (rc != GBU_OK) return rc;
+  if (!len) return GBU_BAD_ARGUMENT;
+  p.len_out = len;
+  return launch(c, K_L16BE, p, stream);
+}
+
+extern "C" int gbu_convert_utf16be_to_utf8(gbu_ctx *c, const uint16_t *src, uint64_t n, uint8_t *dst,
+                                           uint64_t cap, gbu_result *result, gbu_stream stream) {
+  gbu::Params p;
+  int rc = make_params(c, K_C16BE, src, n, 2, false, &p);
+  if (rc != GBU_OK) return rc;
+  if (!result || (cap > 0 && !dst)) return GBU_BAD_ARGUMENT;
+  p.result = result;
+  set_dst(&p, dst, cap, 1);
+  return launch(c, K_C16BE, p, stream);
+}
+
+extern "C" int gbu_convert_utf8_to_utf16be(gbu_ctx *c, const uint8_t *src, uint64_t n, uint16_t *dst,
+                                           uint64_t cap, gbu_result *result, gbu_stream stream) {
+  gbu::Params p;
+  int rc = make_params(c, K_C8BE, src, n, 1, true, &p);
+  if (rc != GBU_OK) return rc;
+  if (!result || (cap > 0 && !dst) || ((uintptr_t)dst & 1)) return GBU_BAD_ARGUMENT;
+  p.result = result;
+  set_dst(&p, dst, cap, 2);
+  return launch(c, K_C8BE, p, stream);
 }
 
 // ---- batched forms -----------------------------------------------------------------------

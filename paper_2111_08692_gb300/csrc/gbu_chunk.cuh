@@ -268,16 +268,22 @@ static __device__ __noinline__ void resolve_utf8_error(const uint8_t *s, uint64_
 }
 
 // UTF-16: a word is flagged exactly when it is the first word of an ill-formed sequence, so
-// the first error lies in the flagged chunk [chunk, chunk + 8).
+// the first error lies in the flagged chunk [chunk, chunk + 8).  BE: the words lie in memory
+// with their bytes in big-endian order.
+template <bool BE = false>
 static __device__ __noinline__ void resolve_utf16_error(const uint16_t *s, uint64_t n, long long chunk,
                                                         uint64_t *off) {
+  auto word = [&](long long i) -> uint32_t {
+    const uint32_t w = s[i];
+    return BE ? ((w >> 8) | ((w & 0xFFu) << 8)) : w;
+  };
   long long i = chunk < 0 ? 0 : chunk;
-  if (i > 0 && i < (long long)n && is_low16(s[i]) && is_high16(s[i - 1])) --i;
+  if (i > 0 && i < (long long)n && is_low16(word(i)) && is_high16(word(i - 1))) --i;
   const long long stop = (chunk + 64) < (long long)n ? chunk + 64 : (long long)n;
   while (i < stop) {
-    const uint32_t w = s[i];
+    const uint32_t w = word(i);
     if ((w & 0xF800u) != 0xD800u) { ++i; continue; }
-    if (is_high16(w) && i + 1 < (long long)n && is_low16(s[i + 1])) { i += 2; continue; }
+    if (is_high16(w) && i + 1 < (long long)n && is_low16(word(i + 1))) { i += 2; continue; }
     *off = (uint64_t)i;
     return;
   }

@@ -7,7 +7,7 @@
 namespace gbu {
 
 // read-only streaming kernels; mode: 0 validate_utf8, 1 utf16_length_from_utf8,
-// 2 validate_utf16le, 3 utf8_length_from_utf16le
+// 2 validate_utf16le, 3 utf8_length_from_utf16le, 4 validate_utf16be, 5 utf8_length_from_utf16be
 const void *stream_kernel_ptr(int mode);
 uint32_t stream_tile_bytes();
 
@@ -17,6 +17,11 @@ const void *utf8_to_utf16_kernel_ptr();
 const void *utf16_to_utf8_kernel_ptr();
 size_t utf8_to_utf16_smem_bytes();
 size_t utf16_to_utf8_smem_bytes();
+// the transcoders between UTF-8 and UTF-16BE (same launch shape as the UTF-16LE ones)
+const void *utf16be_to_utf8_kernel_ptr();
+size_t utf16be_to_utf8_smem_bytes();
+const void *utf8_to_utf16be_kernel_ptr();
+size_t utf8_to_utf16be_smem_bytes();
 // the same transcoders over several strings per launch (SegParams; same shared memory)
 const void *utf8_to_utf16_segments_kernel_ptr();
 const void *utf16_to_utf8_segments_kernel_ptr();

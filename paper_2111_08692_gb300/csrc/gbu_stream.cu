@@ -17,7 +17,14 @@
 
 namespace gbu {
 
-enum StreamMode { S_V8 = 0, S_L16 = 1, S_V16 = 2, S_L8 = 3 };
+enum StreamMode { S_V8 = 0, S_L16 = 1, S_V16 = 2, S_L8 = 3, S_V16BE = 4, S_L8BE = 5 };
+
+// A UTF-16BE mode runs its UTF-16LE mode on words whose two bytes it exchanges after loading.
+template <int MODE>
+__host__ __device__ constexpr int base_mode() { return MODE == S_V16BE ? S_V16 : (MODE == S_L8BE ? S_L8 : MODE); }
+template <int MODE>
+__host__ __device__ constexpr bool big_endian() { return MODE == S_V16BE || MODE == S_L8BE; }
+__device__ __forceinline__ uint32_t swap16x2(uint32_t w) { return __byte_perm(w, 0, 0x2301); }
 
 constexpr int ST_WARPS = STREAM_THREADS / 32;
 constexpr int ST_ROUNDS = 8;                              // 16-byte chunks per lane per tile
@@ -26,10 +33,14 @@ constexpr uint32_t WT_BYTES = 32u * 16u * ST_ROUNDS;      // 4096 bytes per warp
 // Resident CTAs per SM the register budget is held to: three for the validations (at most 80
 // registers), four for the lengths (64).
 template <int MODE>
-constexpr int stream_min_blocks() { return (MODE == S_L16 || MODE == S_L8) ? 4 : 3; }
+__host__ __device__ constexpr int stream_min_blocks() {
+  return (base_mode<MODE>() == S_L16 || base_mode<MODE>() == S_L8) ? 4 : 3;
+}
 
-template <int MODE>
-__global__ void __launch_bounds__(STREAM_THREADS, stream_min_blocks<MODE>()) stream_kernel(const Params p) {
+template <int KMODE>
+__global__ void __launch_bounds__(STREAM_THREADS, stream_min_blocks<KMODE>()) stream_kernel(const Params p) {
+  constexpr int MODE = base_mode<KMODE>();
+  constexpr bool BE = big_endian<KMODE>();
   __shared__ unsigned long long red[ST_WARPS];
   __shared__ int is_last;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -73,6 +84,13 @@ __global__ void __launch_bounds__(STREAM_THREADS, stream_min_blocks<MODE>()) str
     } else {
       pre = load_word_checked(p, t0 - 4);
       post = load_word_checked(p, t0 + WT_BYTES);
+    }
+    if (BE) {
+#pragma unroll
+      for (int r = 0; r < ST_ROUNDS; ++r)
+        v[r] = make_uint4(swap16x2(v[r].x), swap16x2(v[r].y), swap16x2(v[r].z), swap16x2(v[r].w));
+      pre = swap16x2(pre);
+      post = swap16x2(post);
     }
     if (MODE == S_V8 || MODE == S_L16) {
       uint32_t any = 0;
@@ -215,8 +233,8 @@ __global__ void __launch_bounds__(STREAM_THREADS, stream_min_blocks<MODE>()) str
       write_result(p.result, kind, off);
     } else {
       uint64_t off;
-      resolve_utf16_error(reinterpret_cast<const uint16_t *>(p.base + p.off0), p.n,
-                          ((long long)key - (long long)p.off0) / 2, &off);
+      resolve_utf16_error<BE>(reinterpret_cast<const uint16_t *>(p.base + p.off0), p.n,
+                              ((long long)key - (long long)p.off0) / 2, &off);
       write_result(p.result, GBU_SURROGATE, off);
     }
   }
@@ -228,6 +246,8 @@ const void *stream_kernel_ptr(int mode) {
     case S_V8: return (const void *)stream_kernel<S_V8>;
     case S_L16: return (const void *)stream_kernel<S_L16>;
     case S_V16: return (const void *)stream_kernel<S_V16>;
+    case S_V16BE: return (const void *)stream_kernel<S_V16BE>;
+    case S_L8BE: return (const void *)stream_kernel<S_L8BE>;
     default: return (const void *)stream_kernel<S_L8>;
   }
 }
