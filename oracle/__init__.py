@@ -100,6 +100,14 @@ class Codec:
         for name in ("or_convert_utf16be_to_utf8", "or_convert_utf8_to_utf16be"):
             getattr(L, name).restype = Result
             getattr(L, name).argtypes = [vp, sz, vp, sz]
+        L.or_validate_utf32.restype = Result
+        L.or_validate_utf32.argtypes = [vp, sz]
+        for name in ("or_utf8_length_from_utf32", "or_utf32_length_from_utf8"):
+            getattr(L, name).restype = ctypes.c_uint64
+            getattr(L, name).argtypes = [vp, sz]
+        for name in ("or_convert_utf32_to_utf8", "or_convert_utf8_to_utf32"):
+            getattr(L, name).restype = Result
+            getattr(L, name).argtypes = [vp, sz, vp, sz]
         for name in ("or_validate_utf8_batched", "or_validate_utf16le_batched"):
             getattr(L, name).restype = None
             getattr(L, name).argtypes = [vp, vp, sz, vp]
@@ -166,6 +174,35 @@ class Codec:
             cap = self.utf16_length_from_utf8(a)
         dst = np.zeros(cap, dtype=np.uint16)
         r = self.lib.or_convert_utf8_to_utf16be(_ptr(a), a.size, _ptr(dst), cap)
+        return r.as_tuple(), dst
+
+    # UTF-32: uint32 arrays of units (host byte order)
+    def validate_utf32(self, src):
+        a = np.ascontiguousarray(src, dtype=np.uint32)
+        return self.lib.or_validate_utf32(_ptr(a), a.size).as_tuple()
+
+    def utf8_length_from_utf32(self, src) -> int:
+        a = np.ascontiguousarray(src, dtype=np.uint32)
+        return int(self.lib.or_utf8_length_from_utf32(_ptr(a), a.size))
+
+    def utf32_length_from_utf8(self, src) -> int:
+        a = _u8(src)
+        return int(self.lib.or_utf32_length_from_utf8(_ptr(a), a.size))
+
+    def convert_utf32_to_utf8(self, src, cap=None):
+        a = np.ascontiguousarray(src, dtype=np.uint32)
+        if cap is None:
+            cap = self.utf8_length_from_utf32(a)
+        dst = np.zeros(cap, dtype=np.uint8)
+        r = self.lib.or_convert_utf32_to_utf8(_ptr(a), a.size, _ptr(dst), cap)
+        return r.as_tuple(), dst
+
+    def convert_utf8_to_utf32(self, src, cap=None):
+        a = _u8(src)
+        if cap is None:
+            cap = self.utf32_length_from_utf8(a)
+        dst = np.zeros(cap, dtype=np.uint32)
+        r = self.lib.or_convert_utf8_to_utf32(_ptr(a), a.size, _ptr(dst), cap)
         return r.as_tuple(), dst
 
     def validate_utf8_batched(self, src, off):
@@ -264,3 +301,23 @@ def convert_utf16be_to_utf8(src, cap=None):
 
 def convert_utf8_to_utf16be(src, cap=None):
     return default().convert_utf8_to_utf16be(src, cap)
+
+
+def validate_utf32(src):
+    return default().validate_utf32(src)
+
+
+def utf8_length_from_utf32(src) -> int:
+    return default().utf8_length_from_utf32(src)
+
+
+def utf32_length_from_utf8(src) -> int:
+    return default().utf32_length_from_utf8(src)
+
+
+def convert_utf32_to_utf8(src, cap=None):
+    return default().convert_utf32_to_utf8(src, cap)
+
+
+def convert_utf8_to_utf32(src, cap=None):
+    return default().convert_utf8_to_utf32(src, cap)

@@ -74,10 +74,19 @@ static int32_t interval_violation(uint32_t value, int remaining, int N) {
   return OR_OK;
 }
 
-/* Scans UTF-8 in reading order.  When dst16 is not NULL, each character is written as one or
- * two UTF-16 words (Section 3) at indices below cap.  Returns the first error, or
- * {OK, UTF-16 words the whole input needs}. */
+/* Scans UTF-8 in reading order.  Each character is counted, and written at indices below cap
+ * when the destination is not NULL, as one or two UTF-16 words (Section 3) or, when utf32 is
+ * set, as one UTF-32 unit (the value itself).  Returns the first error, or {OK, output units
+ * the whole input needs}. */
+static or_result scan_utf8_to(const uint8_t *src, size_t n, uint16_t *dst16, uint32_t *dst32, size_t cap,
+                              int utf32);
+
 static or_result scan_utf8(const uint8_t *src, size_t n, uint16_t *dst16, size_t cap) {
+  return scan_utf8_to(src, n, dst16, 0, cap, 0);
+}
+
+static or_result scan_utf8_to(const uint8_t *src, size_t n, uint16_t *dst16, uint32_t *dst32, size_t cap,
+                              int utf32) {
   uint64_t out = 0;
   size_t i = 0;
   while (i < n) {
@@ -96,8 +105,11 @@ static or_result scan_utf8(const uint8_t *src, size_t n, uint16_t *dst16, size_t
       kind = interval_violation(value, N - 1 - k, N);
       if (kind != OR_OK) return make_result(kind, i);
     }
-    /* Section 3, UTF-16: one word below U+10000, else a surrogate pair. */
-    if (value < 0x10000) {
+    if (utf32) {
+      if (dst32 && out < cap) dst32[out] = value;
+      out += 1;
+    } else if (value < 0x10000) {
+      /* Section 3, UTF-16: one word below U+10000, else a surrogate pair. */
       if (dst16 && out < cap) dst16[out] = (uint16_t)value;
       out += 1;
     } else {
@@ -282,5 +294,59 @@ or_result or_convert_utf8_to_utf16be(const uint8_t *src, size_t n, uint16_t *dst
   or_result r = or_convert_utf8_to_utf16le(src, n, dst, cap);
   const uint64_t written = r.status == OR_OK ? r.count : cap;  /* every unit written (at most cap) */
   for (uint64_t i = 0; i < written && i < cap; ++i) dst[i] = swap16(dst[i]);
+  return r;
+}
+
+/* UTF-32 (not in the paper, whose problem is UTF-8 and UTF-16): one 32-bit unit per character
+ * holding its value.  A unit is valid when it is a value Section 3 allows: below 1,114,112
+ * (rule 5) and outside D800-DFFF (rule 6); the kinds are those rules' (TOO_LARGE, SURROGATE),
+ * at the unit's index.  Units are little-endian in memory (host order). */
+static int32_t utf32_unit_violation(uint32_t u) {
+  if (u >= 1114112u) return OR_TOO_LARGE;
+  if (u >= 0xD800 && u <= 0xDFFF) return OR_SURROGATE;
+  return OR_OK;
+}
+
+or_result or_validate_utf32(const uint32_t *src, size_t n) {
+  for (size_t i = 0; i < n; ++i) {
+    int32_t k = utf32_unit_violation(src[i]);
+    if (k != OR_OK) return make_result(k, i);
+  }
+  return make_result(OR_OK, n);
+}
+
+/* UTF-8 bytes by value, for any unit: 1 below 0x80, 2 below 0x800, 3 below 0x10000, else 4. */
+uint64_t or_utf8_length_from_utf32(const uint32_t *src, size_t n) {
+  uint64_t total = 0;
+  for (size_t i = 0; i < n; ++i) total += src[i] < 0x80 ? 1 : (src[i] < 0x800 ? 2 : (src[i] < 0x10000 ? 3 : 4));
+  return total;
+}
+
+/* UTF-32 units of a UTF-8 input: one per byte that is not a continuation byte. */
+uint64_t or_utf32_length_from_utf8(const uint8_t *src, size_t n) {
+  uint64_t total = 0;
+  for (size_t i = 0; i < n; ++i)
+    if (!is_continuation(src[i])) total += 1;
+  return total;
+}
+
+or_result or_convert_utf32_to_utf8(const uint32_t *src, size_t n, uint8_t *dst, size_t cap) {
+  uint64_t out = 0;
+  for (size_t i = 0; i < n; ++i) {
+    int32_t k = utf32_unit_violation(src[i]);
+    if (k != OR_OK) return make_result(k, i);
+    uint8_t b[4];
+    int len = utf8_encode(src[i], b);
+    for (int j = 0; j < len; ++j) {
+      if (out < cap) dst[out] = b[j];
+      out += 1;
+    }
+  }
+  return make_result(out > cap ? OR_OUTPUT_TOO_SMALL : OR_OK, out);
+}
+
+or_result or_convert_utf8_to_utf32(const uint8_t *src, size_t n, uint32_t *dst, size_t cap) {
+  or_result r = scan_utf8_to(src, n, 0, dst, cap, 1);
+  if (r.status == OR_OK && r.count > cap) r.status = OR_OUTPUT_TOO_SMALL;
   return r;
 }

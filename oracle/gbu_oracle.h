@@ -65,6 +65,15 @@ uint64_t or_utf8_length_from_utf16be(const uint16_t *src, size_t n);
 or_result or_convert_utf16be_to_utf8(const uint16_t *src, size_t n, uint8_t *dst, size_t cap);
 or_result or_convert_utf8_to_utf16be(const uint8_t *src, size_t n, uint16_t *dst, size_t cap);
 
+/* UTF-32 (one 32-bit unit per value, host byte order).  A unit fails as rule 5 (>= 1,114,112:
+ * OR_TOO_LARGE) or rule 6 (D800-DFFF: OR_SURROGATE) at its index.  The lengths are formulas for
+ * any input: UTF-8 bytes by value (1/2/3/4), and one UTF-32 unit per non-continuation byte. */
+or_result or_validate_utf32(const uint32_t *src, size_t n);
+uint64_t or_utf8_length_from_utf32(const uint32_t *src, size_t n);
+uint64_t or_utf32_length_from_utf8(const uint8_t *src, size_t n);
+or_result or_convert_utf32_to_utf8(const uint32_t *src, size_t n, uint8_t *dst, size_t cap);
+or_result or_convert_utf8_to_utf32(const uint8_t *src, size_t n, uint32_t *dst, size_t cap);
+
 /* Batched forms: a plain loop over B strings given as CSR offsets (B+1 entries, in input code
  * units).  Transcoders write string i at dst + dst_off[i] with capacity
  * dst_off[i+1] - dst_off[i]. */

@@ -150,6 +150,41 @@ def check_all_scalars_utf16be(codec):
         assert r == (want if want[0] != "OK" else ("OK", len(raw.decode("utf-16-be").encode("utf-8"))))
 
 
+def check_all_scalars_utf32(codec):
+    """UTF-32 against CPython's utf-32-le codec: every scalar value round trips through UTF-8,
+    the lengths are exact, and the first invalid unit of random unit strings (above 10FFFF, or
+    a surrogate value) is where CPython's strict decoder reports it, with the kind its value
+    gives."""
+    cps = all_scalars()
+    s = cps.astype("<u4").tobytes().decode("utf-32-le")
+    u8 = np.frombuffer(s.encode("utf-8"), dtype=np.uint8)
+    u32 = np.frombuffer(s.encode("utf-32-le"), dtype=np.uint32)
+    assert codec.validate_utf32(u32) == ("OK", u32.size)
+    assert codec.utf8_length_from_utf32(u32) == u8.size
+    assert codec.utf32_length_from_utf8(u8) == u32.size
+    r, d = codec.convert_utf32_to_utf8(u32)
+    assert r == ("OK", u8.size) and np.array_equal(d, u8)
+    r, d = codec.convert_utf8_to_utf32(u8)
+    assert r == ("OK", u32.size) and np.array_equal(d, u32)
+    rng = np.random.default_rng(8)
+    units = np.array([0x41, 0x7FF, 0xFFFF, 0x10000, 0x10FFFF, 0xD7FF, 0xD800, 0xDFFF, 0xE000, 0x110000,
+                      0xFFFFFFFF], dtype="<u4")
+    for _ in range(20000):
+        u = rng.choice(units, size=int(rng.integers(1, 9)))
+        try:
+            text = u.tobytes().decode("utf-32-le")
+            want = ("OK", u.size)
+        except UnicodeDecodeError as e:
+            bad = int(u[e.start // 4])
+            want = ("TOO_LARGE" if bad > 0x10FFFF else "SURROGATE", e.start // 4)
+        assert codec.validate_utf32(u) == want, (u, want)
+        r, d = codec.convert_utf32_to_utf8(u)
+        if want[0] == "OK":
+            assert r == ("OK", len(text.encode("utf-8"))) and d.tobytes() == text.encode("utf-8")
+        else:
+            assert r == want
+
+
 def check_bruteforce(bf, max_len=3):
     """Every UTF-8 string of 1..max_len bytes against the second formulation."""
     assert bf.mixed_dead_prefixes() == 0

@@ -28,6 +28,10 @@ def test_utf16be_against_cpython():
     P.check_all_scalars_utf16be(oracle.default())
 
 
+def test_utf32_against_cpython():
+    P.check_all_scalars_utf32(oracle.default())
+
+
 def test_bruteforce_up_to_three_bytes(bf):
     P.check_bruteforce(bf, max_len=3)
 
