@@ -52,6 +52,7 @@ def parse():
     ap.add_argument("--no-sweep", action="store_true")
     ap.add_argument("--no-small", action="store_true", help="skip the L2-resident 1 MiB latency table")
     ap.add_argument("--no-be", action="store_true", help="skip the UTF-16BE leg")
+    ap.add_argument("--no-utf32", action="store_true", help="skip the UTF-32 leg")
     ap.add_argument("--small-reps", type=int, default=200)
     ap.add_argument("--sweep-size", type=int, default=256 << 20, help="UTF-8 bytes per invalid-input sweep buffer")
     ap.add_argument("--sweep-reps", type=int, default=5)
@@ -358,6 +359,8 @@ def run_ours(args):
         line["l2_resident_1mib"] = run_small(args, codec, dev)
     if not args.no_be:
         line["utf16be"] = run_be(args, codec, bufs, stream, peak)
+    if not args.no_utf32:
+        line["utf32"] = run_utf32(args, codec, bufs, stream, peak)
     if not args.no_batched and args.batched_strings > 0:
         line["batched"] = run_batched(args, codec, dev, dist, world)
     if not args.no_serving:
@@ -407,6 +410,54 @@ def run_be(args, codec, bufs, stream, peak, reps=3):
                 "frac": round((inb + outb) / ms / 1e6 / peak, 3)}
         assert int(ln.item()) == n8
         del be
+        torch.cuda.empty_cache()
+    return out
+
+
+def run_utf32(args, codec, bufs, stream, peak, reps=3):
+    """The UTF-32 calls on the same text: each profile's UTF-8 buffer transcoded to UTF-32 (by
+    the library, untimed), then validation and the UTF-8 length of that UTF-32 buffer and its
+    transcoding back to UTF-8, and the UTF-32 length and transcoding of the UTF-8 buffer.  Mean of
+    `reps` launches after one untimed; the fraction counts input + output bytes against the
+    measured copy bandwidth."""
+    import torch
+    from paper_2111_08692_gb300 import result_tuple
+    out = {"reps": reps, "ops": {}}
+    for b in bufs:
+        s8 = b["s8"]
+        ln = torch.empty(1, dtype=torch.int64, device=s8.device)
+        res = torch.empty(2, dtype=torch.int64, device=s8.device)
+        n32 = int(codec.utf32_length_from_utf8(s8, out=ln).item())
+        u32 = torch.empty(n32, dtype=torch.int32, device=s8.device)
+        r = result_tuple(codec.convert_utf8_to_utf32(s8, u32, result=res))
+        assert r == ("OK", n32), (b["profile"], r)
+        n8 = s8.numel()
+        d8 = torch.empty(n8, dtype=torch.uint8, device=s8.device)
+        calls = {"validate_utf32": (lambda: codec.validate_utf32(u32, result=res), 4 * n32, 0),
+                 "utf8_length_from_utf32": (lambda: codec.utf8_length_from_utf32(u32, out=ln), 4 * n32, 0),
+                 "convert_utf32_to_utf8": (lambda: codec.convert_utf32_to_utf8(u32, d8, result=res), 4 * n32, n8),
+                 "utf32_length_from_utf8": (lambda: codec.utf32_length_from_utf8(s8, out=ln), n8, 0),
+                 "convert_utf8_to_utf32": (lambda: codec.convert_utf8_to_utf32(s8, u32, result=res), n8, 4 * n32)}
+        for op, (fn, inb, outb) in calls.items():
+            fn()
+            torch.cuda.synchronize()
+            if "length" in op:
+                want = n8 if op == "utf8_length_from_utf32" else n32
+                assert int(ln.item()) == want, (b["profile"], op)
+            else:
+                assert result_tuple(res)[0] == "OK", (b["profile"], op, result_tuple(res))
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(reps):
+                fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / reps
+            out["ops"].setdefault(op, {})[b["profile"]] = {
+                "ms": round(ms, 4), "input_gbs": round(inb / ms / 1e6, 1),
+                "frac": round((inb + outb) / ms / 1e6 / peak, 3)}
+        del u32, d8
         torch.cuda.empty_cache()
     return out
 

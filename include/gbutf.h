@@ -136,6 +136,21 @@ int gbu_convert_utf16be_to_utf8(gbu_ctx *ctx, const uint16_t *src, uint64_t n, u
 int gbu_convert_utf8_to_utf16be(gbu_ctx *ctx, const uint8_t *src, uint64_t n, uint16_t *dst,
                                 uint64_t cap, gbu_result *result, gbu_stream stream);
 
+/* UTF-32 (not in the paper, whose problem is UTF-8 and UTF-16): one 32-bit unit per value, in
+ * host (little-endian) byte order, 4-byte aligned.  A unit is valid when Section 3 allows its
+ * value: below 1,114,112 (rule 5; else GBU_TOO_LARGE) and outside D800-DFFF (rule 6; else
+ * GBU_SURROGATE); the offset is the unit's index.  The lengths are formulas for any input: UTF-8
+ * bytes by value (1 below 0x80, 2 below 0x800, 3 below 0x10000, else 4), and one UTF-32 unit per
+ * UTF-8 byte that is not a continuation byte.  Transcoding validates (rules 1-6 for UTF-8
+ * input); results, capacities and return values as for the UTF-16LE calls. */
+int gbu_validate_utf32(gbu_ctx *ctx, const uint32_t *src, uint64_t n, gbu_result *result, gbu_stream stream);
+int gbu_utf8_length_from_utf32(gbu_ctx *ctx, const uint32_t *src, uint64_t n, uint64_t *len, gbu_stream stream);
+int gbu_utf32_length_from_utf8(gbu_ctx *ctx, const uint8_t *src, uint64_t n, uint64_t *len, gbu_stream stream);
+int gbu_convert_utf32_to_utf8(gbu_ctx *ctx, const uint32_t *src, uint64_t n, uint8_t *dst, uint64_t cap,
+                              gbu_result *result, gbu_stream stream);
+int gbu_convert_utf8_to_utf32(gbu_ctx *ctx, const uint8_t *src, uint64_t n, uint32_t *dst, uint64_t cap,
+                              gbu_result *result, gbu_stream stream);
+
 /* ---- Batched forms ------------------------------------------------------------------------
  * The same six operations over B strings in ONE launch (a persistent grid; strings never wait
  * on one another).  The strings lie back to back in src; string i is src[off[i] : off[i+1]]

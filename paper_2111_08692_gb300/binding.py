@@ -113,6 +113,12 @@ def lib() -> ctypes.CDLL:
             for name in ("gbu_convert_utf16be_to_utf8", "gbu_convert_utf8_to_utf16be"):
                 getattr(L, name).restype = i32
                 getattr(L, name).argtypes = [vp, vp, u64, vp, u64, vp, vp]
+            for name in ("gbu_validate_utf32", "gbu_utf8_length_from_utf32", "gbu_utf32_length_from_utf8"):
+                getattr(L, name).restype = i32
+                getattr(L, name).argtypes = [vp, vp, u64, vp, vp]
+            for name in ("gbu_convert_utf32_to_utf8", "gbu_convert_utf8_to_utf32"):
+                getattr(L, name).restype = i32
+                getattr(L, name).argtypes = [vp, vp, u64, vp, u64, vp, vp]
             L.gbu_chunked_create.restype = vp
             L.gbu_chunked_create.argtypes = [i32, i32, u64]
             L.gbu_chunked_push.restype = i32
@@ -475,6 +481,39 @@ class Codec:
         _check(lib().gbu_convert_utf8_to_utf16be(self.ctx, self._ptr(src), src.numel(), self._ptr(dst), cap,
                                                  result.data_ptr(), self._stream(stream)),
                "gbu_convert_utf8_to_utf16be")
+        return result
+
+    # UTF-32 forms: int32 tensors of units (host byte order)
+    def validate_utf32(self, src, result=None, stream=None):
+        result = self.new_result() if result is None else result
+        _check(lib().gbu_validate_utf32(self.ctx, self._ptr(src), src.numel(), result.data_ptr(),
+                                        self._stream(stream)), "gbu_validate_utf32")
+        return result
+
+    def utf8_length_from_utf32(self, src, out=None, stream=None):
+        out = self.torch.empty(1, dtype=self.torch.int64, device=f"cuda:{self.device}") if out is None else out
+        _check(lib().gbu_utf8_length_from_utf32(self.ctx, self._ptr(src), src.numel(), out.data_ptr(),
+                                                self._stream(stream)), "gbu_utf8_length_from_utf32")
+        return out
+
+    def utf32_length_from_utf8(self, src, out=None, stream=None):
+        out = self.torch.empty(1, dtype=self.torch.int64, device=f"cuda:{self.device}") if out is None else out
+        _check(lib().gbu_utf32_length_from_utf8(self.ctx, self._ptr(src), src.numel(), out.data_ptr(),
+                                                self._stream(stream)), "gbu_utf32_length_from_utf8")
+        return out
+
+    def convert_utf32_to_utf8(self, src, dst, result=None, stream=None, cap=None):
+        result = self.new_result() if result is None else result
+        cap = dst.numel() if cap is None else cap
+        _check(lib().gbu_convert_utf32_to_utf8(self.ctx, self._ptr(src), src.numel(), self._ptr(dst), cap,
+                                               result.data_ptr(), self._stream(stream)), "gbu_convert_utf32_to_utf8")
+        return result
+
+    def convert_utf8_to_utf32(self, src, dst, result=None, stream=None, cap=None):
+        result = self.new_result() if result is None else result
+        cap = dst.numel() if cap is None else cap
+        _check(lib().gbu_convert_utf8_to_utf32(self.ctx, self._ptr(src), src.numel(), self._ptr(dst), cap,
+                                               result.data_ptr(), self._stream(stream)), "gbu_convert_utf8_to_utf32")
         return result
 
     # batched forms: src is the concatenation, off the B+1 offsets (int64 tensor, code units)

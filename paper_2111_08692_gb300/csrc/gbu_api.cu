@@ -15,8 +15,13 @@
 namespace {
 
 // The six kernels, in the order gbu_launch_config reports them (K_COUNT is also the number of
-// batched operations), then the UTF-16BE kernels.
-enum Kernel { K_V8 = 0, K_L8, K_C8, K_V16, K_L16, K_C16, K_COUNT, K_V16BE = K_COUNT, K_L16BE, K_C16BE, K_C8BE, K_ALL };
+// batched operations), then the UTF-16BE and UTF-32 kernels.
+enum Kernel {
+  K_V8 = 0, K_L8, K_C8, K_V16, K_L16, K_C16, K_COUNT,
+  K_V16BE = K_COUNT, K_L16BE, K_C16BE, K_C8BE,
+  K_V32, K_L8F32, K_L32, K_C32, K_C8T32,  // validate, UTF-8 length, UTF-32 length, 32 -> 8, 8 -> 32
+  K_ALL
+};
 
 const void *kernel_ptr(int k) {
   switch (k) {
@@ -29,15 +34,24 @@ const void *kernel_ptr(int k) {
     case K_L16BE: return gbu::stream_kernel_ptr(5);
     case K_C16BE: return gbu::utf16be_to_utf8_kernel_ptr();
     case K_C8BE: return gbu::utf8_to_utf16be_kernel_ptr();
+    case K_V32: return gbu::utf32_stream_kernel_ptr(0);
+    case K_L8F32: return gbu::utf32_stream_kernel_ptr(1);
+    case K_L32: return gbu::utf32_stream_kernel_ptr(2);
+    case K_C32: return gbu::utf32_to_utf8_kernel_ptr();
+    case K_C8T32: return gbu::utf8_to_utf32_kernel_ptr();
     default: return gbu::utf16_to_utf8_kernel_ptr();
   }
 }
-bool is_transcoder(int k) { return k == K_C8 || k == K_C16 || k == K_C16BE || k == K_C8BE; }
+bool is_transcoder(int k) {
+  return k == K_C8 || k == K_C16 || k == K_C16BE || k == K_C8BE || k == K_C32 || k == K_C8T32;
+}
 size_t kernel_smem(int k) {
   if (k == K_C8) return gbu::utf8_to_utf16_smem_bytes();
   if (k == K_C16) return gbu::utf16_to_utf8_smem_bytes();
   if (k == K_C16BE) return gbu::utf16be_to_utf8_smem_bytes();
   if (k == K_C8BE) return gbu::utf8_to_utf16be_smem_bytes();
+  if (k == K_C32) return gbu::utf32_to_utf8_smem_bytes();
+  if (k == K_C8T32) return gbu::utf8_to_utf32_smem_bytes();
   return 0;
 }
 int kernel_threads(int k) { return is_transcoder(k) ? gbu::XT : gbu::STREAM_THREADS; }
@@ -109,9 +123,9 @@ extern "C" gbu_ctx *gbu_create(int device, uint64_t max_units) {
     delete c;
     return nullptr;
   }
-  // scan states: one per transcoder partition of the largest input (UTF-16: 2 bytes per
+  // scan states: one per transcoder partition of the largest input (UTF-32: 4 bytes per
   // unit), plus the extra partition UTF-8 inputs may use past their end
-  uint64_t tiles = (2 * max_units + 64) / gbu::PART_BYTES + 4;
+  uint64_t tiles = (4 * max_units + 64) / gbu::PART_BYTES + 4;
   // ... and one per tile of the u64 scan of up to max_units + 1 values
   const uint64_t scan_tiles = (max_units + 1) / gbu::scan_tile_items() + 2;
   if (scan_tiles > tiles) tiles = scan_tiles;
@@ -229,6 +243,7 @@ static int make_params(gbu_ctx *c, int k, const void *src, uint64_t n, uint32_t 
   if (n > c->max_units) return GBU_BAD_ARGUMENT;
   if (n > 0 && !src) return GBU_BAD_ARGUMENT;
   if (unit_bytes == 2 && ((uintptr_t)src & 1)) return GBU_BAD_ARGUMENT;
+  if (unit_bytes == 4 && ((uintptr_t)src & 3)) return GBU_BAD_ARGUMENT;
   memset(p, 0, sizeof(*p));
   const uintptr_t a = (uintptr_t)src;
   p->base = (const uint8_t *)(a & ~(uintptr_t)15);
@@ -339,6 +354,60 @@ extern "C" int gbu_convert_utf16le_to_utf8(gbu_ctx *c, const uint16_t *src, uint
   p.result = result;
   set_dst(&p, dst, cap, 1);
   return launch(c, K_C16, p, stream);
+}
+
+// ---- UTF-32 ------------------------------------------------------------------------------
+
+extern "C" int gbu_validate_utf32(gbu_ctx *c, const uint32_t *src, uint64_t n, gbu_result *result,
+                                  gbu_stream stream) {
+  gbu::Params p;
+  int rc = make_params(c, K_V32, src, n, 4, false, &p);
+  if (rc != GBU_OK) return rc;
+  if (!result) return GBU_BAD_ARGUMENT;
+  p.result = result;
+  return launch(c, K_V32, p, stream);
+}
+
+extern "C" int gbu_utf8_length_from_utf32(gbu_ctx *c, const uint32_t *src, uint64_t n, uint64_t *len,
+                                          gbu_stream stream) {
+  gbu::Params p;
+  int rc = make_params(c, K_L8F32, src, n, 4, false, &p);
+  if (rc != GBU_OK) return rc;
+  if (!len) return GBU_BAD_ARGUMENT;
+  p.len_out = len;
+  return launch(c, K_L8F32, p, stream);
+}
+
+extern "C" int gbu_utf32_length_from_utf8(gbu_ctx *c, const uint8_t *src, uint64_t n, uint64_t *len,
+                                          gbu_stream stream) {
+  gbu::Params p;
+  int rc = make_params(c, K_L32, src, n, 1, false, &p);
+  if (rc != GBU_OK) return rc;
+  if (!len) return GBU_BAD_ARGUMENT;
+  p.len_out = len;
+  return launch(c, K_L32, p, stream);
+}
+
+extern "C" int gbu_convert_utf32_to_utf8(gbu_ctx *c, const uint32_t *src, uint64_t n, uint8_t *dst,
+                                         uint64_t cap, gbu_result *result, gbu_stream stream) {
+  gbu::Params p;
+  int rc = make_params(c, K_C32, src, n, 4, false, &p);
+  if (rc != GBU_OK) return rc;
+  if (!result || (cap > 0 && !dst)) return GBU_BAD_ARGUMENT;
+  p.result = result;
+  set_dst(&p, dst, cap, 1);
+  return launch(c, K_C32, p, stream);
+}
+
+extern "C" int gbu_convert_utf8_to_utf32(gbu_ctx *c, const uint8_t *src, uint64_t n, uint32_t *dst,
+                                         uint64_t cap, gbu_result *result, gbu_stream stream) {
+  gbu::Params p;
+  int rc = make_params(c, K_C8T32, src, n, 1, true, &p);
+  if (rc != GBU_OK) return rc;
+  if (!result || (cap > 0 && !dst) || ((uintptr_t)dst & 3)) return GBU_BAD_ARGUMENT;
+  p.result = result;
+  set_dst(&p, dst, cap, 4);
+  return launch(c, K_C8T32, p, stream);
 }
 
 // ---- UTF-16BE ----------------------------------------------------------------------------
