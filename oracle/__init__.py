@@ -105,7 +105,11 @@ class Codec:
         for name in ("or_utf8_length_from_utf32", "or_utf32_length_from_utf8"):
             getattr(L, name).restype = ctypes.c_uint64
             getattr(L, name).argtypes = [vp, sz]
-        for name in ("or_convert_utf32_to_utf8", "or_convert_utf8_to_utf32"):
+        for name in ("or_utf16_length_from_utf32", "or_utf32_length_from_utf16le"):
+            getattr(L, name).restype = ctypes.c_uint64
+            getattr(L, name).argtypes = [vp, sz]
+        for name in ("or_convert_utf32_to_utf8", "or_convert_utf8_to_utf32", "or_convert_utf32_to_utf16le",
+                     "or_convert_utf16le_to_utf32"):
             getattr(L, name).restype = Result
             getattr(L, name).argtypes = [vp, sz, vp, sz]
         for name in ("or_validate_utf8_batched", "or_validate_utf16le_batched"):
@@ -203,6 +207,30 @@ class Codec:
             cap = self.utf32_length_from_utf8(a)
         dst = np.zeros(cap, dtype=np.uint32)
         r = self.lib.or_convert_utf8_to_utf32(_ptr(a), a.size, _ptr(dst), cap)
+        return r.as_tuple(), dst
+
+    def utf16_length_from_utf32(self, src) -> int:
+        a = np.ascontiguousarray(src, dtype=np.uint32)
+        return int(self.lib.or_utf16_length_from_utf32(_ptr(a), a.size))
+
+    def utf32_length_from_utf16le(self, src) -> int:
+        a = _u16(src)
+        return int(self.lib.or_utf32_length_from_utf16le(_ptr(a), a.size))
+
+    def convert_utf32_to_utf16le(self, src, cap=None):
+        a = np.ascontiguousarray(src, dtype=np.uint32)
+        if cap is None:
+            cap = self.utf16_length_from_utf32(a)
+        dst = np.zeros(cap, dtype=np.uint16)
+        r = self.lib.or_convert_utf32_to_utf16le(_ptr(a), a.size, _ptr(dst), cap)
+        return r.as_tuple(), dst
+
+    def convert_utf16le_to_utf32(self, src, cap=None):
+        a = _u16(src)
+        if cap is None:
+            cap = self.utf32_length_from_utf16le(a)
+        dst = np.zeros(cap, dtype=np.uint32)
+        r = self.lib.or_convert_utf16le_to_utf32(_ptr(a), a.size, _ptr(dst), cap)
         return r.as_tuple(), dst
 
     def validate_utf8_batched(self, src, off):
@@ -321,3 +349,19 @@ def convert_utf32_to_utf8(src, cap=None):
 
 def convert_utf8_to_utf32(src, cap=None):
     return default().convert_utf8_to_utf32(src, cap)
+
+
+def utf16_length_from_utf32(src) -> int:
+    return default().utf16_length_from_utf32(src)
+
+
+def utf32_length_from_utf16le(src) -> int:
+    return default().utf32_length_from_utf16le(src)
+
+
+def convert_utf32_to_utf16le(src, cap=None):
+    return default().convert_utf32_to_utf16le(src, cap)
+
+
+def convert_utf16le_to_utf32(src, cap=None):
+    return default().convert_utf16le_to_utf32(src, cap)

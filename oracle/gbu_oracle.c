@@ -152,7 +152,17 @@ static int utf8_encode(uint32_t cp, uint8_t b[4]) {
  * DC00-DFFF; a word in DC00-DFFF must follow one in D800-DBFF).  When dst8 is not NULL, each
  * character's UTF-8 bytes are written at indices below cap.  Returns the first error, or
  * {OK, UTF-8 bytes the whole input needs}. */
+static or_result scan_utf16_to(const uint16_t *src, size_t n, uint8_t *dst8, uint32_t *dst32, size_t cap,
+                               int utf32);
+
 static or_result scan_utf16(const uint16_t *src, size_t n, uint8_t *dst8, size_t cap) {
+  return scan_utf16_to(src, n, dst8, 0, cap, 0);
+}
+
+/* As scan_utf16, but when utf32 is set each character is counted (and written) as one UTF-32
+ * unit instead of its UTF-8 bytes. */
+static or_result scan_utf16_to(const uint16_t *src, size_t n, uint8_t *dst8, uint32_t *dst32, size_t cap,
+                               int utf32) {
   uint64_t out = 0;
   size_t i = 0;
   while (i < n) {
@@ -169,6 +179,11 @@ static or_result scan_utf16(const uint16_t *src, size_t n, uint8_t *dst8, size_t
       i += 2;
     } else {
       return make_result(OR_SURROGATE, i);
+    }
+    if (utf32) {
+      if (dst32 && out < cap) dst32[out] = cp;
+      out += 1;
+      continue;
     }
     uint8_t b[4];
     int len = utf8_encode(cp, b);
@@ -347,6 +362,46 @@ or_result or_convert_utf32_to_utf8(const uint32_t *src, size_t n, uint8_t *dst, 
 
 or_result or_convert_utf8_to_utf32(const uint8_t *src, size_t n, uint32_t *dst, size_t cap) {
   or_result r = scan_utf8_to(src, n, 0, dst, cap, 1);
+  if (r.status == OR_OK && r.count > cap) r.status = OR_OUTPUT_TOO_SMALL;
+  return r;
+}
+
+/* UTF-16 words of a UTF-32 input, for any unit: 1 below 0x10000, else 2 (a surrogate pair). */
+uint64_t or_utf16_length_from_utf32(const uint32_t *src, size_t n) {
+  uint64_t total = 0;
+  for (size_t i = 0; i < n; ++i) total += src[i] < 0x10000 ? 1 : 2;
+  return total;
+}
+
+/* UTF-32 units of a UTF-16LE input: one per word that is not a second surrogate (DC00-DFFF). */
+uint64_t or_utf32_length_from_utf16le(const uint16_t *src, size_t n) {
+  uint64_t total = 0;
+  for (size_t i = 0; i < n; ++i)
+    if (src[i] < 0xDC00 || src[i] > 0xDFFF) total += 1;
+  return total;
+}
+
+/* Section 3, UTF-16: one word below U+10000, else the surrogate pair. */
+or_result or_convert_utf32_to_utf16le(const uint32_t *src, size_t n, uint16_t *dst, size_t cap) {
+  uint64_t out = 0;
+  for (size_t i = 0; i < n; ++i) {
+    int32_t k = utf32_unit_violation(src[i]);
+    if (k != OR_OK) return make_result(k, i);
+    if (src[i] < 0x10000) {
+      if (out < cap) dst[out] = (uint16_t)src[i];
+      out += 1;
+    } else {
+      uint32_t v = src[i] - 0x10000;
+      if (out < cap) dst[out] = (uint16_t)(0xD800 + (v >> 10));
+      if (out + 1 < cap) dst[out + 1] = (uint16_t)(0xDC00 + (v & 0x3FF));
+      out += 2;
+    }
+  }
+  return make_result(out > cap ? OR_OUTPUT_TOO_SMALL : OR_OK, out);
+}
+
+or_result or_convert_utf16le_to_utf32(const uint16_t *src, size_t n, uint32_t *dst, size_t cap) {
+  or_result r = scan_utf16_to(src, n, 0, dst, cap, 1);
   if (r.status == OR_OK && r.count > cap) r.status = OR_OUTPUT_TOO_SMALL;
   return r;
 }

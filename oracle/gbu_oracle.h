@@ -73,6 +73,12 @@ uint64_t or_utf8_length_from_utf32(const uint32_t *src, size_t n);
 uint64_t or_utf32_length_from_utf8(const uint8_t *src, size_t n);
 or_result or_convert_utf32_to_utf8(const uint32_t *src, size_t n, uint8_t *dst, size_t cap);
 or_result or_convert_utf8_to_utf32(const uint8_t *src, size_t n, uint32_t *dst, size_t cap);
+/* UTF-16LE <-> UTF-32: UTF-16 words by value (1 below 0x10000, else 2), and one UTF-32 unit per
+ * word that is not a second surrogate (DC00-DFFF). */
+uint64_t or_utf16_length_from_utf32(const uint32_t *src, size_t n);
+uint64_t or_utf32_length_from_utf16le(const uint16_t *src, size_t n);
+or_result or_convert_utf32_to_utf16le(const uint32_t *src, size_t n, uint16_t *dst, size_t cap);
+or_result or_convert_utf16le_to_utf32(const uint16_t *src, size_t n, uint32_t *dst, size_t cap);
 
 /* Batched forms: a plain loop over B strings given as CSR offsets (B+1 entries, in input code
  * units).  Transcoders write string i at dst + dst_off[i] with capacity

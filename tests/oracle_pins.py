@@ -151,8 +151,8 @@ def check_all_scalars_utf16be(codec):
 
 
 def check_all_scalars_utf32(codec):
-    """UTF-32 against CPython's utf-32-le codec: every scalar value round trips through UTF-8,
-    the lengths are exact, and the first invalid unit of random unit strings (above 10FFFF, or
+    """UTF-32 against CPython's utf-32-le codec: every scalar value round trips through UTF-8
+    and UTF-16LE, the lengths are exact, and the first invalid unit of random unit strings (above 10FFFF, or
     a surrogate value) is where CPython's strict decoder reports it, with the kind its value
     gives."""
     cps = all_scalars()
@@ -166,6 +166,27 @@ def check_all_scalars_utf32(codec):
     assert r == ("OK", u8.size) and np.array_equal(d, u8)
     r, d = codec.convert_utf8_to_utf32(u8)
     assert r == ("OK", u32.size) and np.array_equal(d, u32)
+    u16 = np.frombuffer(s.encode("utf-16-le"), dtype=np.uint16)
+    assert codec.utf16_length_from_utf32(u32) == u16.size
+    assert codec.utf32_length_from_utf16le(u16) == u32.size
+    r, d = codec.convert_utf32_to_utf16le(u32)
+    assert r == ("OK", u16.size) and np.array_equal(d, u16)
+    r, d = codec.convert_utf16le_to_utf32(u16)
+    assert r == ("OK", u32.size) and np.array_equal(d, u32)
+    # UTF-16LE -> UTF-32 reports the first unpaired surrogate where CPython's utf-16-le decoder does
+    rng16 = np.random.default_rng(9)
+    words = np.array([0x41, 0x3B1, 0xD800, 0xDBFF, 0xDC00, 0xDFFF, 0xE000], dtype="<u2")
+    for _ in range(20000):
+        w = rng16.choice(words, size=int(rng16.integers(1, 9)))
+        try:
+            text = w.tobytes().decode("utf-16-le")
+            want = ("OK", len(text))
+        except UnicodeDecodeError as e:
+            want = ("SURROGATE", e.start // 2)
+        r, d = codec.convert_utf16le_to_utf32(w)
+        assert r == want, (w, r, want)
+        if want[0] == "OK":
+            assert d.tobytes() == text.encode("utf-32-le")
     rng = np.random.default_rng(8)
     units = np.array([0x41, 0x7FF, 0xFFFF, 0x10000, 0x10FFFF, 0xD7FF, 0xD800, 0xDFFF, 0xE000, 0x110000,
                       0xFFFFFFFF], dtype="<u4")
@@ -181,6 +202,11 @@ def check_all_scalars_utf32(codec):
         r, d = codec.convert_utf32_to_utf8(u)
         if want[0] == "OK":
             assert r == ("OK", len(text.encode("utf-8"))) and d.tobytes() == text.encode("utf-8")
+        else:
+            assert r == want
+        r, d = codec.convert_utf32_to_utf16le(u)
+        if want[0] == "OK":
+            assert r == ("OK", len(text.encode("utf-16-le")) // 2) and d.tobytes() == text.encode("utf-16-le")
         else:
             assert r == want
 
