@@ -74,6 +74,19 @@ static int32_t interval_violation(uint32_t value, int remaining, int N) {
   return OR_OK;
 }
 
+/* Section 3, UTF-16: the words of a value -- itself below U+10000, else the surrogate pair
+ * (the value minus 0x10000, ten high bits on D800 and ten low bits on DC00).  Returns 1 or 2. */
+static int utf16_encode(uint32_t value, uint16_t w[2]) {
+  if (value < 0x10000) {
+    w[0] = (uint16_t)value;
+    return 1;
+  }
+  uint32_t v = value - 0x10000;
+  w[0] = (uint16_t)(0xD800 + (v >> 10));
+  w[1] = (uint16_t)(0xDC00 + (v & 0x3FF));
+  return 2;
+}
+
 /* Scans UTF-8 in reading order.  Each character is counted, and written at indices below cap
  * when the destination is not NULL, as one or two UTF-16 words (Section 3) or, when utf32 is
  * set, as one UTF-32 unit (the value itself).  Returns the first error, or {OK, output units
@@ -108,15 +121,13 @@ static or_result scan_utf8_to(const uint8_t *src, size_t n, uint16_t *dst16, uin
     if (utf32) {
       if (dst32 && out < cap) dst32[out] = value;
       out += 1;
-    } else if (value < 0x10000) {
-      /* Section 3, UTF-16: one word below U+10000, else a surrogate pair. */
-      if (dst16 && out < cap) dst16[out] = (uint16_t)value;
-      out += 1;
     } else {
-      uint32_t v = value - 0x10000;
-      if (dst16 && out < cap) dst16[out] = (uint16_t)(0xD800 + (v >> 10));
-      if (dst16 && out + 1 < cap) dst16[out + 1] = (uint16_t)(0xDC00 + (v & 0x3FF));
-      out += 2;
+      uint16_t w[2];
+      int len = utf16_encode(value, w);
+      for (int k = 0; k < len; ++k) {
+        if (dst16 && out < cap) dst16[out] = w[k];
+        out += 1;
+      }
     }
     i += (size_t)N;
   }
@@ -387,14 +398,11 @@ or_result or_convert_utf32_to_utf16le(const uint32_t *src, size_t n, uint16_t *d
   for (size_t i = 0; i < n; ++i) {
     int32_t k = utf32_unit_violation(src[i]);
     if (k != OR_OK) return make_result(k, i);
-    if (src[i] < 0x10000) {
-      if (out < cap) dst[out] = (uint16_t)src[i];
+    uint16_t w[2];
+    int len = utf16_encode(src[i], w);
+    for (int k = 0; k < len; ++k) {
+      if (out < cap) dst[out] = w[k];
       out += 1;
-    } else {
-      uint32_t v = src[i] - 0x10000;
-      if (out < cap) dst[out] = (uint16_t)(0xD800 + (v >> 10));
-      if (out + 1 < cap) dst[out + 1] = (uint16_t)(0xDC00 + (v & 0x3FF));
-      out += 2;
     }
   }
   return make_result(out > cap ? OR_OUTPUT_TOO_SMALL : OR_OK, out);
