@@ -417,7 +417,8 @@ def run_be(args, codec, bufs, stream, peak, reps=3):
 def run_utf32(args, codec, bufs, stream, peak, reps=3):
     """The UTF-32 calls on the same text: each profile's UTF-8 buffer transcoded to UTF-32 (by
     the library, untimed), then validation and the UTF-8 length of that UTF-32 buffer and its
-    transcoding back to UTF-8, and the UTF-32 length and transcoding of the UTF-8 buffer.  Mean of
+    transcoding to UTF-8 and to UTF-16LE, the UTF-32 length and transcoding of the UTF-8 buffer,
+    and the transcoding of the UTF-16LE buffer to UTF-32.  Mean of
     `reps` launches after one untimed; the fraction counts input + output bytes against the
     measured copy bandwidth."""
     import torch
@@ -433,11 +434,20 @@ def run_utf32(args, codec, bufs, stream, peak, reps=3):
         assert r == ("OK", n32), (b["profile"], r)
         n8 = s8.numel()
         d8 = torch.empty(n8, dtype=torch.uint8, device=s8.device)
+        n16 = int(codec.utf16_length_from_utf32(u32, out=ln).item())
+        d16 = torch.empty(n16, dtype=torch.int16, device=s8.device)
+        s16 = b["s16"]
+        n32b = int(codec.utf32_length_from_utf16le(s16, out=ln).item())
+        u32b = torch.empty(n32b, dtype=torch.int32, device=s8.device)
         calls = {"validate_utf32": (lambda: codec.validate_utf32(u32, result=res), 4 * n32, 0),
                  "utf8_length_from_utf32": (lambda: codec.utf8_length_from_utf32(u32, out=ln), 4 * n32, 0),
                  "convert_utf32_to_utf8": (lambda: codec.convert_utf32_to_utf8(u32, d8, result=res), 4 * n32, n8),
                  "utf32_length_from_utf8": (lambda: codec.utf32_length_from_utf8(s8, out=ln), n8, 0),
-                 "convert_utf8_to_utf32": (lambda: codec.convert_utf8_to_utf32(s8, u32, result=res), n8, 4 * n32)}
+                 "convert_utf8_to_utf32": (lambda: codec.convert_utf8_to_utf32(s8, u32, result=res), n8, 4 * n32),
+                 "convert_utf32_to_utf16le": (lambda: codec.convert_utf32_to_utf16le(u32, d16, result=res),
+                                              4 * n32, 2 * n16),
+                 "convert_utf16le_to_utf32": (lambda: codec.convert_utf16le_to_utf32(s16, u32b, result=res),
+                                              2 * s16.numel(), 4 * n32b)}
         for op, (fn, inb, outb) in calls.items():
             fn()
             torch.cuda.synchronize()
@@ -457,7 +467,7 @@ def run_utf32(args, codec, bufs, stream, peak, reps=3):
             out["ops"].setdefault(op, {})[b["profile"]] = {
                 "ms": round(ms, 4), "input_gbs": round(inb / ms / 1e6, 1),
                 "frac": round((inb + outb) / ms / 1e6 / peak, 3)}
-        del u32, d8
+        del u32, d8, d16, u32b
         torch.cuda.empty_cache()
     return out
 

@@ -150,6 +150,16 @@ int gbu_convert_utf32_to_utf8(gbu_ctx *ctx, const uint32_t *src, uint64_t n, uin
                               gbu_result *result, gbu_stream stream);
 int gbu_convert_utf8_to_utf32(gbu_ctx *ctx, const uint8_t *src, uint64_t n, uint32_t *dst, uint64_t cap,
                               gbu_result *result, gbu_stream stream);
+/* UTF-16LE <-> UTF-32.  Lengths for any input: UTF-16 words of a UTF-32 input (1 per unit below
+ * 0x10000, else 2), and UTF-32 units of a UTF-16LE input (1 per word that is not a second
+ * surrogate DC00-DFFF).  The UTF-16LE input is validated by Section 3's pair rules
+ * (GBU_SURROGATE at the first unpaired surrogate), the UTF-32 input as above. */
+int gbu_utf16_length_from_utf32(gbu_ctx *ctx, const uint32_t *src, uint64_t n, uint64_t *len, gbu_stream stream);
+int gbu_utf32_length_from_utf16le(gbu_ctx *ctx, const uint16_t *src, uint64_t n, uint64_t *len, gbu_stream stream);
+int gbu_convert_utf32_to_utf16le(gbu_ctx *ctx, const uint32_t *src, uint64_t n, uint16_t *dst, uint64_t cap,
+                                 gbu_result *result, gbu_stream stream);
+int gbu_convert_utf16le_to_utf32(gbu_ctx *ctx, const uint16_t *src, uint64_t n, uint32_t *dst, uint64_t cap,
+                                 gbu_result *result, gbu_stream stream);
 
 /* ---- Batched forms ------------------------------------------------------------------------
  * The same six operations over B strings in ONE launch (a persistent grid; strings never wait

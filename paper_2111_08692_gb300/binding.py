@@ -116,7 +116,11 @@ def lib() -> ctypes.CDLL:
             for name in ("gbu_validate_utf32", "gbu_utf8_length_from_utf32", "gbu_utf32_length_from_utf8"):
                 getattr(L, name).restype = i32
                 getattr(L, name).argtypes = [vp, vp, u64, vp, vp]
-            for name in ("gbu_convert_utf32_to_utf8", "gbu_convert_utf8_to_utf32"):
+            for name in ("gbu_utf16_length_from_utf32", "gbu_utf32_length_from_utf16le"):
+                getattr(L, name).restype = i32
+                getattr(L, name).argtypes = [vp, vp, u64, vp, vp]
+            for name in ("gbu_convert_utf32_to_utf8", "gbu_convert_utf8_to_utf32", "gbu_convert_utf32_to_utf16le",
+                         "gbu_convert_utf16le_to_utf32"):
                 getattr(L, name).restype = i32
                 getattr(L, name).argtypes = [vp, vp, u64, vp, u64, vp, vp]
             L.gbu_chunked_create.restype = vp
@@ -514,6 +518,34 @@ class Codec:
         cap = dst.numel() if cap is None else cap
         _check(lib().gbu_convert_utf8_to_utf32(self.ctx, self._ptr(src), src.numel(), self._ptr(dst), cap,
                                                result.data_ptr(), self._stream(stream)), "gbu_convert_utf8_to_utf32")
+        return result
+
+    def utf16_length_from_utf32(self, src, out=None, stream=None):
+        out = self.torch.empty(1, dtype=self.torch.int64, device=f"cuda:{self.device}") if out is None else out
+        _check(lib().gbu_utf16_length_from_utf32(self.ctx, self._ptr(src), src.numel(), out.data_ptr(),
+                                                 self._stream(stream)), "gbu_utf16_length_from_utf32")
+        return out
+
+    def utf32_length_from_utf16le(self, src, out=None, stream=None):
+        out = self.torch.empty(1, dtype=self.torch.int64, device=f"cuda:{self.device}") if out is None else out
+        _check(lib().gbu_utf32_length_from_utf16le(self.ctx, self._ptr(src), src.numel(), out.data_ptr(),
+                                                   self._stream(stream)), "gbu_utf32_length_from_utf16le")
+        return out
+
+    def convert_utf32_to_utf16le(self, src, dst, result=None, stream=None, cap=None):
+        result = self.new_result() if result is None else result
+        cap = dst.numel() if cap is None else cap
+        _check(lib().gbu_convert_utf32_to_utf16le(self.ctx, self._ptr(src), src.numel(), self._ptr(dst), cap,
+                                                  result.data_ptr(), self._stream(stream)),
+               "gbu_convert_utf32_to_utf16le")
+        return result
+
+    def convert_utf16le_to_utf32(self, src, dst, result=None, stream=None, cap=None):
+        result = self.new_result() if result is None else result
+        cap = dst.numel() if cap is None else cap
+        _check(lib().gbu_convert_utf16le_to_utf32(self.ctx, self._ptr(src), src.numel(), self._ptr(dst), cap,
+                                                  result.data_ptr(), self._stream(stream)),
+               "gbu_convert_utf16le_to_utf32")
         return result
 
     # batched forms: src is the concatenation, off the B+1 offsets (int64 tensor, code units)

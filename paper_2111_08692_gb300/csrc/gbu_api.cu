@@ -20,6 +20,7 @@ enum Kernel {
   K_V8 = 0, K_L8, K_C8, K_V16, K_L16, K_C16, K_COUNT,
   K_V16BE = K_COUNT, K_L16BE, K_C16BE, K_C8BE,
   K_V32, K_L8F32, K_L32, K_C32, K_C8T32,  // validate, UTF-8 length, UTF-32 length, 32 -> 8, 8 -> 32
+  K_L16F32, K_L32F16, K_C32T16, K_C16T32,  // UTF-16 length, UTF-32 length of UTF-16, 32 -> 16, 16 -> 32
   K_ALL
 };
 
@@ -39,11 +40,16 @@ const void *kernel_ptr(int k) {
     case K_L32: return gbu::utf32_stream_kernel_ptr(2);
     case K_C32: return gbu::utf32_to_utf8_kernel_ptr();
     case K_C8T32: return gbu::utf8_to_utf32_kernel_ptr();
+    case K_L16F32: return gbu::utf32_stream_kernel_ptr(3);
+    case K_L32F16: return gbu::utf32_stream_kernel_ptr(4);
+    case K_C32T16: return gbu::utf32_to_utf16_kernel_ptr();
+    case K_C16T32: return gbu::utf16_to_utf32_kernel_ptr();
     default: return gbu::utf16_to_utf8_kernel_ptr();
   }
 }
 bool is_transcoder(int k) {
-  return k == K_C8 || k == K_C16 || k == K_C16BE || k == K_C8BE || k == K_C32 || k == K_C8T32;
+  return k == K_C8 || k == K_C16 || k == K_C16BE || k == K_C8BE || k == K_C32 || k == K_C8T32 || k == K_C32T16 ||
+         k == K_C16T32;
 }
 size_t kernel_smem(int k) {
   if (k == K_C8) return gbu::utf8_to_utf16_smem_bytes();
@@ -52,6 +58,8 @@ size_t kernel_smem(int k) {
   if (k == K_C8BE) return gbu::utf8_to_utf16be_smem_bytes();
   if (k == K_C32) return gbu::utf32_to_utf8_smem_bytes();
   if (k == K_C8T32) return gbu::utf8_to_utf32_smem_bytes();
+  if (k == K_C32T16) return gbu::utf32_to_utf16_smem_bytes();
+  if (k == K_C16T32) return gbu::utf16_to_utf32_smem_bytes();
   return 0;
 }
 int kernel_threads(int k) { return is_transcoder(k) ? gbu::XT : gbu::STREAM_THREADS; }
@@ -408,6 +416,48 @@ extern "C" int gbu_convert_utf8_to_utf32(gbu_ctx *c, const uint8_t *src, uint64_
   p.result = result;
   set_dst(&p, dst, cap, 4);
   return launch(c, K_C8T32, p, stream);
+}
+
+extern "C" int gbu_utf16_length_from_utf32(gbu_ctx *c, const uint32_t *src, uint64_t n, uint64_t *len,
+                                           gbu_stream stream) {
+  gbu::Params p;
+  int rc = make_params(c, K_L16F32, src, n, 4, false, &p);
+  if (rc != GBU_OK) return rc;
+  if (!len) return GBU_BAD_ARGUMENT;
+  p.len_out = len;
+  return launch(c, K_L16F32, p, stream);
+}
+
+extern "C" int gbu_utf32_length_from_utf16le(gbu_ctx *c, const uint16_t *src, uint64_t n, uint64_t *len,
+                                             gbu_stream stream) {
+  gbu::Params p;
+  int rc = make_params(c, K_L32F16, src, n, 2, false, &p);
+  if (rc != GBU_OK) return rc;
+  if (!len) return GBU_BAD_ARGUMENT;
+  p.len_out = len;
+  return launch(c, K_L32F16, p, stream);
+}
+
+extern "C" int gbu_convert_utf32_to_utf16le(gbu_ctx *c, const uint32_t *src, uint64_t n, uint16_t *dst,
+                                            uint64_t cap, gbu_result *result, gbu_stream stream) {
+  gbu::Params p;
+  int rc = make_params(c, K_C32T16, src, n, 4, false, &p);
+  if (rc != GBU_OK) return rc;
+  if (!result || (cap > 0 && !dst) || ((uintptr_t)dst & 1)) return GBU_BAD_ARGUMENT;
+  p.result = result;
+  set_dst(&p, dst, cap, 2);
+  return launch(c, K_C32T16, p, stream);
+}
+
+extern "C" int gbu_convert_utf16le_to_utf32(gbu_ctx *c, const uint16_t *src, uint64_t n, uint32_t *dst,
+                                            uint64_t cap, gbu_result *result, gbu_stream stream) {
+  gbu::Params p;
+  int rc = make_params(c, K_C16T32, src, n, 2, false, &p);
+  if (rc != GBU_OK) return rc;
+  if (!result || (cap > 0 && !dst) || ((uintptr_t)dst & 3)) return GBU_BAD_ARGUMENT;
+  p.result = result;
+  set_dst(&p, dst, cap, 4);
+  return launch(c, K_C16T32, p, stream);
 }
 
 // ---- UTF-16BE ----------------------------------------------------------------------------

@@ -23,12 +23,17 @@ size_t utf16be_to_utf8_smem_bytes();
 const void *utf8_to_utf16be_kernel_ptr();
 size_t utf8_to_utf16be_smem_bytes();
 // UTF-32: read-only kernel (mode 0 validate_utf32, 1 utf8_length_from_utf32,
-// 2 utf32_length_from_utf8) and the transcoders between UTF-8 and UTF-32
+// 2 utf32_length_from_utf8, 3 utf16_length_from_utf32, 4 utf32_length_from_utf16le) and the
+// transcoders between UTF-32 and UTF-8 / UTF-16LE
 const void *utf32_stream_kernel_ptr(int mode);
 const void *utf32_to_utf8_kernel_ptr();
 size_t utf32_to_utf8_smem_bytes();
 const void *utf8_to_utf32_kernel_ptr();
 size_t utf8_to_utf32_smem_bytes();
+const void *utf32_to_utf16_kernel_ptr();
+size_t utf32_to_utf16_smem_bytes();
+const void *utf16_to_utf32_kernel_ptr();
+size_t utf16_to_utf32_smem_bytes();
 // the same transcoders over several strings per launch (SegParams; same shared memory)
 const void *utf8_to_utf16_segments_kernel_ptr();
 const void *utf16_to_utf8_segments_kernel_ptr();

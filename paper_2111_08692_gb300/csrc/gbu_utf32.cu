@@ -1,15 +1,19 @@
-// gbu_utf32.cu -- UTF-32: validation, lengths, and transcoding between UTF-8 and UTF-32.
+// gbu_utf32.cu -- UTF-32: validation, lengths, and transcoding to and from UTF-8 and UTF-16LE.
 //
 // UTF-32 is not in the paper, whose problem is UTF-8 and UTF-16: each 32-bit unit (host byte
 // order) holds one value, valid when Section 3 allows it -- below 1,114,112 (rule 5) and outside
 // D800-DFFF (rule 6); the first invalid unit is reported with that rule's kind at its index.
-//   * utf32_stream_kernel: the read-only operations (validation, the UTF-8 length of a UTF-32
-//     input, the UTF-32 length of a UTF-8 input), streaming 4 KB warp tiles like the UTF-8 and
-//     UTF-16 read-only kernels; a unit needs no neighbour.
+//   * utf32_stream_kernel: the read-only operations (validation, the UTF-8 and UTF-16 lengths of
+//     a UTF-32 input, the UTF-32 length of a UTF-8 or UTF-16LE input), streaming 4 KB warp tiles
+//     like the UTF-8 and UTF-16 read-only kernels; a unit needs no neighbour.
 //   * utf32_to_utf8_kernel / utf8_to_utf32_kernel: the partition loop of gbu_xcode.cuh with the
 //     two codecs below.  UTF-32 -> UTF-8 encodes each unit in 1-4 bytes; UTF-8 -> UTF-32 checks
 //     rules 1-6 with the word-level tests of gbu_chunk.cuh and stores one unit per leading byte,
 //     decoded from the four bytes that start there.
+//   * utf32_to_utf16_kernel / utf16_to_utf32_kernel: the same loop between UTF-16LE and UTF-32:
+//     a unit becomes one word (below 0x10000) or a surrogate pair; a UTF-16 word that is not a
+//     second surrogate becomes one unit (a first surrogate with its partner, which may be the
+//     first word of the next region), with Section 3's pair rules checked word by word.
 #include <stdint.h>
 
 #include "gbu_chunk.cuh"
@@ -39,7 +43,7 @@ static __device__ __noinline__ void resolve_utf32_error(const uint32_t *s, uint6
 
 // ---- read-only kernel ---------------------------------------------------------------------
 
-enum Utf32Mode { U_V32 = 0, U_L8 = 1, U_L32 = 2 };
+enum Utf32Mode { U_V32 = 0, U_L8 = 1, U_L32 = 2, U_L16 = 3, U_L32F16 = 4 };
 
 template <int MODE>
 __global__ void __launch_bounds__(STREAM_THREADS) utf32_stream_kernel(const Params p) {
@@ -68,12 +72,23 @@ __global__ void __launch_bounds__(STREAM_THREADS) utf32_stream_kernel(const Para
         // units outside the buffer read as zero, which is valid
         const bool bad = utf32_bad(U[0]) || utf32_bad(U[1]) || utf32_bad(U[2]) || utf32_bad(U[3]);
         if (bad && (unsigned long long)c < err_pos) err_pos = (unsigned long long)c;
-      } else if (MODE == U_L8) {
+      } else if (MODE == U_L8 || MODE == U_L16) {
         uint32_t n = 0;
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
           const bool valid = !edge || (c + 4 * j >= lo && c + 4 * j < hi);
-          n += valid ? utf8_len_of_unit(U[j]) : 0u;
+          const uint32_t len = MODE == U_L8 ? utf8_len_of_unit(U[j]) : (U[j] >= 0x10000u ? 2u : 1u);
+          n += valid ? len : 0u;
+        }
+        total += n;
+      } else if (MODE == U_L32F16) {
+        // UTF-16LE input: one unit per word that is not a second surrogate
+        uint32_t n = 0;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          const uint32_t w = (U[j >> 1] >> (16 * (j & 1))) & 0xFFFFu;
+          const bool valid = !edge || (c + 2 * j >= lo && c + 2 * j < hi);
+          n += (valid && (w & 0xFC00u) != 0xDC00u) ? 1u : 0u;
         }
         total += n;
       } else {
@@ -277,6 +292,177 @@ struct Utf8ToUtf32 {
   }
 };
 
+// ---- UTF-32 -> UTF-16LE codec ----------------------------------------------------------------
+
+struct Utf32ToUtf16 {
+  using Out = uint16_t;
+  static constexpr uint32_t STAGE = 2 * 128 + 32;  // 128 units of at most 2 words + alignment slack
+  static constexpr uint32_t F_NONASCII = 1;        // a unit >= 0x80 (or a chunk at a buffer end)
+  static constexpr uint32_t ASCII_MASK = 0xFFFFFF80u;
+  static constexpr uint32_t CHUNK_UNITS = 4;
+  static constexpr uint32_t REGION_UNITS = 128;
+  static constexpr uint32_t DIRECT_ALIGN = 4;  // its lanes store 4 words (8 bytes) each
+
+  __device__ __forceinline__ static bool ascii_region(uint32_t, uint32_t rflags) { return rflags == 0; }
+
+  __device__ __forceinline__ static void ascii_direct(uint16_t *dst, uint4 v, uint32_t, long long,
+                                                      unsigned long long &) {
+    const int lane = threadIdx.x & 31;
+    reinterpret_cast<uint2 *>(dst)[lane] = make_uint2(__byte_perm(v.x, v.y, 0x5410), __byte_perm(v.z, v.w, 0x5410));
+  }
+
+  __device__ __forceinline__ static uint32_t count(const Params &p, uint4 v, long long c, bool edge,
+                                                   uint32_t &flags) {
+    const uint32_t U[4] = {v.x, v.y, v.z, v.w};
+    if (!edge && ((U[0] | U[1] | U[2] | U[3]) & ASCII_MASK) == 0) {
+      flags = 0;
+      return 4;
+    }
+    flags = F_NONASCII;
+    uint32_t n = 0;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const bool valid = !edge || (c + 4 * j >= (long long)p.off0 && c + 4 * j < (long long)p.vbytes);
+      n += valid ? (U[j] >= 0x10000u ? 2u : 1u) : 0u;
+    }
+    return n;
+  }
+
+  // One word per unit below 0x10000, else the surrogate pair (Section 3); an invalid unit flags
+  // the chunk.
+  __device__ __forceinline__ static Region convert(const Params &p, uint4 v, uint32_t, uint32_t, long long c,
+                                                   bool edge, bool, uint16_t *st, uint32_t base, uint32_t x0,
+                                                   uint32_t rtot, uint32_t, unsigned long long &err_pos) {
+    const uint32_t U[4] = {v.x, v.y, v.z, v.w};
+    uint32_t o = base + x0;
+    bool bad = false;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const bool valid = !edge || (c + 4 * j >= (long long)p.off0 && c + 4 * j < (long long)p.vbytes);
+      if (!valid) continue;
+      const uint32_t u = U[j];
+      bad = bad || utf32_bad(u);
+      if (u < 0x10000u) {
+        st[o++] = (uint16_t)u;
+      } else {
+        const uint32_t t = u - 0x10000u;
+        st[o] = (uint16_t)(0xD800u + ((t >> 10) & 0x3FFu));
+        st[o + 1] = (uint16_t)(0xDC00u + (t & 0x3FFu));
+        o += 2;
+      }
+    }
+    if (bad && (unsigned long long)c < err_pos) err_pos = (unsigned long long)c;
+    return Region{rtot, 0u, 0u, rtot};
+  }
+};
+
+// ---- UTF-16LE -> UTF-32 codec ----------------------------------------------------------------
+
+struct Utf16ToUtf32 {
+  using Out = uint32_t;
+  static constexpr uint32_t STAGE = 256 + 32;  // at most one unit per word + alignment slack
+  static constexpr uint32_t F_NONASCII = 1;    // a word >= 0x80 (or a chunk at a buffer end)
+  static constexpr uint32_t ASCII_MASK = 0xFF80FF80u;
+  static constexpr uint32_t CHUNK_UNITS = 8;
+  static constexpr uint32_t REGION_UNITS = 256;
+  static constexpr uint32_t DIRECT_ALIGN = 4;  // its lanes store 8 units (32 bytes) each
+
+  __device__ __forceinline__ static bool ascii_region(uint32_t, uint32_t rflags) { return rflags == 0; }
+
+  __device__ __forceinline__ static void ascii_direct(uint32_t *dst, uint4 v, uint32_t, long long,
+                                                      unsigned long long &) {
+    const int lane = threadIdx.x & 31;
+    uint4 *d = reinterpret_cast<uint4 *>(dst) + 2 * lane;
+    d[0] = make_uint4(v.x & 0xFFFFu, v.x >> 16, v.y & 0xFFFFu, v.y >> 16);
+    d[1] = make_uint4(v.z & 0xFFFFu, v.z >> 16, v.w & 0xFFFFu, v.w >> 16);
+  }
+
+  __device__ __forceinline__ static uint32_t count(const Params &p, uint4 v, long long c, bool edge,
+                                                   uint32_t &flags) {
+    const uint32_t W[4] = {v.x, v.y, v.z, v.w};
+    if (!edge && ((W[0] | W[1] | W[2] | W[3]) & ASCII_MASK) == 0) {
+      flags = 0;
+      return 8;
+    }
+    flags = F_NONASCII;
+    uint32_t n = 0;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const uint32_t w = (W[j >> 1] >> (16 * (j & 1))) & 0xFFFFu;
+      const bool valid = !edge || (c + 2 * j >= (long long)p.off0 && c + 2 * j < (long long)p.vbytes);
+      n += (valid && !is_low16(w)) ? 1u : 0u;
+    }
+    return n;
+  }
+
+  // A word that is not a second surrogate stores one unit: its value, or with its partner the
+  // pair's value (the partner may be the next region's first word, `next`).  A word breaking
+  // the pair rules flags the chunk.
+  __device__ __forceinline__ static Region convert(const Params &p, uint4 v, uint32_t prev, uint32_t next,
+                                                   long long c, bool edge, bool, uint32_t *st, uint32_t base,
+                                                   uint32_t x0, uint32_t rtot, uint32_t,
+                                                   unsigned long long &err_pos) {
+    const uint32_t W[4] = {v.x, v.y, v.z, v.w};
+    uint32_t u[10];  // u[0] = word before the chunk, u[1..8] own words, u[9] = word after
+    u[0] = prev >> 16;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      u[1 + 2 * k] = W[k] & 0xFFFFu;
+      u[2 + 2 * k] = W[k] >> 16;
+    }
+    u[9] = next & 0xFFFFu;
+    uint32_t o = base + x0;
+    bool err = false;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const bool valid = !edge || (c + 2 * j >= (long long)p.off0 && c + 2 * j < (long long)p.vbytes);
+      if (!valid) continue;
+      const uint32_t w = u[j + 1];
+      const bool hs = is_high16(w), ls = is_low16(w);
+      const bool pair = hs && is_low16(u[j + 2]);
+      err = err || (hs && !pair) || (ls && !is_high16(u[j]));
+      if (!ls) st[o++] = pair ? (((w & 0x3FFu) << 10) | (u[j + 2] & 0x3FFu)) + 0x10000u : w;
+    }
+    if (err && (unsigned long long)c < err_pos) err_pos = (unsigned long long)c;
+    return Region{rtot, 0u, 0u, rtot};
+  }
+};
+
+__global__ void __launch_bounds__(XT, XBLOCKS) utf32_to_utf16_kernel(const Params p) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];  // sizeof(XSmem), set at launch
+  XSmem<Utf32ToUtf16> &sm = *reinterpret_cast<XSmem<Utf32ToUtf16> *>(smem_raw);
+  transcode<Utf32ToUtf16>(p, sm, [&](uint32_t status, unsigned long long key, unsigned long long tot) {
+    if (status) {
+      write_result(p.result, GBU_TIMEOUT, 0);
+    } else if (key != NO_ERROR) {
+      int32_t kind;
+      uint64_t off;
+      resolve_utf32_error(reinterpret_cast<const uint32_t *>(p.base + p.off0), p.n,
+                          ((long long)key - (long long)p.off0) / 4, &kind, &off);
+      write_result(p.result, kind, off);
+    } else {
+      write_result(p.result, tot > p.cap ? GBU_OUTPUT_TOO_SMALL : GBU_OK, tot);
+    }
+  });
+}
+
+__global__ void __launch_bounds__(XT, XBLOCKS) utf16_to_utf32_kernel(const Params p) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];  // sizeof(XSmem), set at launch
+  XSmem<Utf16ToUtf32> &sm = *reinterpret_cast<XSmem<Utf16ToUtf32> *>(smem_raw);
+  transcode<Utf16ToUtf32>(p, sm, [&](uint32_t status, unsigned long long key, unsigned long long tot) {
+    if (status) {
+      write_result(p.result, GBU_TIMEOUT, 0);
+    } else if (key != NO_ERROR) {
+      uint64_t off;
+      resolve_utf16_error(reinterpret_cast<const uint16_t *>(p.base + p.off0), p.n,
+                          ((long long)key - (long long)p.off0) / 2, &off);
+      write_result(p.result, GBU_SURROGATE, off);
+    } else {
+      write_result(p.result, tot > p.cap ? GBU_OUTPUT_TOO_SMALL : GBU_OK, tot);
+    }
+  });
+}
+
 __global__ void __launch_bounds__(XT, XBLOCKS) utf32_to_utf8_kernel(const Params p) {
   extern __shared__ __align__(128) unsigned char smem_raw[];  // sizeof(XSmem), set at launch
   XSmem<Utf32ToUtf8> &sm = *reinterpret_cast<XSmem<Utf32ToUtf8> *>(smem_raw);
@@ -316,9 +502,15 @@ const void *utf32_stream_kernel_ptr(int mode) {
   switch (mode) {
     case U_V32: return (const void *)utf32_stream_kernel<U_V32>;
     case U_L8: return (const void *)utf32_stream_kernel<U_L8>;
+    case U_L16: return (const void *)utf32_stream_kernel<U_L16>;
+    case U_L32F16: return (const void *)utf32_stream_kernel<U_L32F16>;
     default: return (const void *)utf32_stream_kernel<U_L32>;
   }
 }
+const void *utf32_to_utf16_kernel_ptr() { return (const void *)utf32_to_utf16_kernel; }
+size_t utf32_to_utf16_smem_bytes() { return sizeof(XSmem<Utf32ToUtf16>); }
+const void *utf16_to_utf32_kernel_ptr() { return (const void *)utf16_to_utf32_kernel; }
+size_t utf16_to_utf32_smem_bytes() { return sizeof(XSmem<Utf16ToUtf32>); }
 const void *utf32_to_utf8_kernel_ptr() { return (const void *)utf32_to_utf8_kernel; }
 size_t utf32_to_utf8_smem_bytes() { return sizeof(XSmem<Utf32ToUtf8>); }
 const void *utf8_to_utf32_kernel_ptr() { return (const void *)utf8_to_utf32_kernel; }
