@@ -72,13 +72,20 @@ __global__ void __launch_bounds__(STREAM_THREADS) utf32_stream_kernel(const Para
         // units outside the buffer read as zero, which is valid
         const bool bad = utf32_bad(U[0]) || utf32_bad(U[1]) || utf32_bad(U[2]) || utf32_bad(U[3]);
         if (bad && (unsigned long long)c < err_pos) err_pos = (unsigned long long)c;
-      } else if (MODE == U_L8 || MODE == U_L16) {
+      } else if (MODE == U_L8) {
         uint32_t n = 0;
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
           const bool valid = !edge || (c + 4 * j >= lo && c + 4 * j < hi);
-          const uint32_t len = MODE == U_L8 ? utf8_len_of_unit(U[j]) : (U[j] >= 0x10000u ? 2u : 1u);
-          n += valid ? len : 0u;
+          n += valid ? utf8_len_of_unit(U[j]) : 0u;
+        }
+        total += n;
+      } else if (MODE == U_L16) {
+        uint32_t n = 0;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const bool valid = !edge || (c + 4 * j >= lo && c + 4 * j < hi);
+          n += valid ? (U[j] >= 0x10000u ? 2u : 1u) : 0u;
         }
         total += n;
       } else if (MODE == U_L32F16) {
