@@ -1,5 +1,5 @@
 /*
- * gbu_oracle.c -- scalar CPU reference codec for UTF-8 and UTF-16 (LE and BE).
+ * gbu_oracle.c -- scalar CPU reference codec for UTF-8, UTF-16 (LE and BE) and UTF-32.
  *
  * TEST INFRASTRUCTURE ONLY: see gbu_oracle.h.  Plain C, one character at a time, no tables,
  * no blocking, no SIMD.  Nothing here is shared with the CUDA library.
@@ -28,7 +28,9 @@
  * hand from Section 3 (tests/golden/), a round trip of all 1,112,064 scalar values against
  * CPython's codecs, brute force over every UTF-8 string of up to four bytes against a second
  * formulation and against CPython's decoder offsets, and every pair of 16-bit words against a
- * closed form.  Every function below is pinned; the error kinds are pinned by the brute
+ * closed form; the UTF-16BE and UTF-32 functions are pinned by CPython's utf-16-be and
+ * utf-32-le codecs on every scalar value and by random unpaired surrogates and out-of-range
+ * units.  Every function below is pinned; the error kinds are pinned by the brute
  * force's completion enumeration (a kind other than TOO_SHORT must be broken by every
  * completion of the bytes read).
  */

@@ -1,5 +1,5 @@
 /*
- * gbu_oracle.h -- scalar CPU reference codec for UTF-8 and UTF-16 (LE and BE).
+ * gbu_oracle.h -- scalar CPU reference codec for UTF-8, UTF-16 (LE and BE) and UTF-32.
  *
  * TEST INFRASTRUCTURE ONLY.  The test suite, the smoke check and the CPU-baseline leg of the
  * benchmark call this code; the CUDA library never includes, links or calls it, and this code
@@ -9,7 +9,7 @@
  * What it computes follows the paper's Section 3 (the UTF-8 byte layout, the six validity
  * rules, and UTF-16 surrogate pairs) and Section 5 (every transcoding also validates).
  * Offsets, counts and capacities are in code units of the input or output format: bytes for
- * UTF-8, 16-bit units for UTF-16LE.
+ * UTF-8, 16-bit units for UTF-16LE and UTF-16BE, 32-bit units for UTF-32.
  *
  * Parity status of each function is stated in oracle/gbu_oracle.c.
  */
