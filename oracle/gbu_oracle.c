@@ -30,9 +30,9 @@
  * formulation and against CPython's decoder offsets, and every pair of 16-bit words against a
  * closed form; the UTF-16BE and UTF-32 functions are pinned by CPython's utf-16-be and
  * utf-32-le codecs on every scalar value and by random unpaired surrogates and out-of-range
- * units.  Every function below is pinned; the error kinds are pinned by the brute
- * force's completion enumeration (a kind other than TOO_SHORT must be broken by every
- * completion of the bytes read).
+ * units, and the UTF-32 lengths also by closed forms on arbitrary input.  Every function below
+ * is pinned; the error kinds are pinned by the brute force's completion enumeration (a kind
+ * other than TOO_SHORT must be broken by every completion of the bytes read).
  */
 #include "gbu_oracle.h"
 

@@ -2,7 +2,8 @@
 
 Each function raises AssertionError when the codec under test disagrees with:
   * the hand-derived fixtures in tests/golden/ (paper Section 3 boundaries and rules),
-  * CPython's strict ``utf-8`` / ``utf-16-le`` codecs (an independent library decoder),
+  * CPython's strict ``utf-8`` / ``utf-16-le`` / ``utf-16-be`` / ``utf-32-le`` codecs (an
+    independent library decoder),
   * the brute-force second formulation in tests/helpers/bruteforce.c, or
   * closed forms of the length formulas.
 They take the codec and the brute-force library as arguments so that the mutation test can
@@ -296,6 +297,11 @@ def check_length_closed_forms(codec):
         assert u8.size == 1000 * u8_per and u16.size == 1000 * u16_per
         assert codec.utf16_length_from_utf8(u8) == 1000 * u16_per
         assert codec.utf8_length_from_utf16le(u16) == 1000 * u8_per
+        # UTF-32: one unit per character whatever its size
+        assert codec.utf8_length_from_utf32(cps) == 1000 * u8_per
+        assert codec.utf16_length_from_utf32(cps) == 1000 * u16_per
+        assert codec.utf32_length_from_utf8(u8) == 1000
+        assert codec.utf32_length_from_utf16le(u16) == 1000
     # formulas on arbitrary (invalid) input: one word per non-continuation byte plus one per
     # byte F0-FF; two bytes per surrogate word
     junk = np.arange(256, dtype=np.uint8)
@@ -303,3 +309,16 @@ def check_length_closed_forms(codec):
     sur = np.arange(0xD800, 0xE000, dtype=np.uint16)
     assert codec.utf8_length_from_utf16le(sur) == 2 * 2048
     assert codec.utf16_length_from_utf8(b"") == 0 and codec.utf8_length_from_utf16le(b"") == 0
+    # the UTF-32 lengths on arbitrary input: one unit per non-continuation byte; one per word
+    # that is not a second surrogate (a first surrogate stands for its pair); UTF-8 bytes and
+    # UTF-16 words of a unit by its value alone (a surrogate value as a three-byte form, a unit
+    # above 10FFFF as a four-byte form or a pair)
+    assert codec.utf32_length_from_utf8(junk) == 256 - 64
+    assert codec.utf32_length_from_utf16le(np.arange(0xD800, 0xDC00, dtype=np.uint16)) == 1024
+    assert codec.utf32_length_from_utf16le(np.arange(0xDC00, 0xE000, dtype=np.uint16)) == 0
+    bad = np.array([0xD800, 0xDFFF, 0x110000, 0xFFFFFFFF], dtype=np.uint32)
+    assert codec.utf8_length_from_utf32(bad) == 3 + 3 + 4 + 4
+    assert codec.utf16_length_from_utf32(bad) == 1 + 1 + 2 + 2
+    empty32 = np.zeros(0, dtype=np.uint32)
+    assert codec.utf8_length_from_utf32(empty32) == 0 and codec.utf16_length_from_utf32(empty32) == 0
+    assert codec.utf32_length_from_utf8(b"") == 0 and codec.utf32_length_from_utf16le(b"") == 0

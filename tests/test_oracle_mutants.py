@@ -35,12 +35,36 @@ MUTANTS = [
      "  return r;\n}\n\nor_result or_validate_utf16le"),
     ("rule 1 reported as rule 3", "if ((lead & 0xF8) == 0xF8) return make_result(OR_HEADER_BITS, i);",
      "if ((lead & 0xF8) == 0xF8) return make_result(OR_TOO_LONG, i);"),
+    # UTF-16BE and UTF-32
+    ("UTF-16BE output left in little-endian order",
+     "  for (uint64_t i = 0; i < written && i < cap; ++i) dst[i] = swap16(dst[i]);\n", ""),
+    ("UTF-16BE byte exchange loses the high byte", "return (uint16_t)((w >> 8) | (w << 8));",
+     "return (uint16_t)(w >> 8);"),
+    ("UTF-32 rule 5 bound off by one", "if (u >= 1114112u) return OR_TOO_LARGE;",
+     "if (u > 1114112u) return OR_TOO_LARGE;"),
+    ("UTF-32 surrogate range only the first surrogates", "if (u >= 0xD800 && u <= 0xDFFF) return OR_SURROGATE;",
+     "if (u >= 0xD800 && u <= 0xDBFF) return OR_SURROGATE;"),
+    ("UTF-32 to UTF-8 skips validation",
+     "    if (k != OR_OK) return make_result(k, i);\n    uint8_t b[4];", "    uint8_t b[4];"),
+    ("UTF-8 length of a UTF-32 unit: four-byte bound off by one", "(src[i] < 0x10000 ? 3 : 4)",
+     "(src[i] <= 0x10000 ? 3 : 4)"),
+    ("UTF-32 length of UTF-8 counts four-byte leads twice",
+     "    if (!is_continuation(src[i])) total += 1;\n  return total;",
+     "    if (!is_continuation(src[i])) total += 1 + (src[i] >= 0xF0);\n  return total;"),
+    ("UTF-16 length of a UTF-32 unit: pair bound off by one", "total += src[i] < 0x10000 ? 1 : 2;",
+     "total += src[i] < 0xFFFF ? 1 : 2;"),
+    ("UTF-32 length of UTF-16 counts second surrogates instead of first",
+     "if (src[i] < 0xDC00 || src[i] > 0xDFFF) total += 1;", "if (src[i] < 0xD800 || src[i] > 0xDBFF) total += 1;"),
+    ("UTF-8 to UTF-32 stores the low 16 bits", "if (dst32 && out < cap) dst32[out] = value;",
+     "if (dst32 && out < cap) dst32[out] = value & 0xFFFF;"),
 ]
 
 
 def _battery(codec, bf):
     P.check_golden(codec)
     P.check_all_scalars(codec)
+    P.check_all_scalars_utf16be(codec)
+    P.check_all_scalars_utf32(codec)
     P.check_bruteforce(bf, max_len=3)
     P.check_utf16_pairs(bf, codec, full=False)
     P.check_length_closed_forms(codec)
