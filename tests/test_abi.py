@@ -52,3 +52,72 @@ def test_product_code_never_imports_the_oracle():
             text = open(f).read()
             assert not re.search(r"^\s*(import|from)\s+oracle\b", text, re.M), f
             assert "gbu_oracle" not in text, f
+
+
+_HANDLES = r"(?:const\s+)?(?:gbu_ctx|gbu_chunked|gbu_server|gbu_arena|gbu_graph)\s*\*"
+
+
+def _int_entry_points_taking_a_handle():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = re.sub(r"/\*.*?\*/", "", open(h).read(), flags=re.S)
+        for m in re.finditer(r"\bint\s+(gbu_[a-z0-9_]+)\s*\(\s*" + _HANDLES, text):
+            names.add(m.group(1))
+    names.discard("gbu_launch_config")  # returns the number of values written (0 for NULL)
+    return sorted(names)
+
+
+def _placeholder(t):
+    # pointers NULL; counts, sizes and ops 1 (so that "n > 0 with a NULL pointer" applies too)
+    import ctypes
+    if t is ctypes.c_void_p or isinstance(t, type(ctypes.POINTER(ctypes.c_int))):
+        return None
+    return 1
+
+
+def test_null_handles_are_bad_arguments_without_a_launch():
+    """Every int entry point that takes a context, resumable stream, server, arena or graph
+    rejects a NULL one with GBU_BAD_ARGUMENT before touching a device (the header's argument
+    rule), and the binding declares the argument types of each."""
+    import paper_2111_08692_gb300 as g
+    L = g.lib()
+    names = _int_entry_points_taking_a_handle()
+    assert len(names) >= 40, names
+    for name in names:
+        f = getattr(L, name)
+        assert f.argtypes, name + " has no argtypes in the binding"
+        rc = f(*[_placeholder(t) for t in f.argtypes])
+        want = -17 if name == "gbu_server_poll" else 17  # poll returns a count, or minus a status
+        assert rc == want, (name, rc)
+
+
+def test_null_safe_queries_and_argument_checks_before_the_device():
+    import paper_2111_08692_gb300 as g
+    L = g.lib()
+    assert L.gbu_launch_count(None) == 0
+    assert L.gbu_launch_config(None, None, 0) == 0
+    assert L.gbu_graph_kernels(None) == 0
+    assert L.gbu_server_now_ns(None) == 0
+    assert L.gbu_arena_used(None) == 0 and L.gbu_arena_largest_free(None) == 0
+    for destroy in ("gbu_destroy", "gbu_chunked_destroy", "gbu_server_destroy", "gbu_graph_destroy",
+                    "gbu_arena_destroy"):
+        getattr(L, destroy)(None)  # a NULL handle is ignored
+    # the allocation-free transcoder checks its size and pointers before its device setup
+    assert L.gbu_convert_utf8_to_utf16le_noalloc(None, 16, None, 0, None, None) == 17
+    assert L.gbu_convert_utf8_to_utf16le_noalloc(None, (1 << 28) + 1, None, 0, None, None) == 20
+    # a resumable stream with an unknown operation or no chunk size is refused before any device call
+    assert not L.gbu_chunked_create(0, 99, 1024)
+    assert not L.gbu_chunked_create(0, 0, 0)
+    # the host-side cut and combination functions check their arguments
+    assert L.gbu_shard_cuts_utf8_host(None, 0, 0, None) == 17
+    assert L.gbu_combine_shards(None, None, 0, None) == 17
+
+
+def test_create_without_a_device_returns_null():
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    import paper_2111_08692_gb300 as g
+    L = g.lib()
+    assert not L.gbu_create(0, 1 << 20)
+    assert not L.gbu_chunked_create(0, 0, 1024)
