@@ -61,6 +61,23 @@ def check_golden(codec):
         assert r == ("OK", len(u16)) and np.array_equal(d, u16), hex(cp)
         r, d = codec.convert_utf16le_to_utf8(u16)
         assert r == ("OK", len(u8)) and d.tobytes() == u8, hex(cp)
+        # the same character as UTF-16BE (each word's bytes exchanged) and as one UTF-32 unit
+        be = u16.byteswap()
+        assert codec.validate_utf16be(be) == ("OK", len(u16)), hex(cp)
+        r, d = codec.convert_utf16be_to_utf8(be)
+        assert r == ("OK", len(u8)) and d.tobytes() == u8, hex(cp)
+        r, d = codec.convert_utf8_to_utf16be(u8)
+        assert r == ("OK", len(u16)) and np.array_equal(d, be), hex(cp)
+        u32 = np.array([cp], dtype=np.uint32)
+        assert codec.validate_utf32(u32) == ("OK", 1), hex(cp)
+        r, d = codec.convert_utf8_to_utf32(u8)
+        assert r == ("OK", 1) and np.array_equal(d, u32), hex(cp)
+        r, d = codec.convert_utf32_to_utf8(u32)
+        assert r == ("OK", len(u8)) and d.tobytes() == u8, hex(cp)
+        r, d = codec.convert_utf32_to_utf16le(u32)
+        assert r == ("OK", len(u16)) and np.array_equal(d, u16), hex(cp)
+        r, d = codec.convert_utf16le_to_utf32(u16)
+        assert r == ("OK", 1) and np.array_equal(d, u32), hex(cp)
     # all the fixture's characters in one string, then cut at every capacity
     all8 = b"".join(s[1] for s in scal)
     all16 = np.concatenate([s[2] for s in scal])
@@ -77,6 +94,8 @@ def check_golden(codec):
         assert codec.validate_utf8(arr) == (kind, off), arr.tobytes().hex()
         r, _ = codec.convert_utf8_to_utf16le(arr, 16)
         assert r == (kind, off), arr.tobytes().hex()
+        r, _ = codec.convert_utf8_to_utf32(arr, 16)
+        assert r == (kind, off), arr.tobytes().hex()
         # CPython's strict decoder reports the same first offset
         try:
             arr.tobytes().decode("utf-8")
@@ -87,6 +106,9 @@ def check_golden(codec):
         assert codec.validate_utf16le(arr) == (kind, off), arr
         r, _ = codec.convert_utf16le_to_utf8(arr, 16)
         assert r == (kind, off), arr
+        r, _ = codec.convert_utf16le_to_utf32(arr, 16)
+        assert r == (kind, off), arr
+        assert codec.validate_utf16be(arr.byteswap()) == (kind, off), arr
         try:
             arr.tobytes().decode("utf-16-le")
             raise AssertionError("CPython accepted %r" % arr)
