@@ -144,3 +144,42 @@ def test_batched_strings():
                 s16.decode("utf-16-le")
         if not d["err8"][i] and not d["err16"][i]:
             assert s8.decode("utf-8") == s16.decode("utf-16-le"), i
+
+
+def test_serving_pools_and_trace():
+    pools = W.serving_pools(pool_bytes=1 << 20, error_every=1 << 14)
+    assert set(pools) == set(W.PROFILE_ORDER)
+    for prof, p in pools.items():
+        u8, u16 = p["u8"], p["u16"]
+        u8.tobytes().decode("utf-8")
+        u16.tobytes().decode("utf-16-le")
+        # character starts (plus the end), and the corrupted copies differ only at some of them
+        assert np.array_equal(p["starts8"][:-1], np.flatnonzero((u8 & 0xC0) != 0x80)) and p["starts8"][-1] == u8.size
+        d8 = np.flatnonzero(p["bad8"] != u8)
+        d16 = np.flatnonzero(p["bad16"] != u16)
+        assert 1 <= d8.size <= u8.size // (1 << 14) and 1 <= d16.size <= u16.size // (1 << 14)
+        assert np.isin(d8, p["starts8"]).all() and np.isin(d16, p["starts16"]).all()
+        assert (p["bad8"][d8] >= 0xF8).all() and ((p["bad16"][d16] >= 0xDC00) & (p["bad16"][d16] < 0xE000)).all()
+
+    count, rate = 20000, 1e5
+    t = W.serving_trace(count, rate, pools, p_bad=0.1)
+    arr = t["arrival_ns"]
+    assert arr[0] == 0 and (np.diff(arr) >= 0).all()
+    mean_gap = arr[-1] / (count - 1) / 1e9
+    assert abs(mean_gap * rate - 1) < 0.05  # Poisson arrivals at the offered rate
+    frac = np.bincount(t["op"], minlength=4) / count
+    for f, want in zip(frac, (0.05, 0.05, 0.45, 0.45)):
+        assert abs(f - want) <= 5 * (want * (1 - want) / count) ** 0.5, frac
+    assert abs(t["bad"].mean() - 0.1) <= 5 * (0.09 / count) ** 0.5
+    for i in range(count):
+        p = pools[W.PROFILE_ORDER[t["profile"][i]]]
+        utf16 = t["op"][i] in (1, 3)
+        st = p["starts16"] if utf16 else p["starts8"]
+        s0, n = int(t["start"][i]), int(t["n"][i])
+        assert n * (2 if utf16 else 1) <= 16 << 20
+        # every request is a slice between character starts, so a clean one is valid text
+        k = np.searchsorted(st, [s0, s0 + n])
+        assert (k < st.size).all() and st[k[0]] == s0 and st[k[1]] == s0 + n, i
+        if not t["bad"][i] and i % 50 == 0:
+            src = p["u16"] if utf16 else p["u8"]
+            src[s0:s0 + n].tobytes().decode("utf-16-le" if utf16 else "utf-8")
