@@ -344,3 +344,36 @@ def check_length_closed_forms(codec):
     empty32 = np.zeros(0, dtype=np.uint32)
     assert codec.utf8_length_from_utf32(empty32) == 0 and codec.utf16_length_from_utf32(empty32) == 0
     assert codec.utf32_length_from_utf8(b"") == 0 and codec.utf32_length_from_utf16le(b"") == 0
+
+
+def check_edge_cases(codec):
+    """Empty inputs, and an input error that takes precedence over a too-small capacity (the
+    error's offset lies past the capacity), for every transcoder; the units before the cut are
+    still the conversion of the valid prefix."""
+    e8, e16, e32 = np.zeros(0, np.uint8), np.zeros(0, np.uint16), np.zeros(0, np.uint32)
+    assert codec.validate_utf8(e8) == ("OK", 0) and codec.validate_utf16le(e16) == ("OK", 0)
+    assert codec.validate_utf16be(e16) == ("OK", 0) and codec.validate_utf32(e32) == ("OK", 0)
+    for f, e in ((codec.convert_utf8_to_utf16le, e8), (codec.convert_utf16le_to_utf8, e16),
+                 (codec.convert_utf8_to_utf16be, e8), (codec.convert_utf16be_to_utf8, e16),
+                 (codec.convert_utf8_to_utf32, e8), (codec.convert_utf32_to_utf8, e32),
+                 (codec.convert_utf16le_to_utf32, e16), (codec.convert_utf32_to_utf16le, e32)):
+        assert f(e)[0] == ("OK", 0)
+        assert f(e, 0)[0] == ("OK", 0)
+    # "ab€" (U+20AC: E2 82 AC) then an invalid unit at index 5 (UTF-8) or 3 (words and units)
+    u8 = np.frombuffer("ab€".encode() + b"\xff", np.uint8)
+    u16 = np.array([0x61, 0x62, 0x20AC, 0xDC00], np.uint16)
+    u32 = np.array([0x61, 0x62, 0x20AC, 0x110000], np.uint32)
+    # (transcoder, input, expected result, first output unit as it lies in memory)
+    cases = [(codec.convert_utf8_to_utf16le, u8, ("HEADER_BITS", 5), 0x61),
+             (codec.convert_utf8_to_utf16be, u8, ("HEADER_BITS", 5), 0x6100),
+             (codec.convert_utf8_to_utf32, u8, ("HEADER_BITS", 5), 0x61),
+             (codec.convert_utf16le_to_utf8, u16, ("SURROGATE", 3), 0x61),
+             (codec.convert_utf16be_to_utf8, u16.byteswap(), ("SURROGATE", 3), 0x61),
+             (codec.convert_utf16le_to_utf32, u16, ("SURROGATE", 3), 0x61),
+             (codec.convert_utf32_to_utf8, u32, ("TOO_LARGE", 3), 0x61),
+             (codec.convert_utf32_to_utf16le, u32, ("TOO_LARGE", 3), 0x61)]
+    for f, src, want, first in cases:
+        for cap in (0, 1, 2):
+            r, d = f(src, cap)
+            assert r == want, (f.__name__, cap, r)
+            assert cap == 0 or int(d[0]) == first, (f.__name__, cap, d)

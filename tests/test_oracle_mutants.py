@@ -55,6 +55,12 @@ MUTANTS = [
      "total += src[i] < 0xFFFF ? 1 : 2;"),
     ("UTF-32 length of UTF-16 counts second surrogates instead of first",
      "if (src[i] < 0xDC00 || src[i] > 0xDFFF) total += 1;", "if (src[i] < 0xD800 || src[i] > 0xDBFF) total += 1;"),
+    ("UTF-8 to UTF-16 capacity checked before the input error",
+     "or_result r = scan_utf8(src, n, dst, cap);\n  if (r.status == OR_OK && r.count > cap)",
+     "or_result r = scan_utf8(src, n, dst, cap);\n  if (r.count > cap)"),
+    ("UTF-16 to UTF-8 capacity checked before the input error",
+     "or_result r = scan_utf16(src, n, dst, cap);\n  if (r.status == OR_OK && r.count > cap)",
+     "or_result r = scan_utf16(src, n, dst, cap);\n  if (r.count > cap)"),
     ("UTF-8 to UTF-32 stores the low 16 bits", "if (dst32 && out < cap) dst32[out] = value;",
      "if (dst32 && out < cap) dst32[out] = value & 0xFFFF;"),
 ]
@@ -68,6 +74,7 @@ def _battery(codec, bf):
     P.check_bruteforce(bf, max_len=3)
     P.check_utf16_pairs(bf, codec, full=False)
     P.check_length_closed_forms(codec)
+    P.check_edge_cases(codec)
     P.check_cpython_offsets(bf, three_byte_leads=range(0xE0, 0xF8))
 
 

@@ -65,6 +65,10 @@ def test_empty_inputs():
     assert o.convert_utf16le_to_utf8(b"")[0] == ("OK", 0)
 
 
+def test_edge_cases_every_transcoder():
+    P.check_edge_cases(oracle.default())
+
+
 def test_error_takes_precedence_over_capacity():
     o = oracle.default()
     src = "ab€".encode() + b"\xff"
