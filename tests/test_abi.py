@@ -121,3 +121,19 @@ def test_create_without_a_device_returns_null():
     L = g.lib()
     assert not L.gbu_create(0, 1 << 20)
     assert not L.gbu_chunked_create(0, 0, 1024)
+
+
+@pytest.mark.parametrize("lang,std", [("c", "-std=c99"), ("c++", "-std=c++11")])
+def test_header_is_plain_c(lang, std):
+    """include/gbutf.h needs no CUDA or torch header: it compiles on its own as strict C99 and
+    as C++11 (streams are opaque pointers, results plain structs)."""
+    import shutil
+    cc = shutil.which("gcc" if lang == "c" else "g++")
+    if cc is None:
+        pytest.skip("no host compiler")
+    src = ('#include "gbutf.h"\n'
+           'typedef char gbu_result_is_16_bytes[sizeof(gbu_result) == 16 ? 1 : -1];\n'
+           'int main(void) { return 0; }\n')
+    subprocess.run([cc, std, "-Wall", "-Wextra", "-Werror", "-pedantic", "-fsyntax-only", "-x", lang,
+                    "-I", os.path.join(ROOT, "include"), "-"], input=src, text=True, check=True,
+                   capture_output=True)
