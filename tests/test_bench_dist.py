@@ -68,3 +68,36 @@ def test_bench_arguments_parse(flag, monkeypatch):
     monkeypatch.setattr(sys, "argv", ["bench.py", flag, "--steps", "4", "--warmup", "3"])
     a = bench.parse()
     assert a.steps == 4 and a.warmup == 3 and a.gpus == 1
+
+
+def _run_bench(args, tmp_path, extra_env=None):
+    import subprocess
+    env = dict(os.environ, GBU_WORKLOAD_CACHE=str(tmp_path / "cache"))
+    env.update(extra_env or {})
+    return subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), *args], cwd=ROOT, env=env,
+                          capture_output=True, text=True, timeout=600)
+
+
+def test_reference_arm_line(tmp_path):
+    """`bench.py --impl reference` (the oracle on the host cores, on bounded samples of the same
+    workload) prints one JSON line with the contract's keys."""
+    import json
+    p = _run_bench(["--impl", "reference", "--size", str(1 << 20), "--cpu-sample", str(1 << 18),
+                    "--steps", "2", "--warmup", "1"], tmp_path)
+    assert p.returncode == 0, p.stderr[-2000:]
+    lines = [ln for ln in p.stdout.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1, p.stdout
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["unit"] == "GB/s" and d["higher_is_better"] is True
+    assert d["steps"] == 2 and d["warmup"] == 1 and d["n_gpus"] == 1 and d["value"] > 0
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
+    assert d["cpu_baseline"]["value"] == d["value"] and d["cpu_baseline"]["sample"]
+    assert d["e2e"] == {"value": d["value"], "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+    assert d["config"]["workload"] and "model" not in d["config"]
+
+
+def test_reference_arm_other_ranks_exit_quietly(tmp_path):
+    p = _run_bench(["--impl", "reference", "--size", str(1 << 20), "--steps", "1", "--warmup", "1"], tmp_path,
+                   {"RANK": "1", "LOCAL_RANK": "1", "WORLD_SIZE": "2"})
+    assert p.returncode == 0, p.stderr[-2000:]
+    assert not [ln for ln in p.stdout.splitlines() if ln.startswith("{")]
