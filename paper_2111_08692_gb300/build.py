@@ -64,8 +64,9 @@ KERNEL_SOURCES = {
 
 
 def strip_comments(text: str) -> str:
-    """C/C++ source without its comments and blank lines (string and character literals are
-    kept as they are), so that editing a comment does not change a kernel's hash."""
+    """C/C++ source without its comments and whitespace (comment markers inside string and
+    character literals are kept), so that editing a comment or the layout does not change a
+    kernel's hash."""
     out, i, n = [], 0, len(text)
     while i < n:
         c = text[i]
