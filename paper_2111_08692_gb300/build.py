@@ -56,10 +56,10 @@ _STREAM = ["gbu_stream.cu", "gbu_chunk.cuh", "gbu_device.cuh"]
 KERNEL_SOURCES = {
     "validate_utf8": _STREAM, "utf16_length_from_utf8": _STREAM,
     "validate_utf16le": _STREAM, "utf8_length_from_utf16le": _STREAM,
-    "convert_utf8_to_utf16le": ["gbu_utf8.cu", "gbu_codec_utf8.cuh", "gbu_xcode.cuh", "gbu_chunk.cuh",
-                                "gbu_device.cuh"],
-    "convert_utf16le_to_utf8": ["gbu_utf16.cu", "gbu_codec_utf16.cuh", "gbu_xcode.cuh", "gbu_chunk.cuh",
-                                "gbu_device.cuh"],
+    "convert_utf8_to_utf16le": ["gbu_utf8.cu", "gbu_wide_utf8.cuh", "gbu_wide.cuh", "gbu_codec_utf8.cuh",
+                                "gbu_xcode.cuh", "gbu_chunk.cuh", "gbu_device.cuh"],
+    "convert_utf16le_to_utf8": ["gbu_utf16.cu", "gbu_wide_utf16.cuh", "gbu_wide.cuh", "gbu_codec_utf16.cuh",
+                                "gbu_xcode.cuh", "gbu_chunk.cuh", "gbu_device.cuh"],
 }
 
 

@@ -179,7 +179,7 @@ extern "C" gbu_ctx *gbu_create(int device, uint64_t max_units) {
            c->scan_blocks_per_sm >= 1;
   for (int d = 0; d < 2 && occ_ok; ++d) {
     const void *f = d == 0 ? gbu::utf8_to_utf16_segments_kernel_ptr() : gbu::utf16_to_utf8_segments_kernel_ptr();
-    const size_t smem = d == 0 ? gbu::utf8_to_utf16_smem_bytes() : gbu::utf16_to_utf8_smem_bytes();
+    const size_t smem = d == 0 ? gbu::utf8_to_utf16_segments_smem_bytes() : gbu::utf16_to_utf8_segments_smem_bytes();
     occ_ok = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) == cudaSuccess &&
              cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c->seg_blocks_per_sm[d], f, gbu::XT, smem) ==
                  cudaSuccess &&
@@ -253,9 +253,12 @@ static int make_params(gbu_ctx *c, int k, const void *src, uint64_t n, uint32_t 
   if (unit_bytes == 2 && ((uintptr_t)src & 1)) return GBU_BAD_ARGUMENT;
   if (unit_bytes == 4 && ((uintptr_t)src & 3)) return GBU_BAD_ARGUMENT;
   memset(p, 0, sizeof(*p));
+  // the source rounded down to 16 bytes (32 for the UTF-8 <-> UTF-16LE transcoders, whose
+  // lanes read 32 bytes at a time)
   const uintptr_t a = (uintptr_t)src;
-  p->base = (const uint8_t *)(a & ~(uintptr_t)15);
-  p->off0 = (uint32_t)(a & 15);
+  const uintptr_t amask = (k == K_C8 || k == K_C16) ? 31 : 15;
+  p->base = (const uint8_t *)(a & ~amask);
+  p->off0 = (uint32_t)(a & amask);
   p->n = n;
   p->vbytes = p->off0 + n * unit_bytes;
   // UTF-8 validation looks at the three positions past the end (a cut sequence fails there)
@@ -816,7 +819,7 @@ int gbu_internal_convert_segments(gbu_ctx *c, int op, const gbu::StringDesc *des
   void *args[] = {(void *)&q};
   cudaError_t e = cudaLaunchKernel(
       d == 0 ? gbu::utf8_to_utf16_segments_kernel_ptr() : gbu::utf16_to_utf8_segments_kernel_ptr(), dim3((unsigned)grid),
-      dim3(gbu::XT), args, d == 0 ? gbu::utf8_to_utf16_smem_bytes() : gbu::utf16_to_utf8_smem_bytes(),
+      dim3(gbu::XT), args, d == 0 ? gbu::utf8_to_utf16_segments_smem_bytes() : gbu::utf16_to_utf8_segments_smem_bytes(),
       (cudaStream_t)stream);
   if (e != cudaSuccess) {
     cudaGetLastError();

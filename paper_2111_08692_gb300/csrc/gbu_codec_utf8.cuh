@@ -248,7 +248,8 @@ struct Utf8ToUtf16 {
       if (bad && (unsigned long long)c < err_pos) err_pos = (unsigned long long)c;
       return Region{rtot, 0u, 0u, rtot};
     }
-    const General r = convert_general(p.off0, (long long)p.vbytes, v, prev, next, c, edge, st, base, x0, rtot, err_pos);
+    const General r =
+        convert_general(p.off0, (long long)p.vbytes, v, prev, next, c, edge, st, base, x0, rtot, err_pos, STAGE);
     err_pos = r.err_pos;
     return r.g;
   }
@@ -260,11 +261,20 @@ struct Utf8ToUtf16 {
 
   // Any region (one at a buffer end, or one whose output would overflow the staging buffer,
   // which only happens after an error): per-byte word counts with the buffer's bounds, and
-  // a bounds test before every store.  Kept out of line so that the hot loop does not carry
-  // its registers.
+  // a bounds test before every store.  `stage` is the staging buffer's size in words.  Kept
+  // out of line so that the hot loop does not carry its registers.
   __device__ __noinline__ static General convert_general(long long lo, long long hi, uint4 v, uint32_t prev, uint32_t next,
                                                           long long c, bool edge, uint16_t *st, uint32_t base,
-                                                          uint32_t x0, uint32_t rtot, unsigned long long err_pos) {
+                                                          uint32_t x0, uint32_t rtot, unsigned long long err_pos,
+                                                          uint32_t stage) {
+    return convert_general_body(lo, hi, v, prev, next, c, edge, st, base, x0, rtot, err_pos, stage);
+  }
+
+  // The body of convert_general, for callers that inline it.
+  __device__ __forceinline__ static General convert_general_body(long long lo, long long hi, uint4 v, uint32_t prev,
+                                                                 uint32_t next, long long c, bool edge, uint16_t *st,
+                                                                 uint32_t base, uint32_t x0, uint32_t rtot,
+                                                                 unsigned long long err_pos, uint32_t stage) {
     uint32_t W[6];
     W[0] = prev;
     W[1] = v.x; W[2] = v.y; W[3] = v.z; W[4] = v.w;
@@ -287,7 +297,7 @@ struct Utf8ToUtf16 {
     x0 += base;
     // a chunk that would overflow the staging buffer lies after the first error: it stores
     // nothing (its validation still runs)
-    const bool store = x0 + cnt <= STAGE;
+    const bool store = x0 + cnt <= stage;
     {
       uint32_t c2 = 0, c3 = 0, c4 = 0;
 #pragma unroll
@@ -348,7 +358,7 @@ struct Utf8ToUtf16 {
       err |= bad;
     }
     if (err && (unsigned long long)c < err_pos) err_pos = (unsigned long long)c;
-    if (g.total > STAGE - base) g.total = STAGE - base;  // only after the first error
+    if (g.total > stage - base) g.total = stage - base;  // only after the first error
     return General{g, err_pos};
   }
 };

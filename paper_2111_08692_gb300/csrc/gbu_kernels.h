@@ -34,9 +34,11 @@ const void *utf32_to_utf16_kernel_ptr();
 size_t utf32_to_utf16_smem_bytes();
 const void *utf16_to_utf32_kernel_ptr();
 size_t utf16_to_utf32_smem_bytes();
-// the same transcoders over several strings per launch (SegParams; same shared memory)
+// the same transcoders over several strings per launch (SegParams)
 const void *utf8_to_utf16_segments_kernel_ptr();
 const void *utf16_to_utf8_segments_kernel_ptr();
+size_t utf8_to_utf16_segments_smem_bytes();
+size_t utf16_to_utf8_segments_smem_bytes();
 
 // batched kernels (mode: BatchMode; nwarps: 4, 8 or 16 warps per CTA) and the u64 scan
 const void *batch_kernel_ptr(int mode, int nwarps);

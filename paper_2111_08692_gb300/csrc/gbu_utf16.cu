@@ -1,16 +1,18 @@
-// gbu_utf16.cu -- the single-buffer UTF-16LE -> UTF-8 transcoder (validating): the partition
-// loop of gbu_xcode.cuh with the codec of gbu_codec_utf16.cuh.
+// gbu_utf16.cu -- the UTF-16LE -> UTF-8 transcoders (validating): the single-buffer kernel (the
+// wide partition loop of gbu_wide.cuh with the codec of gbu_wide_utf16.cuh) and the kernel over
+// several strings (the partition loop of gbu_xcode.cuh with the codec of gbu_codec_utf16.cuh).
 #include <stdint.h>
 
 #include "gbu_codec_utf16.cuh"
 #include "gbu_kernels.h"
+#include "gbu_wide_utf16.cuh"
 
 namespace gbu {
 
 __global__ void __launch_bounds__(XT, XBLOCKS) utf16_to_utf8_kernel(const Params p) {
-  extern __shared__ __align__(128) unsigned char smem_raw[];  // sizeof(XSmem), set at launch
-  XSmem<Utf16ToUtf8> &sm = *reinterpret_cast<XSmem<Utf16ToUtf8> *>(smem_raw);
-  transcode<Utf16ToUtf8>(p, sm, [&](uint32_t status, unsigned long long key, unsigned long long tot) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];  // sizeof(WSmem), set at launch
+  WSmem<Utf16ToUtf8Wide> &sm = *reinterpret_cast<WSmem<Utf16ToUtf8Wide> *>(smem_raw);
+  wtranscode<Utf16ToUtf8Wide>(p, sm, [&](uint32_t status, unsigned long long key, unsigned long long tot) {
     if (status) {
       write_result(p.result, GBU_TIMEOUT, 0);
     } else if (key != NO_ERROR) {
@@ -46,7 +48,8 @@ __global__ void __launch_bounds__(XT, XBLOCKS) utf16_to_utf8_segments_kernel(con
 }
 
 const void *utf16_to_utf8_kernel_ptr() { return (const void *)utf16_to_utf8_kernel; }
-size_t utf16_to_utf8_smem_bytes() { return sizeof(XSmem<Utf16ToUtf8>); }
+size_t utf16_to_utf8_smem_bytes() { return sizeof(WSmem<Utf16ToUtf8Wide>); }
+size_t utf16_to_utf8_segments_smem_bytes() { return sizeof(XSmem<Utf16ToUtf8>); }
 
 const void *utf16_to_utf8_segments_kernel_ptr() { return (const void *)utf16_to_utf8_segments_kernel; }
 

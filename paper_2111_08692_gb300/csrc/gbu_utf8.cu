@@ -1,16 +1,18 @@
-// gbu_utf8.cu -- the single-buffer UTF-8 -> UTF-16LE transcoder (validating): the partition
-// loop of gbu_xcode.cuh with the codec of gbu_codec_utf8.cuh.
+// gbu_utf8.cu -- the UTF-8 -> UTF-16LE transcoders (validating): the single-buffer kernel (the
+// wide partition loop of gbu_wide.cuh with the codec of gbu_wide_utf8.cuh) and the kernel over
+// several strings (the partition loop of gbu_xcode.cuh with the codec of gbu_codec_utf8.cuh).
 #include <stdint.h>
 
 #include "gbu_codec_utf8.cuh"
 #include "gbu_kernels.h"
+#include "gbu_wide_utf8.cuh"
 
 namespace gbu {
 
 __global__ void __launch_bounds__(XT, XBLOCKS) utf8_to_utf16_kernel(const Params p) {
-  extern __shared__ __align__(128) unsigned char smem_raw[];  // sizeof(XSmem), set at launch
-  XSmem<Utf8ToUtf16> &sm = *reinterpret_cast<XSmem<Utf8ToUtf16> *>(smem_raw);
-  transcode<Utf8ToUtf16>(p, sm, [&](uint32_t status, unsigned long long key, unsigned long long tot) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];  // sizeof(WSmem), set at launch
+  WSmem<Utf8ToUtf16Wide> &sm = *reinterpret_cast<WSmem<Utf8ToUtf16Wide> *>(smem_raw);
+  wtranscode<Utf8ToUtf16Wide>(p, sm, [&](uint32_t status, unsigned long long key, unsigned long long tot) {
     if (status) {
       write_result(p.result, GBU_TIMEOUT, 0);
     } else if (key != NO_ERROR) {
@@ -46,7 +48,8 @@ __global__ void __launch_bounds__(XT, XBLOCKS) utf8_to_utf16_segments_kernel(con
 }
 
 const void *utf8_to_utf16_kernel_ptr() { return (const void *)utf8_to_utf16_kernel; }
-size_t utf8_to_utf16_smem_bytes() { return sizeof(XSmem<Utf8ToUtf16>); }
+size_t utf8_to_utf16_smem_bytes() { return sizeof(WSmem<Utf8ToUtf16Wide>); }
+size_t utf8_to_utf16_segments_smem_bytes() { return sizeof(XSmem<Utf8ToUtf16>); }
 
 const void *utf8_to_utf16_segments_kernel_ptr() { return (const void *)utf8_to_utf16_segments_kernel; }
 

@@ -1,0 +1,228 @@
+// gbu_wide_utf16.cuh -- the UTF-16LE -> UTF-8 codec (validating) of the wide partition loop
+// (gbu_wide.cuh): a lane validates and converts 16 consecutive words (32 bytes).
+//
+// Paper Section 3: words 0000-D7FF and E000-FFFF are characters by themselves; a word in
+// D800-DBFF must be followed by one in DC00-DFFF and the pair encodes
+// ((first & 0x3FF) << 10 | (second & 0x3FF)) + 0x10000.  The UTF-8 sizes are 1 byte below
+// 0x80, 2 below 0x800, 3 otherwise, and 2 per surrogate word (a pair's first word writes all 4
+// bytes, over its own 2 slots and its partner's).  Section 4 routes whole registers by range;
+// here the routes are taken per warp region from the count pass's flags: all ASCII (words
+// narrowed to bytes), one and two bytes, no surrogates, ASCII and pairs only (emoji-heavy
+// text), and the general pair route.  Words are encoded one at a time into the warp's staging
+// buffer through 32-bit shared-memory addresses.
+#pragma once
+
+#include <stdint.h>
+
+#include "gbu_codec_utf16.cuh"
+#include "gbu_wide.cuh"
+
+namespace gbu {
+
+struct Utf16ToUtf8Wide {
+  using Out = uint8_t;
+  using Narrow = Utf16ToUtf8;
+  // a region of 512 words yields at most 1536 bytes, +2 for a pair cut at its end, plus 15
+  // bytes of alignment offset
+  static constexpr uint32_t WSTAGE = 3 * 512 + 32;
+  static_assert(3 * 512 + 2 + 15 + 1 <= WSTAGE, "staging buffer too small");
+
+  static constexpr uint32_t F_SUR = Narrow::F_SUR;
+  static constexpr uint32_t F_THREE = Narrow::F_THREE;
+  static constexpr uint32_t F_WIDE = Narrow::F_WIDE;
+
+  static constexpr uint32_t ASCII_MASK = 0xFF80FF80u;  // nonzero in a word: a word >= 0x80
+  static constexpr uint32_t LANE_UNITS = 16;            // bytes out of 16 ASCII words
+  static constexpr uint32_t WREGION_UNITS = 512;        // bytes out of an all-ASCII region
+  static constexpr uint32_t WDIRECT_ALIGN = 16;         // its lanes store 16 bytes each
+
+  // 512 words and 512 bytes: every word of an inside region is ASCII.
+  __device__ __forceinline__ static bool wascii_region(uint32_t rtot, uint32_t) { return rtot == 512u; }
+
+  // The low bytes of the lane's 16 words (all ASCII).
+  __device__ __forceinline__ static uint4 narrow16(const uint32_t W[8]) {
+    return make_uint4(__byte_perm(W[0], W[1], 0x6420), __byte_perm(W[2], W[3], 0x6420),
+                      __byte_perm(W[4], W[5], 0x6420), __byte_perm(W[6], W[7], 0x6420));
+  }
+
+  // An all-ASCII region inside the buffer whose output starts at dst, 16-byte aligned: each
+  // lane narrows its 16 words into one 16-byte store (Section 4's ASCII route).
+  __device__ __forceinline__ static void wascii_direct(uint8_t *dst, const uint32_t W[8], uint32_t, long long,
+                                                       unsigned long long &) {
+    const int lane = threadIdx.x & 31;
+    reinterpret_cast<uint4 *>(dst)[lane] = narrow16(W);
+  }
+
+  // UTF-8 bytes of the lane's 16 words and the route flags.  Inside the buffer the high bytes
+  // of four words are gathered into one register (and their low bytes into another) and
+  // tested four at a time: >= 0x80 (a nonzero high byte, or bit 7 of the low byte), >= 0x800
+  // (high byte >= 08) and surrogate (high byte D8-DF); the flags, in bit 7 of each byte, are
+  // summed by byte dot products.
+  __device__ __forceinline__ static uint32_t wcount(const Params &p, const uint32_t W[8], long long c, bool edge,
+                                                    uint32_t &flags) {
+    if (!edge) {
+      uint32_t any = 0;
+#pragma unroll
+      for (int k = 0; k < 8; ++k) any |= W[k];
+      flags = 0;
+      if ((any & ASCII_MASK) == 0) return 16;  // all ASCII
+      uint32_t a80 = 0, a800 = 0, sub = 0;
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const uint32_t hb = __byte_perm(W[2 * i], W[2 * i + 1], 0x7531);
+        const uint32_t lb = __byte_perm(W[2 * i], W[2 * i + 1], 0x6420);
+        const uint32_t g80 = (((hb & 0x7F7F7F7Fu) + 0x7F7F7F7Fu) | hb | lb) & 0x80808080u;
+        const uint32_t g800 = (((hb & 0x78787878u) + 0x78787878u) | hb) & 0x80808080u;
+        const uint32_t t = (hb & 0xF8F8F8F8u) ^ 0xD8D8D8D8u;
+        const uint32_t sr = ~(((t & 0x7F7F7F7Fu) + 0x7F7F7F7Fu) | t) & 0x80808080u;
+        a80 = __dp4a(g80, 0x01010101u, a80);
+        a800 = __dp4a(g800, 0x01010101u, a800);
+        sub = __dp4a(sr, 0x01010101u, sub);
+      }
+      // every surrogate is >= 0x800: a80 - sub counts the words >= 0x80 that are not surrogates
+      flags = (sub ? F_SUR : 0u) | (a800 ? F_THREE : 0u) | (a80 != sub ? F_WIDE : 0u);
+      return 16u + ((a80 + a800 - sub) >> 7);
+    }
+    flags = F_SUR | F_THREE | F_WIDE;
+    uint32_t cnt = 0;
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+      const uint32_t w = (W[j >> 1] >> (16 * (j & 1))) & 0xFFFFu;
+      const bool valid = c + 2 * j >= (long long)p.off0 && c + 2 * j < (long long)p.vbytes;
+      cnt += valid ? len8_of_word(w) : 0u;
+    }
+    return cnt;
+  }
+
+  // Word j (0..15) of the lane.
+  __device__ __forceinline__ static uint32_t word(const uint32_t W[8], int j) {
+    return (j & 1) ? W[j >> 1] >> 16 : W[j >> 1] & 0xFFFFu;
+  }
+
+  // The UTF-8 form of one word that is not part of a surrogate pair at shared address a: one,
+  // two or three bytes (a lone surrogate takes the three-byte form; what it writes lies past
+  // the first error).
+  __device__ __forceinline__ static void sts_bmp(uint32_t a, uint32_t w, bool g1, bool g2) {
+    const uint32_t c6 = w & 0x3Fu, t6 = w >> 6;
+    sts_u8(a, g2 ? 0xE0u + (w >> 12) : (g1 ? 0xC0u + t6 : w));
+    if (g1) sts_u8(a + 1, g2 ? (0x80u | (t6 & 0x3Fu)) : 0x80u + c6);
+    if (g2) sts_u8(a + 2, 0x80u + c6);
+  }
+
+  // The four bytes of the pair (w, wn) at shared address a.
+  __device__ __forceinline__ static void sts_pair(uint32_t a, uint32_t w, uint32_t wn) {
+    const uint32_t t = (w & 0x3FFu) + 0x40u;  // the code point >> 10
+    sts_u8(a, 0xF0u | (t >> 8));
+    sts_u8(a + 1, 0x80u | ((t >> 2) & 0x3Fu));
+    sts_u8(a + 2, 0x80u | ((t & 3u) << 4) | ((wn >> 6) & 0xFu));
+    sts_u8(a + 3, 0x80u | (wn & 0x3Fu));
+  }
+
+  __device__ __forceinline__ static Region wconvert(const Params &p, const uint32_t W[8], uint32_t prev,
+                                                    uint32_t next, long long c, bool edge, bool inside, uint8_t *st,
+                                                    uint32_t base, uint32_t x0, uint32_t rtot, uint32_t rflags,
+                                                    unsigned long long &err_pos) {
+    const int lane = threadIdx.x & 31;
+    const uint32_t sbase = smem_addr(st);
+    if (!inside) {
+      // a region at a buffer end: the 16-byte generic path of the narrow codec on each half
+      // (a pair cut by the region's start is judged by lane 0's first half, one cut by its end
+      // by lane 31's second half)
+      const uint4 A = make_uint4(W[0], W[1], W[2], W[3]), B = make_uint4(W[4], W[5], W[6], W[7]);
+      uint32_t fa;
+      const uint32_t na = Narrow::count(p, A, c, edge, fa);
+      const Region ga = Narrow::convert_generic(p, A, prev, W[4], c, edge, st, base, x0, rtot, err_pos);
+      const Region gb = Narrow::convert_generic(p, B, W[3], next, c + 16, edge, st, base, x0 + na, rtot, err_pos);
+      return Region{rtot, ga.skip, gb.extra, rtot};
+    }
+    if (rtot == 512u) {
+      // 512 words and 512 bytes: every word is ASCII (Section 4's ASCII route)
+      const uint4 b = narrow16(W);
+      const uint32_t x = base + 16 * lane;
+      const uint32_t a = sbase + x;
+      if ((x & 15) == 0) {
+        sts_v4(a, b.x, b.y, b.z, b.w);
+      } else if ((x & 3) == 0) {
+        sts_u32(a, b.x);
+        sts_u32(a + 4, b.y);
+        sts_u32(a + 8, b.z);
+        sts_u32(a + 12, b.w);
+      } else {
+        const uint32_t q[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+        for (int i = 0; i < 16; ++i) sts_u8(a + i, q[i >> 2] >> (8 * (i & 3)));
+      }
+      return Region{512u, 0u, 0u, 512u};
+    }
+    Region g{rtot, 0u, 0u, rtot};
+    uint32_t o = sbase + base + x0;
+    if (!(rflags & (F_SUR | F_THREE))) {
+      // only words below 0x800 (Section 4's one-and-two-byte route)
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        const uint32_t w = word(W, j);
+        const bool g1 = w >= 0x80u;
+        sts_u8(o, g1 ? 0xC0u + (w >> 6) : w);
+        if (g1) sts_u8(o + 1, 0x80u | (w & 0x3Fu));
+        o += g1 ? 2u : 1u;
+      }
+      return g;
+    }
+    if (!(rflags & F_SUR)) {
+      // no surrogate in the region: every word is a character of one to three bytes
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        const uint32_t w = word(W, j);
+        const bool g1 = w >= 0x80u, g2 = w >= 0x800u;
+        sts_bmp(o, w, g1, g2);
+        o += 1u + (g1 ? 1u : 0u) + (g2 ? 1u : 0u);
+      }
+      return g;
+    }
+    // Surrogates present.  A first surrogate followed by a second one writes all four bytes
+    // of the pair (its two slots and its partner's); the second writes nothing.  A pair cut
+    // by the region's end is written by this region (2 bytes past its end), a pair cut by
+    // its start by the previous region.
+    const uint32_t u0 = prev >> 16, u17 = next & 0xFFFFu;
+    const bool cut_start = is_low16(word(W, 0)) && is_high16(u0);
+    const bool cut_end = is_high16(word(W, 15)) && is_low16(u17);
+    g.skip = __shfl_sync(0xffffffffu, cut_start ? 2u : 0u, 0);
+    g.extra = __shfl_sync(0xffffffffu, cut_end ? 2u : 0u, 31);
+    if (!(rflags & F_WIDE)) {
+      // only ASCII words and surrogates (emoji-heavy text): an ASCII word writes its byte and
+      // every other word two slots' worth, all four bytes of a pair coming from its first
+      // word; the pair rules are checked on whole words
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        const uint32_t w = word(W, j), wn = j < 15 ? word(W, j + 1) : u17;
+        const bool sur = (w & 0xF800u) == 0xD800u;
+        if (!sur) sts_u8(o, w);
+        if (is_high16(w) && is_low16(wn)) sts_pair(o, w, wn);
+        o += sur ? 2u : 1u;
+      }
+      const uint32_t A[4] = {W[0], W[1], W[2], W[3]}, B[4] = {W[4], W[5], W[6], W[7]};
+      if ((utf16_pair_errors_inside(A, prev, W[4]) || utf16_pair_errors_inside(B, W[3], next)) &&
+          (unsigned long long)c < err_pos)
+        err_pos = (unsigned long long)c;
+      return g;
+    }
+    bool err = false;
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+      const uint32_t w = word(W, j);
+      const uint32_t wp = j > 0 ? word(W, j - 1) : u0, wn = j < 15 ? word(W, j + 1) : u17;
+      const bool g1 = w >= 0x80u, g2 = w >= 0x800u;
+      const bool hs = is_high16(w), ls = is_low16(w);
+      const bool pair = hs && is_low16(wn);
+      const bool follows = ls && is_high16(wp);
+      err |= (hs && !pair) || (ls && !follows);
+      if (pair) sts_pair(o, w, wn);
+      else if (!follows) sts_bmp(o, w, g1, g2);
+      o += (hs || ls) ? 2u : 1u + (g1 ? 1u : 0u) + (g2 ? 1u : 0u);
+    }
+    if (err && (unsigned long long)c < err_pos) err_pos = (unsigned long long)c;
+    return g;
+  }
+};
+
+}  // namespace gbu
