@@ -362,5 +362,36 @@ __device__ __forceinline__ void sts_u32(uint32_t a, uint32_t v) {
 __device__ __forceinline__ void sts_v4(uint32_t a, uint32_t x, uint32_t y, uint32_t z, uint32_t w) {
   asm volatile("st.shared.v4.u32 [%0], {%1, %2, %3, %4};" ::"r"(a), "r"(x), "r"(y), "r"(z), "r"(w) : "memory");
 }
-
+// Stores issued only where a flag bit is clear (or set), with the staging address advanced in
+// the same predicate: one PTX block per position, so that ptxas emits a logic op that sets the
+// predicate, the predicated store and the predicated add, and nothing else (an `if` around an
+// asm statement would become a branch, and a condition passed in as a value would be tested
+// again).  `sa` advances by `step` bytes where the store happens.
+template <int STEP>
+__device__ __forceinline__ void sts_u16_if_clear(uint32_t &sa, uint32_t v, uint32_t flags, uint32_t bit) {
+  asm volatile(
+      "{\n\t.reg .pred q;\n\t.reg .b32 t;\n\tand.b32 t, %2, %3;\n\tsetp.eq.b32 q, t, 0;\n\t"
+      "@q st.shared.u16 [%0], %1;\n\t@q add.u32 %0, %0, %4;\n\t}"
+      : "+r"(sa)
+      : "h"((unsigned short)v), "r"(flags), "r"(bit), "n"(STEP)
+      : "memory");
+}
+template <int STEP>
+__device__ __forceinline__ void sts_u16_if_set(uint32_t &sa, uint32_t v, uint32_t flags, uint32_t bit) {
+  asm volatile(
+      "{\n\t.reg .pred q;\n\t.reg .b32 t;\n\tand.b32 t, %2, %3;\n\tsetp.ne.b32 q, t, 0;\n\t"
+      "@q st.shared.u16 [%0], %1;\n\t@q add.u32 %0, %0, %4;\n\t}"
+      : "+r"(sa)
+      : "h"((unsigned short)v), "r"(flags), "r"(bit), "n"(STEP)
+      : "memory");
+}
+// A byte at a + OFF where (flags & bit) != 0 (the address is not advanced).
+template <int OFF>
+__device__ __forceinline__ void sts_u8_if_set(uint32_t a, uint32_t v, uint32_t flags, uint32_t bit) {
+  asm volatile(
+      "{\n\t.reg .pred q;\n\t.reg .b32 t;\n\tand.b32 t, %2, %3;\n\tsetp.ne.b32 q, t, 0;\n\t"
+      "@q st.shared.u8 [%0+%4], %1;\n\t}" ::"r"(a),
+      "h"((unsigned short)v), "r"(flags), "r"(bit), "n"(OFF)
+      : "memory");
+}
 }  // namespace gbu

@@ -99,23 +99,53 @@ struct Utf16ToUtf8Wide {
     return (j & 1) ? W[j >> 1] >> 16 : W[j >> 1] & 0xFFFFu;
   }
 
-  // The UTF-8 form of one word that is not part of a surrogate pair at shared address a: one,
-  // two or three bytes (a lone surrogate takes the three-byte form; what it writes lies past
-  // the first error).
-  __device__ __forceinline__ static void sts_bmp(uint32_t a, uint32_t w, bool g1, bool g2) {
-    const uint32_t c6 = w & 0x3Fu, t6 = w >> 6;
-    sts_u8(a, g2 ? 0xE0u + (w >> 12) : (g1 ? 0xC0u + t6 : w));
-    if (g1) sts_u8(a + 1, g2 ? (0x80u | (t6 & 0x3Fu)) : 0x80u + c6);
-    if (g2) sts_u8(a + 2, 0x80u + c6);
+  // Staging stores, each a single PTX block whose predicates come from mask tests of the word
+  // (one logic op each), so that ptxas emits predicated stores and adds and no branch.
+
+  // A word below 0x800 at shared address o: b0, then b1 where the word is >= 0x80 (a nonzero
+  // w & FF80); o advances by the bytes written.
+  __device__ __forceinline__ static void sts_12(uint32_t &o, uint32_t w, uint32_t b0, uint32_t b1) {
+    asm volatile(
+        "{\n\t.reg .pred q;\n\t.reg .b32 t;\n\tand.b32 t, %1, 0xFF80;\n\tsetp.ne.b32 q, t, 0;\n\t"
+        "st.shared.u8 [%0], %2;\n\t@q st.shared.u8 [%0+1], %3;\n\tadd.u32 %0, %0, 1;\n\t@q add.u32 %0, %0, 1;\n\t}"
+        : "+r"(o)
+        : "r"(w), "h"((unsigned short)b0), "h"((unsigned short)b1)
+        : "memory");
   }
 
-  // The four bytes of the pair (w, wn) at shared address a.
-  __device__ __forceinline__ static void sts_pair(uint32_t a, uint32_t w, uint32_t wn) {
-    const uint32_t t = (w & 0x3FFu) + 0x40u;  // the code point >> 10
-    sts_u8(a, 0xF0u | (t >> 8));
-    sts_u8(a + 1, 0x80u | ((t >> 2) & 0x3Fu));
-    sts_u8(a + 2, 0x80u | ((t & 3u) << 4) | ((wn >> 6) & 0xFu));
-    sts_u8(a + 3, 0x80u | (wn & 0x3Fu));
+  // A word that is not a surrogate: b0, then b1 where it is >= 0x80 and b2 where it is >= 0x800.
+  __device__ __forceinline__ static void sts_123(uint32_t &o, uint32_t w, uint32_t b0, uint32_t b1, uint32_t b2) {
+    asm volatile(
+        "{\n\t.reg .pred q1, q2;\n\t.reg .b32 t1, t2;\n\tand.b32 t1, %1, 0xFF80;\n\tsetp.ne.b32 q1, t1, 0;\n\t"
+        "and.b32 t2, %1, 0xF800;\n\tsetp.ne.b32 q2, t2, 0;\n\t"
+        "st.shared.u8 [%0], %2;\n\t@q1 st.shared.u8 [%0+1], %3;\n\t@q2 st.shared.u8 [%0+2], %4;\n\t"
+        "add.u32 %0, %0, 1;\n\t@q1 add.u32 %0, %0, 1;\n\t@q2 add.u32 %0, %0, 1;\n\t}"
+        : "+r"(o)
+        : "r"(w), "h"((unsigned short)b0), "h"((unsigned short)b1), "h"((unsigned short)b2)
+        : "memory");
+  }
+
+  // One word of a register: its first byte b0 at o, and b1 at o+1 where (S & BIT) != 0; o
+  // advances by the bytes written.
+  template <uint32_t BIT>
+  __device__ __forceinline__ static void sts_1or2(uint32_t &o, uint32_t S, uint32_t b0, uint32_t b1) {
+    asm volatile(
+        "{\n\t.reg .pred q;\n\t.reg .b32 t;\n\tand.b32 t, %1, %4;\n\tsetp.ne.b32 q, t, 0;\n\t"
+        "st.shared.u8 [%0], %2;\n\t@q st.shared.u8 [%0+1], %3;\n\tadd.u32 %0, %0, 1;\n\t@q add.u32 %0, %0, 1;\n\t}"
+        : "+r"(o)
+        : "r"(S), "r"(b0), "r"(b1), "n"(BIT)
+        : "memory");
+  }
+
+  // The UTF-8 form of one word that is not part of a surrogate pair: b0..b2 of its one-, two-
+  // or three-byte form (a lone surrogate takes the three-byte form; what it writes lies past the
+  // first error).
+  __device__ __forceinline__ static void bmp_bytes(uint32_t w, uint32_t &b0, uint32_t &b1, uint32_t &b2) {
+    const uint32_t c6 = w & 0x3Fu, t6 = w >> 6;
+    const bool g1 = w >= 0x80u, g2 = w >= 0x800u;
+    b0 = g2 ? 0xE0u + (w >> 12) : (g1 ? 0xC0u + t6 : w);
+    b1 = g2 ? (0x80u | (t6 & 0x3Fu)) : 0x80u + c6;
+    b2 = 0x80u + c6;
   }
 
   __device__ __forceinline__ static Region wconvert(const Params &p, const uint32_t W[8], uint32_t prev,
@@ -161,10 +191,7 @@ struct Utf16ToUtf8Wide {
 #pragma unroll
       for (int j = 0; j < 16; ++j) {
         const uint32_t w = word(W, j);
-        const bool g1 = w >= 0x80u;
-        sts_u8(o, g1 ? 0xC0u + (w >> 6) : w);
-        if (g1) sts_u8(o + 1, 0x80u | (w & 0x3Fu));
-        o += g1 ? 2u : 1u;
+        sts_12(o, w, w >= 0x80u ? 0xC0u + (w >> 6) : w, 0x80u | (w & 0x3Fu));
       }
       return g;
     }
@@ -173,9 +200,9 @@ struct Utf16ToUtf8Wide {
 #pragma unroll
       for (int j = 0; j < 16; ++j) {
         const uint32_t w = word(W, j);
-        const bool g1 = w >= 0x80u, g2 = w >= 0x800u;
-        sts_bmp(o, w, g1, g2);
-        o += 1u + (g1 ? 1u : 0u) + (g2 ? 1u : 0u);
+        uint32_t b0, b1, b2;
+        bmp_bytes(w, b0, b1, b2);
+        sts_123(o, w, b0, b1, b2);
       }
       return g;
     }
@@ -189,21 +216,63 @@ struct Utf16ToUtf8Wide {
     g.skip = __shfl_sync(0xffffffffu, cut_start ? 2u : 0u, 0);
     g.extra = __shfl_sync(0xffffffffu, cut_end ? 2u : 0u, 31);
     if (!(rflags & F_WIDE)) {
-      // only ASCII words and surrogates (emoji-heavy text): an ASCII word writes its byte and
-      // every other word two slots' worth, all four bytes of a pair coming from its first
-      // word; the pair rules are checked on whole words
-#pragma unroll
-      for (int j = 0; j < 16; ++j) {
-        const uint32_t w = word(W, j), wn = j < 15 ? word(W, j + 1) : u17;
-        const bool sur = (w & 0xF800u) == 0xD800u;
-        if (!sur) sts_u8(o, w);
-        if (is_high16(w) && is_low16(wn)) sts_pair(o, w, wn);
-        o += sur ? 2u : 1u;
+      // Only ASCII words and surrogates (emoji-heavy text), two words per register at a time.
+      // An ASCII word writes its byte.  Each surrogate writes the two bytes of its own two
+      // slots: a first surrogate (code point bits 20-12) F0 | t >> 8 and 80 | (t >> 2) & 3F with
+      // t = (w & 3FF) + 40, a second one (bits 11-0) 80 | (w' & 3) << 4 | (w >> 6) & F and
+      // 80 | w & 3F, w' the word before it.  For a valid pair that is its four bytes; an
+      // unpaired surrogate is an error, and what it writes lies past the first error.
+      uint32_t hprev = lanes16_sur(prev) & ~(prev << 5);  // the word before: a first surrogate (bit 31)
+      uint32_t wprev = prev;
+      uint32_t err = 0;
+      uint32_t Lc = 0, Hc = 0;  // the current register's second- and first-surrogate flags
+      {
+        const uint32_t S = lanes16_sur(W[0]);
+        Hc = S & ~(W[0] << 5);
+        Lc = S & (W[0] << 5);
       }
-      const uint32_t A[4] = {W[0], W[1], W[2], W[3]}, B[4] = {W[4], W[5], W[6], W[7]};
-      if ((utf16_pair_errors_inside(A, prev, W[4]) || utf16_pair_errors_inside(B, W[3], next)) &&
-          (unsigned long long)c < err_pos)
-        err_pos = (unsigned long long)c;
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        const uint32_t X = W[k];
+        // flags of the next register (for lane 31, the word after the region)
+        uint32_t Hn, Ln;
+        {
+          const uint32_t Y = k < 7 ? W[k + 1] : (next & 0xFFFFu);
+          const uint32_t S = lanes16_sur(Y);
+          Hn = S & ~(Y << 5);
+          Ln = S & (Y << 5);
+        }
+        // pair rules: a first surrogate must be followed by a second one, a second one preceded
+        // by a first one (flags in bit 15 of each 16-bit lane)
+        const uint32_t low_after = __funnelshift_r(Lc, Ln, 16);
+        const uint32_t high_before = __funnelshift_l(hprev, Hc, 16);
+        err |= (Hc & ~low_after) | (Lc & ~high_before);
+        // both slot pairs of both words, as 16-bit lanes (low byte first)
+        const uint32_t T = (X & 0x03FF03FFu) + 0x00400040u;
+        const uint32_t hb0 = ((T >> 8) & 0x00070007u) | 0x00F000F0u;
+        const uint32_t hb1 = ((T >> 2) & 0x003F003Fu) | 0x00800080u;
+        const uint32_t HI = hb1 * 256u + hb0;
+        const uint32_t Xp = __funnelshift_l(wprev, X, 16);  // each lane's word before
+        const uint32_t lb2 = (Xp & 0x00030003u) * 16u + (((X >> 6) & 0x000F000Fu) | 0x00800080u);
+        const uint32_t lb3 = (X & 0x003F003Fu) | 0x00800080u;
+        const uint32_t LO = lb3 * 256u + lb2;
+        const uint32_t Hm = prmt(Hc, 0u, 0xBB99u), Lm = prmt(Lc, 0u, 0xBB99u);
+        const uint32_t R = (HI & Hm) | (LO & Lm) | (X & ~(Hm | Lm));
+        const uint32_t Sc = Hc | Lc;
+        sts_1or2<0x8000u>(o, Sc, R, R >> 8);
+        sts_1or2<0x80000000u>(o, Sc, R >> 16, R >> 24);
+        hprev = Hc;
+        wprev = X;
+        Hc = Hn;
+        Lc = Ln;
+      }
+      // a pair cut by the region's end: lane 31 also writes its second half (2 bytes past the
+      // region's end, as in the other routes)
+      if (lane == 31 && is_high16(word(W, 15)) && is_low16(u17)) {
+        sts_u8(o, 0x80u | ((word(W, 15) & 3u) << 4) | ((u17 >> 6) & 0xFu));
+        sts_u8(o + 1, 0x80u | (u17 & 0x3Fu));
+      }
+      if (err && (unsigned long long)c < err_pos) err_pos = (unsigned long long)c;
       return g;
     }
     bool err = false;
@@ -216,8 +285,21 @@ struct Utf16ToUtf8Wide {
       const bool pair = hs && is_low16(wn);
       const bool follows = ls && is_high16(wp);
       err |= (hs && !pair) || (ls && !follows);
-      if (pair) sts_pair(o, w, wn);
-      else if (!follows) sts_bmp(o, w, g1, g2);
+      // the word's bytes: a pair's four, nothing for a pair's second word, else its one to
+      // three (a lone surrogate takes the three-byte form)
+      const uint32_t c6 = w & 0x3Fu, t6 = w >> 6;
+      const uint32_t t = (w & 0x3FFu) + 0x40u;  // a pair's code point >> 10
+      const uint32_t b0 = pair ? 0xF0u | (t >> 8) : (g2 ? 0xE0u + (w >> 12) : (g1 ? 0xC0u + t6 : w));
+      const uint32_t b1 = pair ? 0x80u | ((t >> 2) & 0x3Fu) : (g2 ? 0x80u | (t6 & 0x3Fu) : 0x80u + c6);
+      const uint32_t b2 = pair ? 0x80u | ((t & 3u) << 4) | ((wn >> 6) & 0xFu) : 0x80u + c6;
+      const uint32_t nb = pair ? 4u : (follows ? 0u : 1u + (g1 ? 1u : 0u) + (g2 ? 1u : 0u));
+      // nb = 0..4 bytes: byte i is stored where nb > i, i.e. where bit i of m = 0xF >> (4 - nb)
+      // is set (tested by the fused stores)
+      const uint32_t m = 0xFu >> (4u - nb);
+      sts_u8_if_set<0>(o, b0, m, 1u);
+      sts_u8_if_set<1>(o, b1, m, 2u);
+      sts_u8_if_set<2>(o, b2, m, 4u);
+      sts_u8_if_set<3>(o, 0x80u | (wn & 0x3Fu), m, 8u);
       o += (hs || ls) ? 2u : 1u + (g1 ? 1u : 0u) + (g2 ? 1u : 0u);
     }
     if (err && (unsigned long long)c < err_pos) err_pos = (unsigned long long)c;

@@ -99,23 +99,25 @@ struct Utf8ToUtf16Wide {
       flags = 0;
       return 32;
     }
-    // per byte, as bit 7: not a continuation byte (10xxxxxx), and >= F0; a byte dot product
-    // with 0x01 weights adds 0x80 per flag
-    uint32_t acc = 0, c2 = 0, c3 = 0, c4 = 0;
+    // per byte, as bit 7: not a continuation byte (10xxxxxx), >= C0, >= E0 and >= F0.  Byte dot
+    // products with 0x01 weights (FMA pipe) add 0x80 per flag; the leading-byte classes follow
+    // from the sums (C0-DF present when there are more bytes >= C0 than >= E0, and so on), so
+    // the integer ALU does four logic operations per word
+    uint32_t an = 0, aG = 0, aE = 0, aF = 0;
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
-      const uint32_t w = W[k], s1 = w << 1, s2 = w << 2, s3 = w << 3;
+      const uint32_t w = W[k], s1 = w * 2u, s2 = w * 4u, s3 = w * 8u;
       const uint32_t vm = edge ? byte_range_mask(c + 4 * k, p.off0, (long long)p.vbytes) : 0x80808080u;
-      const uint32_t ge = w & s1 & vm;   // >= C0
-      const uint32_t f0 = ge & s2 & s3;  // >= F0
-      acc = __dp4a((~w | s1) & vm, 0x01010101u, acc);
-      acc = __dp4a(f0, 0x01010101u, acc);
-      c2 |= ge & ~s2;
-      c3 |= ge & s2 & ~s3;
-      c4 |= f0;
+      const uint32_t ge = w & s1 & vm;  // >= C0
+      const uint32_t gE = ge & s2;      // >= E0
+      const uint32_t f0 = gE & s3;      // >= F0
+      an = __dp4a((~w | s1) & vm, 0x01010101u, an);
+      aG = __dp4a(ge, 0x01010101u, aG);
+      aE = __dp4a(gE, 0x01010101u, aE);
+      aF = __dp4a(f0, 0x01010101u, aF);
     }
-    flags = F_NONASCII | (c2 ? F_C2 : 0u) | (c3 ? F_C3 : 0u) | (c4 ? F_C4 : 0u);
-    return acc >> 7;
+    flags = F_NONASCII | (aG > aE ? F_C2 : 0u) | (aE > aF ? F_C3 : 0u) | (aF ? F_C4 : 0u);
+    return (an + aF) >> 7;
   }
 
   // Validates the lane's 32 bytes W[1..8] (W[0] the word before, W[9] the word after) of a
@@ -208,14 +210,8 @@ struct Utf8ToUtf16Wide {
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
         const uint32_t bit = 0x80u << (8 * j);
-        if (!(isC & bit)) {
-          sts_u16(sa, plane_word(L, H, j));
-          sa += 2;
-          if (H4 && (gF & bit)) {
-            sts_u16(sa, plane_word(Lls, Hls, j));
-            sa += 2;
-          }
-        }
+        sts_u16_if_clear<2>(sa, plane_word(L, H, j), isC, bit);
+        if (H4) sts_u16_if_set<2>(sa, plane_word(Lls, Hls, j), gF, bit);
       }
     }
     return bad;
