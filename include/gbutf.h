@@ -122,6 +122,26 @@ int gbu_convert_utf8_to_utf16le(gbu_ctx *ctx, const uint8_t *src, uint64_t n, ui
 int gbu_convert_utf16le_to_utf8(gbu_ctx *ctx, const uint16_t *src, uint64_t n, uint8_t *dst,
                                 uint64_t cap, gbu_result *result, gbu_stream stream);
 
+/* Host-synchronising forms of the six calls above: the same operation on the same arguments
+ * (without `result`), run on `stream`, which the call then waits for; the result comes back by
+ * value.  This is the problem as the paper states it (Section 1; Section 5: transcoding includes
+ * validation): one call in, and out either the output length or the kind and offset of the
+ * first error.
+ *   validate / convert: the gbu_result the asynchronous call would have written;
+ *   lengths: {GBU_OK, length}.
+ * A launch failure returns {that status (GBU_BAD_ARGUMENT, GBU_CUDA_ERROR), 0}; a NULL ctx
+ * returns {GBU_BAD_ARGUMENT, 0}.  The result travels through a slot of the context's workspace
+ * (device memory) and one device-to-host copy, so calls on one context must not overlap, as
+ * for the asynchronous calls. */
+gbu_result gbu_validate_utf8_sync(gbu_ctx *ctx, const uint8_t *src, uint64_t n, gbu_stream stream);
+gbu_result gbu_validate_utf16le_sync(gbu_ctx *ctx, const uint16_t *src, uint64_t n, gbu_stream stream);
+gbu_result gbu_utf16_length_from_utf8_sync(gbu_ctx *ctx, const uint8_t *src, uint64_t n, gbu_stream stream);
+gbu_result gbu_utf8_length_from_utf16le_sync(gbu_ctx *ctx, const uint16_t *src, uint64_t n, gbu_stream stream);
+gbu_result gbu_convert_utf8_to_utf16le_sync(gbu_ctx *ctx, const uint8_t *src, uint64_t n, uint16_t *dst,
+                                            uint64_t cap, gbu_stream stream);
+gbu_result gbu_convert_utf16le_to_utf8_sync(gbu_ctx *ctx, const uint16_t *src, uint64_t n, uint8_t *dst,
+                                            uint64_t cap, gbu_stream stream);
+
 /* UTF-16BE: the same words as UTF-16LE (Section 3) with each word's most significant byte first
  * in memory (the byte order RFC 2781 names; no byte-order-mark sniffing).  src / dst are the
  * words as they lie in memory (2-byte aligned).  Results, units, capacities, error offsets and
@@ -211,6 +231,17 @@ typedef enum {
   GBU_OP_UTF8_LENGTH_FROM_UTF16LE = 4,
   GBU_OP_CONVERT_UTF16LE_TO_UTF8 = 5
 } gbu_op;
+
+/* The per-string alternative to a batched call, for measuring what batching saves: the same
+ * B strings (input offsets off[B+1] in input code units, and for the transcoders output
+ * offsets dst_off[B+1] in output code units, both in HOST memory) handled by B single-buffer
+ * calls of operation `op` issued one after another from a C loop on `stream`, string i's
+ * result into results[i] (device; lengths into ((uint64_t *)results)[i]).  src, dst and
+ * results are device memory, as for the batched call.  Returns the first launch error, or
+ * GBU_OK; B launches are made.  The paper has no counterpart: it transcodes one buffer at a
+ * time (Section 5), which this loop repeats per string. */
+int gbu_per_string_loop(gbu_ctx *ctx, int op, const void *src, const uint64_t *off, uint64_t B, void *dst,
+                        const uint64_t *dst_off, gbu_result *results, gbu_stream stream);
 
 /* Launch geometry of a batched operation.  A CTA of warps_per_cta warps claims
  * strings_per_claim consecutive strings at a time; each warp takes one string at a time,
@@ -350,10 +381,14 @@ void gbu_arena_destroy(gbu_arena *arena);
  *
  * The workspace is a static device array of the library (128 B + 8 B per 16 KiB partition),
  * sized for n <= GBU_NOALLOC_MAX_UNITS bytes; a larger n returns GBU_NOALLOC_TOO_LARGE and
- * enqueues nothing.  Runs on the CURRENT device.  The first call on each device does a
- * one-time setup there (looks up the array's device address, queries the occupancy, clears
- * the array with synchronous copies and a device synchronise), so make that first call before
- * any stream capture.  The library never allocates on any call.
+ * enqueues nothing.  Runs on the CURRENT device, with a context's default settings (early
+ * exit on), so its result and dst[0 : valid prefix] equal the context path's.  The first call
+ * on each device does a one-time setup there (looks up the array's device address, queries
+ * the occupancy, clears the array with synchronous copies and a device synchronise), so make
+ * that first call before any stream capture: if `stream` is being captured when the setup is
+ * still needed, the call returns GBU_CUDA_ERROR without touching the device, and a later call
+ * outside the capture runs the setup.  A setup that fails is tried again by the next call.
+ * The library never allocates on any call.
  *
  * There is ONE workspace per device, shared by every call: two calls whose kernels overlap
  * (different streams, or threads, without ordering between them) race on it and both give

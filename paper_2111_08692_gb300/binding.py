@@ -123,6 +123,15 @@ def lib() -> ctypes.CDLL:
                          "gbu_convert_utf16le_to_utf32"):
                 getattr(L, name).restype = i32
                 getattr(L, name).argtypes = [vp, vp, u64, vp, u64, vp, vp]
+            for name in ("gbu_validate_utf8_sync", "gbu_validate_utf16le_sync", "gbu_utf16_length_from_utf8_sync",
+                         "gbu_utf8_length_from_utf16le_sync"):
+                getattr(L, name).restype = GbuResult
+                getattr(L, name).argtypes = [vp, vp, u64, vp]
+            for name in ("gbu_convert_utf8_to_utf16le_sync", "gbu_convert_utf16le_to_utf8_sync"):
+                getattr(L, name).restype = GbuResult
+                getattr(L, name).argtypes = [vp, vp, u64, vp, u64, vp]
+            L.gbu_per_string_loop.restype = i32
+            L.gbu_per_string_loop.argtypes = [vp, i32, vp, vp, u64, vp, vp, vp, vp]
             L.gbu_chunked_create.restype = vp
             L.gbu_chunked_create.argtypes = [i32, i32, u64]
             L.gbu_chunked_push.restype = i32
@@ -458,6 +467,37 @@ class Codec:
                "gbu_convert_utf8_to_utf16le")
         return result
 
+    # host-synchronising forms: (status name, count) by value, the stream waited for
+    def _sync(self, fn, name, *args):
+        r = fn(self.ctx, *args)
+        return STATUS.get(r.status, r.status), int(r.count)
+
+    def validate_utf8_sync(self, src, stream=None):
+        return self._sync(lib().gbu_validate_utf8_sync, "gbu_validate_utf8_sync", self._ptr(src), src.numel(),
+                          self._stream(stream))
+
+    def validate_utf16le_sync(self, src, stream=None):
+        return self._sync(lib().gbu_validate_utf16le_sync, "gbu_validate_utf16le_sync", self._ptr(src), src.numel(),
+                          self._stream(stream))
+
+    def utf16_length_from_utf8_sync(self, src, stream=None):
+        return self._sync(lib().gbu_utf16_length_from_utf8_sync, "gbu_utf16_length_from_utf8_sync", self._ptr(src),
+                          src.numel(), self._stream(stream))
+
+    def utf8_length_from_utf16le_sync(self, src, stream=None):
+        return self._sync(lib().gbu_utf8_length_from_utf16le_sync, "gbu_utf8_length_from_utf16le_sync",
+                          self._ptr(src), src.numel(), self._stream(stream))
+
+    def convert_utf8_to_utf16le_sync(self, src, dst, stream=None, cap=None):
+        cap = dst.numel() if cap is None else cap
+        return self._sync(lib().gbu_convert_utf8_to_utf16le_sync, "gbu_convert_utf8_to_utf16le_sync", self._ptr(src),
+                          src.numel(), self._ptr(dst), cap, self._stream(stream))
+
+    def convert_utf16le_to_utf8_sync(self, src, dst, stream=None, cap=None):
+        cap = dst.numel() if cap is None else cap
+        return self._sync(lib().gbu_convert_utf16le_to_utf8_sync, "gbu_convert_utf16le_to_utf8_sync", self._ptr(src),
+                          src.numel(), self._ptr(dst), cap, self._stream(stream))
+
     # UTF-16BE forms: int16 tensors holding the words as they lie in memory (big-endian bytes)
     def validate_utf16be(self, src, result=None, stream=None):
         result = self.new_result() if result is None else result
@@ -662,11 +702,26 @@ def combine_shards(cuts, parts) -> tuple[str, int]:
 def convert_utf8_to_utf16le_noalloc(src, dst, result, stream=None, cap=None):
     """The context-free transcoder on the current device (no allocation: the caller passes
     ``dst`` and ``result``).  ``src`` holds at most NOALLOC_MAX_UNITS bytes; calls must not
-    overlap one another (they share one workspace per device)."""
+    overlap one another (they share one workspace per device).
+
+    The tensors are checked before the call, since the C function has no context device to
+    check them against and takes ``cap`` in 16-bit units: ``src`` must be uint8, ``dst`` have
+    2-byte elements, ``result`` hold at least 16 bytes, and all three lie on the current CUDA
+    device.  A tensor that fails a check raises GbuError and nothing is enqueued."""
     import torch
+    name = "gbu_convert_utf8_to_utf16le_noalloc"
     if src.numel() > NOALLOC_MAX_UNITS:
-        raise GbuError(f"gbu_convert_utf8_to_utf16le_noalloc: input of {src.numel()} bytes is above "
+        raise GbuError(f"{name}: input of {src.numel()} bytes is above "
                        f"the limit of {NOALLOC_MAX_UNITS} bytes of the allocation-free form")
+    if src.dtype != torch.uint8:
+        raise GbuError(f"{name}: src must be a uint8 tensor, not {src.dtype}")
+    if dst.element_size() != 2:
+        raise GbuError(f"{name}: dst must have 2-byte elements (UTF-16 units), not {dst.dtype}")
+    if result.numel() * result.element_size() < 16:
+        raise GbuError(f"{name}: result must hold at least 16 bytes (one gbu_result)")
+    for what, t in (("src", src), ("dst", dst), ("result", result)):
+        if not t.is_cuda or t.device.index != torch.cuda.current_device():
+            raise GbuError(f"{name}: {what} is not on the current CUDA device")
     if stream is None:
         stream = torch.cuda.current_stream()
     s = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)

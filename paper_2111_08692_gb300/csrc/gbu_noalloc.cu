@@ -8,15 +8,15 @@
 // uses a workspace that exists from module load: a file-scope __device__ array, sized for
 // inputs of up to GBU_NOALLOC_MAX_UNITS bytes.  Nothing is allocated, on any call.
 //
-// The kernel is the context path's utf8_to_utf16_kernel unchanged; only where its workspace
-// lives differs.  The kernel's last CTA leaves the workspace ready for the next launch
-// (ticket, done counter and first-error key reset, epoch advanced), so after the one-time
-// setup below the workspace needs no host-side work between calls.
+// The kernel is the context path's utf8_to_utf16_kernel with the context's default settings
+// (early exit on, the same wait limit); only where its workspace lives differs.  The kernel's
+// last CTA leaves the workspace ready for the next launch (ticket, done counter and
+// first-error key reset, epoch advanced), so after the one-time setup below the workspace
+// needs no host-side work between calls.
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <string.h>
 
-#include <functional>
 #include <mutex>
 
 #include "gbu_device.cuh"
@@ -26,10 +26,10 @@
 namespace {
 
 // Partition states the workspace holds: one per partition (PART_BYTES) of the input, the input's
-// first byte sitting anywhere in a 16-byte word and the three positions past its end being
+// first byte sitting anywhere in a 32-byte block and the three positions past its end being
 // judged too.
 constexpr uint32_t NOALLOC_STATES = (uint32_t)(GBU_NOALLOC_MAX_UNITS / gbu::PART_BYTES) + 1u;
-static_assert(((uint64_t)GBU_NOALLOC_MAX_UNITS + 15 + 3 + gbu::PART_BYTES - 1) / gbu::PART_BYTES <=
+static_assert(((uint64_t)GBU_NOALLOC_MAX_UNITS + 31 + 3 + gbu::PART_BYTES - 1) / gbu::PART_BYTES <=
                   NOALLOC_STATES,
               "workspace too small for the stated maximum");
 static_assert(sizeof(gbu::WsHeader) % 8 == 0, "header must keep the states 8-byte aligned");
@@ -43,22 +43,23 @@ static __device__ __align__(256) uint64_t noalloc_scratch[NOALLOC_WORDS];
 constexpr int MAX_DEVICES = 64;
 
 struct DeviceSetup {
-  std::once_flag once;
-  int rc = GBU_CUDA_ERROR;
+  std::mutex mu;
+  bool ready = false;           // set once the setup below has succeeded (then never cleared)
   uint64_t *scratch = nullptr;  // device address of noalloc_scratch on this device
   int grid = 0;                 // SMs x resident CTAs of the kernel
 };
 DeviceSetup setups[MAX_DEVICES];
 
-// One-time setup on `device` (which is current): the kernel's shared-memory opt-in, the
-// symbol's device address, the grid size,
-// and the workspace's initial contents: every state word zero (epoch 0, never a live epoch),
-// the header's counters zero, its epoch 1 and its first-error key "none".
-void setup_device(DeviceSetup &s, int device) {
+// Setup on `device` (which is current): the kernel's shared-memory opt-in, the symbol's device
+// address, the grid size, and the workspace's initial contents: every state word zero (epoch
+// 0, never a live epoch), the header's counters zero, its epoch 1 and its first-error key
+// "none".  Returns GBU_OK and marks s ready, or GBU_CUDA_ERROR and leaves s as it was, so that
+// a later call tries again.  Called with s.mu held.
+int setup_device(DeviceSetup &s, int device) {
   void *addr = nullptr;
   if (cudaGetSymbolAddress(&addr, noalloc_scratch) != cudaSuccess || !addr) {
     cudaGetLastError();
-    return;
+    return GBU_CUDA_ERROR;
   }
   int sms = 0, bps = 0;
   const size_t smem = gbu::utf8_to_utf16_smem_bytes();
@@ -69,7 +70,7 @@ void setup_device(DeviceSetup &s, int device) {
           cudaSuccess ||
       sms < 1 || bps < 1) {
     cudaGetLastError();
-    return;
+    return GBU_CUDA_ERROR;
   }
   gbu::WsHeader h;
   memset(&h, 0, sizeof(h));
@@ -80,11 +81,28 @@ void setup_device(DeviceSetup &s, int device) {
       cudaMemcpy(addr, &h, sizeof(h), cudaMemcpyHostToDevice) != cudaSuccess ||
       cudaDeviceSynchronize() != cudaSuccess) {
     cudaGetLastError();
-    return;
+    return GBU_CUDA_ERROR;
   }
   s.scratch = static_cast<uint64_t *>(addr);
   s.grid = sms * bps;
-  s.rc = GBU_OK;
+  s.ready = true;
+  return GBU_OK;
+}
+
+// Runs the setup of `device` unless it has succeeded before.  The setup's synchronous copies
+// and device synchronise are not allowed while a stream is being captured (and would spoil
+// the capture), so a call that needs the setup while `stream` is capturing returns
+// GBU_CUDA_ERROR without trying; a later call outside the capture runs it.
+int ensure_setup(DeviceSetup &s, int device, cudaStream_t stream) {
+  std::lock_guard<std::mutex> lock(s.mu);
+  if (s.ready) return GBU_OK;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(stream, &cs) != cudaSuccess) {
+    cudaGetLastError();
+    return GBU_CUDA_ERROR;
+  }
+  if (cs != cudaStreamCaptureStatusNone) return GBU_CUDA_ERROR;
+  return setup_device(s, device);
 }
 
 }  // namespace
@@ -100,14 +118,14 @@ extern "C" int gbu_convert_utf8_to_utf16le_noalloc(const uint8_t *src, uint64_t 
     return GBU_CUDA_ERROR;
   }
   DeviceSetup &s = setups[device];
-  std::call_once(s.once, setup_device, std::ref(s), device);
-  if (s.rc != GBU_OK) return s.rc;
+  const int rc = ensure_setup(s, device, (cudaStream_t)stream);
+  if (rc != GBU_OK) return rc;
 
   gbu::Params p;
   memset(&p, 0, sizeof(p));
   const uintptr_t a = (uintptr_t)src;
-  p.base = (const uint8_t *)(a & ~(uintptr_t)15);
-  p.off0 = (uint32_t)(a & 15);
+  p.base = (const uint8_t *)(a & ~(uintptr_t)31);  // the kernel's lanes read 32 bytes at a time
+  p.off0 = (uint32_t)(a & 31);
   p.n = n;
   p.vbytes = p.off0 + n;
   const uint64_t span = n == 0 ? 0 : p.vbytes + 3;  // the three positions past the end
@@ -115,8 +133,9 @@ extern "C" int gbu_convert_utf8_to_utf16le_noalloc(const uint8_t *src, uint64_t 
   p.ws = reinterpret_cast<gbu::WsHeader *>(s.scratch);
   p.states = s.scratch + sizeof(gbu::WsHeader) / 8;
   p.max_states = NOALLOC_STATES;
-  p.wait_limit = 1u << 22;
+  p.wait_limit = 1u << 22;  // as a context's default
   p.skip_tile = -1;
+  p.early_exit = 1;         // as a context's default
   p.result = result;
   const uintptr_t d = (uintptr_t)dst;
   p.dbase = (uint8_t *)(d & ~(uintptr_t)15);
