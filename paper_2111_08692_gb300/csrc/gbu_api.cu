@@ -87,6 +87,8 @@ struct gbu_ctx {
   uint64_t max_units;
   int num_sms;
   gbu::WsHeader *ws;   // device
+  gbu_result *sync_res; // device, right after the header: the result slot of the *_sync calls
+  uint64_t *sync_len;   // device, after sync_res: the length slot of the *_sync length calls
   uint64_t *states;    // device
   uint32_t max_states;
   uint32_t wait_limit;
@@ -142,10 +144,13 @@ extern "C" gbu_ctx *gbu_create(int device, uint64_t max_units) {
     return nullptr;
   }
   c->max_states = (uint32_t)tiles;
-  if (cudaMalloc(&c->ws, sizeof(gbu::WsHeader)) != cudaSuccess) {
+  // the header, then the *_sync calls' result and length slots (one allocation)
+  if (cudaMalloc(&c->ws, sizeof(gbu::WsHeader) + sizeof(gbu_result) + sizeof(uint64_t)) != cudaSuccess) {
     delete c;
     return nullptr;
   }
+  c->sync_res = reinterpret_cast<gbu_result *>(c->ws + 1);
+  c->sync_len = reinterpret_cast<uint64_t *>(c->sync_res + 1);
   if (cudaMalloc(&c->states, (size_t)c->max_states * sizeof(uint64_t)) != cudaSuccess) {
     cudaFree(c->ws);
     delete c;
@@ -365,6 +370,113 @@ extern "C" int gbu_convert_utf16le_to_utf8(gbu_ctx *c, const uint16_t *src, uint
   p.result = result;
   set_dst(&p, dst, cap, 1);
   return launch(c, K_C16, p, stream);
+}
+
+// ---- host-synchronising forms ---------------------------------------------------------------
+
+// Completes a *_sync call: rc is the launch status of the asynchronous call, which wrote its
+// result (or, for a length, the length) into the context's slot on `stream`.  Copies the slot
+// back and waits for the stream.
+static gbu_result finish_sync(gbu_ctx *c, int rc, gbu_stream stream, bool length) {
+  gbu_result r;
+  r.status = rc;
+  r.reserved = 0;
+  r.count = 0;
+  if (rc != GBU_OK) return r;
+  DeviceGuard g(c->device);
+  uint64_t len = 0;
+  void *host = length ? (void *)&len : (void *)&r;
+  const void *dev = length ? (const void *)c->sync_len : (const void *)c->sync_res;
+  if (cudaMemcpyAsync(host, dev, length ? sizeof(len) : sizeof(r), cudaMemcpyDeviceToHost, (cudaStream_t)stream) !=
+          cudaSuccess ||
+      cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) {
+    cudaGetLastError();
+    r.status = GBU_CUDA_ERROR;
+    r.reserved = 0;
+    r.count = 0;
+    return r;
+  }
+  if (length) {
+    r.status = GBU_OK;
+    r.count = len;
+  }
+  return r;
+}
+
+static gbu_result bad_argument_result() {
+  gbu_result r;
+  r.status = GBU_BAD_ARGUMENT;
+  r.reserved = 0;
+  r.count = 0;
+  return r;
+}
+
+extern "C" gbu_result gbu_validate_utf8_sync(gbu_ctx *c, const uint8_t *src, uint64_t n, gbu_stream stream) {
+  if (!c) return bad_argument_result();
+  return finish_sync(c, gbu_validate_utf8(c, src, n, c->sync_res, stream), stream, false);
+}
+
+extern "C" gbu_result gbu_validate_utf16le_sync(gbu_ctx *c, const uint16_t *src, uint64_t n, gbu_stream stream) {
+  if (!c) return bad_argument_result();
+  return finish_sync(c, gbu_validate_utf16le(c, src, n, c->sync_res, stream), stream, false);
+}
+
+extern "C" gbu_result gbu_utf16_length_from_utf8_sync(gbu_ctx *c, const uint8_t *src, uint64_t n,
+                                                      gbu_stream stream) {
+  if (!c) return bad_argument_result();
+  return finish_sync(c, gbu_utf16_length_from_utf8(c, src, n, c->sync_len, stream), stream, true);
+}
+
+extern "C" gbu_result gbu_utf8_length_from_utf16le_sync(gbu_ctx *c, const uint16_t *src, uint64_t n,
+                                                        gbu_stream stream) {
+  if (!c) return bad_argument_result();
+  return finish_sync(c, gbu_utf8_length_from_utf16le(c, src, n, c->sync_len, stream), stream, true);
+}
+
+extern "C" gbu_result gbu_convert_utf8_to_utf16le_sync(gbu_ctx *c, const uint8_t *src, uint64_t n, uint16_t *dst,
+                                                       uint64_t cap, gbu_stream stream) {
+  if (!c) return bad_argument_result();
+  return finish_sync(c, gbu_convert_utf8_to_utf16le(c, src, n, dst, cap, c->sync_res, stream), stream, false);
+}
+
+extern "C" gbu_result gbu_convert_utf16le_to_utf8_sync(gbu_ctx *c, const uint16_t *src, uint64_t n, uint8_t *dst,
+                                                       uint64_t cap, gbu_stream stream) {
+  if (!c) return bad_argument_result();
+  return finish_sync(c, gbu_convert_utf16le_to_utf8(c, src, n, dst, cap, c->sync_res, stream), stream, false);
+}
+
+extern "C" int gbu_per_string_loop(gbu_ctx *c, int op, const void *src, const uint64_t *off, uint64_t B, void *dst,
+                                   const uint64_t *dst_off, gbu_result *results, gbu_stream stream) {
+  if (!c) return GBU_BAD_ARGUMENT;
+  if (op < 0 || op >= K_COUNT || (B > 0 && (!off || !results))) return GBU_BAD_ARGUMENT;
+  const bool xcode = op == GBU_OP_CONVERT_UTF8_TO_UTF16LE || op == GBU_OP_CONVERT_UTF16LE_TO_UTF8;
+  if (xcode && B > 0 && !dst_off) return GBU_BAD_ARGUMENT;
+  const uint8_t *s8 = static_cast<const uint8_t *>(src);
+  const uint16_t *s16 = static_cast<const uint16_t *>(src);
+  for (uint64_t i = 0; i < B; ++i) {
+    const uint64_t a = off[i], n = off[i + 1] - off[i];
+    int rc;
+    switch (op) {
+      case GBU_OP_VALIDATE_UTF8: rc = gbu_validate_utf8(c, s8 + a, n, results + i, stream); break;
+      case GBU_OP_UTF16_LENGTH_FROM_UTF8:
+        rc = gbu_utf16_length_from_utf8(c, s8 + a, n, reinterpret_cast<uint64_t *>(results) + i, stream);
+        break;
+      case GBU_OP_CONVERT_UTF8_TO_UTF16LE:
+        rc = gbu_convert_utf8_to_utf16le(c, s8 + a, n, static_cast<uint16_t *>(dst) + dst_off[i],
+                                         dst_off[i + 1] - dst_off[i], results + i, stream);
+        break;
+      case GBU_OP_VALIDATE_UTF16LE: rc = gbu_validate_utf16le(c, s16 + a, n, results + i, stream); break;
+      case GBU_OP_UTF8_LENGTH_FROM_UTF16LE:
+        rc = gbu_utf8_length_from_utf16le(c, s16 + a, n, reinterpret_cast<uint64_t *>(results) + i, stream);
+        break;
+      default:
+        rc = gbu_convert_utf16le_to_utf8(c, s16 + a, n, static_cast<uint8_t *>(dst) + dst_off[i],
+                                         dst_off[i + 1] - dst_off[i], results + i, stream);
+        break;
+    }
+    if (rc != GBU_OK) return rc;
+  }
+  return GBU_OK;
 }
 
 // ---- UTF-32 ------------------------------------------------------------------------------

@@ -151,3 +151,17 @@ def test_kernel_hash_ignores_comments_only():
     for op in b.KERNEL_SOURCES:
         h = b.kernel_hash(op)
         assert len(h) == 12 and int(h, 16) >= 0 and h == b.kernel_hash(op)
+
+
+def test_sync_forms_return_bad_argument_by_value_for_a_null_context():
+    """The six host-synchronising calls return their gbu_result by value; a NULL context gives
+    {GBU_BAD_ARGUMENT, 0} before any device call."""
+    import paper_2111_08692_gb300 as g
+    L = g.lib()
+    for name in ("gbu_validate_utf8_sync", "gbu_validate_utf16le_sync", "gbu_utf16_length_from_utf8_sync",
+                 "gbu_utf8_length_from_utf16le_sync"):
+        r = getattr(L, name)(None, None, 0, None)
+        assert (r.status, r.reserved, r.count) == (17, 0, 0), name
+    for name in ("gbu_convert_utf8_to_utf16le_sync", "gbu_convert_utf16le_to_utf8_sync"):
+        r = getattr(L, name)(None, None, 0, None, 0, None)
+        assert (r.status, r.reserved, r.count) == (17, 0, 0), name

@@ -57,9 +57,11 @@ def test_empty_and_tiny(codec, torch):
 
 
 def test_all_two_byte_strings(codec, torch):
-    """Every two-byte UTF-8 string: validation and conversion, one call each."""
+    """Every two-byte UTF-8 string: validation (the asynchronous call) and conversion (the
+    host-synchronising call), one call each, against the oracle."""
     from paper_2111_08692_gb300 import result_tuple
     data = np.zeros(2, np.uint8)
+    dst = torch.full((4,), 0x5A5A, dtype=torch.int16, device="cuda")
     for b0 in range(0x80, 0x100):  # ASCII first bytes reduce to one-byte strings
         for b1 in range(256):
             data[0], data[1] = b0, b1
@@ -67,6 +69,13 @@ def test_all_two_byte_strings(codec, torch):
             src = torch.from_numpy(data.copy()).to("cuda")
             got = result_tuple(codec.validate_utf8(src))
             assert got == want, (b0, b1, got, want)
+            cwant, cdst = oracle.convert_utf8_to_utf16le(data, 2)
+            cgot = codec.convert_utf8_to_utf16le_sync(src, dst[:2])
+            assert cgot == cwant, (b0, b1, cgot, cwant)
+            if cwant[0] == "OK":
+                out = dst.cpu().numpy().view(np.uint16)
+                assert np.array_equal(out[:cwant[1]], cdst[:cwant[1]]), (b0, b1)
+                assert np.all(out[2:] == 0x5A5A), (b0, b1)
 
 
 def test_lengths_and_alignments(codec, torch):
@@ -113,7 +122,10 @@ def test_errors_near_tile_and_warp_boundaries(codec, torch):
     base = _mixed(max(3 * PART, 5 * TILE) + 2 * TILE, 3)
     starts = char_starts_utf8(base)
     targets = []
+    # streaming tiles, 512-byte and 1 KiB warp regions, 16- and 32-byte lane chunks, 4 KiB warp
+    # slices and partitions
     for b in (TILE, 2 * TILE, 3 * TILE, 512, 1024 + 512, 5 * TILE, TTILE + 16, 2 * TTILE - 16,
+              32, 992, 1024, 1056, 2048, 3072, 4096, 4096 + 1024, 8192 - 32, 12288,
               PART, PART + 512, 2 * PART, 3 * PART - 512):
         targets += [b - 5, b - 4, b - 3, b - 2, b - 1, b, b + 1, b + 2, b + 3]
     targets += [0, 1, 2, 15, 16, 17]
