@@ -658,24 +658,31 @@ def run_batched(args, codec, dev, dist, world):
         side.synchronize()
         per[name] = round(a.elapsed_time(z) / 3, 4)
 
-    # the per-string launch loop: each string through the single-buffer transcoders
+    # the per-string launch loop: each string through the single-buffer transcoders, issued
+    # by the library's C loop (gbu_per_string_loop), so that the ratio counts launches, not the
+    # interpreter
     S = min(args.loop_sample, B)
-    from paper_2111_08692_gb300 import gbu_convert_utf16le_to_utf8, gbu_convert_utf8_to_utf16le
-    off8, off16 = b["off8"], b["off16"]
-    p8, p16 = s8.data_ptr(), s16.data_ptr()
-    lres = torch.empty((2, 2), dtype=torch.int64, device=dev)
-    big = max(int(np.max(np.diff(off8[:S + 1].astype(np.int64)))), int(3 * np.max(np.diff(off16[:S + 1].astype(np.int64)))), 1)
-    ld16 = torch.empty(big, dtype=torch.int16, device=dev)
-    ld8 = torch.empty(big, dtype=torch.uint8, device=dev)
-    calls = [(p8 + int(off8[i]), int(off8[i + 1] - off8[i]), p16 + 2 * int(off16[i]), int(off16[i + 1] - off16[i]))
-             for i in range(S)]
+    from paper_2111_08692_gb300 import lib as _lib
+    L = _lib()
+    off8 = np.ascontiguousarray(b["off8"][:S + 1], dtype=np.uint64)
+    off16 = np.ascontiguousarray(b["off16"][:S + 1], dtype=np.uint64)
+    n8s, n16s = np.diff(off8.astype(np.int64)), np.diff(off16.astype(np.int64))
+    # worst-case packed outputs: n words for 8 -> 16, 3n bytes for 16 -> 8
+    doff16 = np.concatenate([[0], np.cumsum(n8s)]).astype(np.uint64)
+    doff8 = np.concatenate([[0], np.cumsum(3 * n16s)]).astype(np.uint64)
+    ld16 = torch.empty(max(int(doff16[-1]), 1), dtype=torch.int16, device=dev)
+    ld8 = torch.empty(max(int(doff8[-1]), 1), dtype=torch.uint8, device=dev)
+    lres = torch.empty((2, S, 2), dtype=torch.int64, device=dev)
     ctx, sh = codec.ctx, side.cuda_stream
-    q16, q8, qr0, qr1 = ld16.data_ptr(), ld8.data_ptr(), lres[0].data_ptr(), lres[1].data_ptr()
+    p8, p16 = s8.data_ptr(), s16.data_ptr()
 
     def loop():
-        for a8, n8_, a16, n16_ in calls:
-            gbu_convert_utf8_to_utf16le(ctx, a8, n8_, q16, n8_, qr0, sh)
-            gbu_convert_utf16le_to_utf8(ctx, a16, n16_, q8, 3 * n16_, qr1, sh)
+        for rc in (L.gbu_per_string_loop(ctx, 2, p8, off8.ctypes.data, S, ld16.data_ptr(), doff16.ctypes.data,
+                                         lres[0].data_ptr(), sh),
+                   L.gbu_per_string_loop(ctx, 5, p16, off16.ctypes.data, S, ld8.data_ptr(), doff8.ctypes.data,
+                                         lres[1].data_ptr(), sh)):
+            if rc != 0:
+                raise RuntimeError(f"gbu_per_string_loop: {rc}")
 
     loop()
     side.synchronize()
@@ -696,7 +703,8 @@ def run_batched(args, codec, dev, dist, world):
             "gpu_launches": int(launches), "kernel_ms": per, "tuned": tuned,
             "per_string_loop": {"strings": S, "ms": round(loop_ms, 3), "strings_per_s": round(loop_sps, 1),
                                 "gpu_launches": int(loop_launches),
-                                "calls": "convert_utf8_to_utf16le + convert_utf16le_to_utf8 per string"},
+                                "calls": "convert_utf8_to_utf16le then convert_utf16le_to_utf8, one "
+                                         "launch per string from the library's C loop (gbu_per_string_loop)"},
             "speedup_vs_loop": round(value / world / loop_sps, 1),
             "config": {"workload": f"{B} strings, log-normal UTF-8 lengths (median 64 B, sigma 1.5, 1 B..64 KiB), "
                                    "five profiles, 1% with one injected error; both directions into packed outputs",
@@ -904,19 +912,50 @@ def cpu_baseline(bufs, sample):
     return out
 
 
+def _cpu_cuts(a, P: int):
+    """Shard boundaries of the CPU baseline: P + 1 positions, the nominal start floor(k n / P)
+    of each shard moved forward to a character start (UTF-8: past continuation bytes, at most
+    three; UTF-16: off a second surrogate that follows a first one)."""
+    import numpy as np
+    n = a.size
+    cuts = [0]
+    for k in range(1, P):
+        c = max(k * n // P, cuts[-1])
+        if a.dtype == np.uint8:
+            for _ in range(3):
+                if c < n and (int(a[c]) & 0xC0) == 0x80:
+                    c += 1
+        elif 0 < c < n and 0xDC00 <= int(a[c]) <= 0xDFFF and 0xD800 <= int(a[c - 1]) <= 0xDBFF:
+            c += 1
+        cuts.append(min(c, n))
+    cuts.append(n)
+    return cuts
+
+
+def _cpu_combine(cuts, parts):
+    """The whole buffer's (status, count) from its shards' results: the first shard (in order)
+    with an input error gives the error, its offset moved by the shard's start; otherwise the
+    counts add up (an output that is too small is reported as for the whole buffer)."""
+    total = 0
+    for k, (kind, count) in enumerate(parts):
+        if kind not in ("OK", "OUTPUT_TOO_SMALL"):
+            return kind, cuts[k] + count
+        total += count
+    return "OK", total
+
+
 def cpu_baseline_all_cores(o, work):
     """The same work on every host core: each buffer is split into as many shards as cores at
-    character boundaries (the library's host cut function), the reference codec runs on the
-    shards in parallel threads (its calls release the interpreter lock), and the shards'
-    results are combined with gbu_combine_shards."""
+    character boundaries (_cpu_cuts), the reference codec runs on the shards in parallel threads
+    (its calls release the interpreter lock), and the shards' results are combined
+    (_cpu_combine)."""
     import concurrent.futures as cf
-    from paper_2111_08692_gb300 import combine_shards, shard_cuts_host
     cores = os.cpu_count() or 1
     jobs = []
     for a8, a16 in work:
-        c8, c16 = shard_cuts_host(a8, cores), shard_cuts_host(a16, cores)
-        jobs.append((a8, c8, [a8[int(c8[k]):int(c8[k + 1])] for k in range(cores)],
-                     a16, c16, [a16[int(c16[k]):int(c16[k + 1])] for k in range(cores)]))
+        c8, c16 = _cpu_cuts(a8, cores), _cpu_cuts(a16, cores)
+        jobs.append((a8, c8, [a8[c8[k]:c8[k + 1]] for k in range(cores)],
+                     a16, c16, [a16[c16[k]:c16[k + 1]] for k in range(cores)]))
 
     def shard8(s):
         return (o.validate_utf8(s), o.utf16_length_from_utf8(s), o.convert_utf8_to_utf16le(s)[0])
@@ -931,8 +970,8 @@ def cpu_baseline_all_cores(o, work):
             r8 = list(ex.map(shard8, s8))
             r16 = list(ex.map(shard16, s16))
             for r, c in ((r8, c8), (r16, c16)):
-                combine_shards(c, [x[0] for x in r])
-                combine_shards(c, [x[2] for x in r])
+                _cpu_combine(c, [x[0] for x in r])
+                _cpu_combine(c, [x[2] for x in r])
             nbytes += 3 * a8.size + 6 * a16.size
         dt = time.perf_counter() - t
     return {"value": round(nbytes / dt / 1e9, 3), "unit": "GB/s", "cores": cores,

@@ -101,3 +101,41 @@ def test_reference_arm_other_ranks_exit_quietly(tmp_path):
                    {"RANK": "1", "LOCAL_RANK": "1", "WORLD_SIZE": "2"})
     assert p.returncode == 0, p.stderr[-2000:]
     assert not [ln for ln in p.stdout.splitlines() if ln.startswith("{")]
+
+
+def test_cpu_baseline_shards_combine_to_the_whole_buffer_result():
+    """The all-cores CPU baseline's own cut and combination: shards cut at character
+    boundaries and run through the oracle give, combined, the oracle's result on the whole
+    buffer (valid input, and input with errors in several shards)."""
+    import numpy as np
+
+    import bench
+    import oracle
+    import workloads as W
+    u8, u16 = W.profile_buffers("mixed", 200_003, 100_001, 77, cache=False)
+    bad8 = u8.copy()
+    for k in (150_000, 60_000, 180_000):  # several errors; the first one decides
+        while (bad8[k] & 0xC0) == 0x80:
+            k -= 1
+        bad8[k] = 0xFF
+    bad16 = u16.copy()
+    bad16[70_000] = 0xDC00
+    bad16[30_000] = 0xD800
+    bad16[30_001] = 0x41
+    for P in (1, 2, 7, 16):
+        for a in (u8, bad8):
+            cuts = bench._cpu_cuts(a, P)
+            assert cuts[0] == 0 and cuts[-1] == a.size and cuts == sorted(cuts)
+            assert all(c == a.size or (int(a[c]) & 0xC0) != 0x80 for c in cuts[1:-1])
+            got = bench._cpu_combine(cuts, [oracle.validate_utf8(a[cuts[k]:cuts[k + 1]]) for k in range(P)])
+            assert got == oracle.validate_utf8(a), (P, got)
+            conv = [oracle.convert_utf8_to_utf16le(a[cuts[k]:cuts[k + 1]])[0] for k in range(P)]
+            assert bench._cpu_combine(cuts, conv) == oracle.convert_utf8_to_utf16le(a)[0]
+        for a in (u16, bad16):
+            cuts = bench._cpu_cuts(a, P)
+            assert all(not (0xDC00 <= int(a[c]) <= 0xDFFF and 0xD800 <= int(a[c - 1]) <= 0xDBFF)
+                       for c in cuts[1:-1] if 0 < c < a.size)
+            got = bench._cpu_combine(cuts, [oracle.validate_utf16le(a[cuts[k]:cuts[k + 1]]) for k in range(P)])
+            assert got == oracle.validate_utf16le(a), (P, got)
+            conv = [oracle.convert_utf16le_to_utf8(a[cuts[k]:cuts[k + 1]])[0] for k in range(P)]
+            assert bench._cpu_combine(cuts, conv) == oracle.convert_utf16le_to_utf8(a)[0]

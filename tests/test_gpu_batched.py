@@ -283,3 +283,50 @@ def test_batched_full_size_one_million_strings(torch, codec):
     transcoding into exact slots, against the oracle."""
     b = W.batched_strings(1_000_000, 1000)
     _check_all(torch, codec, b, (8, 64, 4096))
+
+
+def test_per_string_loop_matches_the_oracle_string_by_string(torch, codec):
+    """gbu_per_string_loop (one single-buffer call per string, issued from the library's C loop,
+    host offsets): every operation, each string's result and defined output units against the
+    oracle, and the destination's canary after the last slot."""
+    from paper_2111_08692_gb300 import lib
+    L = lib()
+    b = _batch(400, 77, err=0.1)
+    u8, off8, u16, off16 = b["u8"], b["off8"], b["u16"], b["off16"]
+    off8, off16 = np.ascontiguousarray(off8, np.uint64), np.ascontiguousarray(off16, np.uint64)
+    B = off8.size - 1
+    s8, s16 = _dev(torch, u8), _dev(torch, u16, torch.int16)
+    stream = torch.cuda.current_stream().cuda_stream
+    res = torch.zeros((B, 2), dtype=torch.int64, device="cuda")
+    for op, fn, src, s_dev, off in ((0, oracle.validate_utf8, u8, s8, off8), (3, oracle.validate_utf16le, u16, s16, off16)):
+        assert L.gbu_per_string_loop(codec.ctx, op, s_dev.data_ptr(), off.ctypes.data, B, None, None,
+                                     res.data_ptr(), stream) == 0
+        want = [fn(src[int(off[i]):int(off[i + 1])]) for i in range(B)]
+        assert _gpu_results(res) == want
+    for op, fn, src, s_dev, off in ((1, oracle.utf16_length_from_utf8, u8, s8, off8),
+                                    (4, oracle.utf8_length_from_utf16le, u16, s16, off16)):
+        assert L.gbu_per_string_loop(codec.ctx, op, s_dev.data_ptr(), off.ctypes.data, B, None, None,
+                                     res.data_ptr(), stream) == 0
+        got = res.cpu().numpy().view(np.uint64)[:, 0]
+        assert np.array_equal(got, _oracle_lengths(fn, src, off))
+    for op, conv, plen, lenf, src, s_dev, off, unit in (
+            (2, oracle.convert_utf8_to_utf16le_batched, oracle.utf16_length_from_utf8, oracle.utf16_length_from_utf8,
+             u8, s8, off8, np.uint16),
+            (5, oracle.convert_utf16le_to_utf8_batched, oracle.utf8_length_from_utf16le, oracle.utf8_length_from_utf16le,
+             u16, s16, off16, np.uint8)):
+        caps = _oracle_lengths(lenf, src, off).astype(np.int64)
+        dst_off = np.zeros(B + 1, dtype=np.uint64)
+        np.cumsum(caps, out=dst_off[1:].view(np.int64))
+        canary = 0x5A5A if unit == np.uint16 else 0x5A
+        dst = torch.full((int(dst_off[-1]) + 64,), canary, dtype=torch.int16 if unit == np.uint16 else torch.uint8,
+                         device="cuda")
+        assert L.gbu_per_string_loop(codec.ctx, op, s_dev.data_ptr(), off.ctypes.data, B, dst.data_ptr(),
+                                     dst_off.ctypes.data, res.data_ptr(), stream) == 0
+        want, odst = conv(src, off, dst_off)
+        assert _gpu_results(res) == want
+        host = dst.cpu().numpy()
+        if unit == np.uint16:
+            host = host.view(np.uint16)
+        mask = _defined_mask(dst_off, want, src, off, plen)
+        assert np.array_equal(host[:int(dst_off[-1])][mask], odst[mask])
+        assert np.all(host[int(dst_off[-1]):] == canary)
