@@ -102,29 +102,6 @@ struct Utf16ToUtf8Wide {
   // Staging stores, each a single PTX block whose predicates come from mask tests of the word
   // (one logic op each), so that ptxas emits predicated stores and adds and no branch.
 
-  // A word below 0x800 at shared address o: b0, then b1 where the word is >= 0x80 (a nonzero
-  // w & FF80); o advances by the bytes written.
-  __device__ __forceinline__ static void sts_12(uint32_t &o, uint32_t w, uint32_t b0, uint32_t b1) {
-    asm volatile(
-        "{\n\t.reg .pred q;\n\t.reg .b32 t;\n\tand.b32 t, %1, 0xFF80;\n\tsetp.ne.b32 q, t, 0;\n\t"
-        "st.shared.u8 [%0], %2;\n\t@q st.shared.u8 [%0+1], %3;\n\tadd.u32 %0, %0, 1;\n\t@q add.u32 %0, %0, 1;\n\t}"
-        : "+r"(o)
-        : "r"(w), "h"((unsigned short)b0), "h"((unsigned short)b1)
-        : "memory");
-  }
-
-  // A word that is not a surrogate: b0, then b1 where it is >= 0x80 and b2 where it is >= 0x800.
-  __device__ __forceinline__ static void sts_123(uint32_t &o, uint32_t w, uint32_t b0, uint32_t b1, uint32_t b2) {
-    asm volatile(
-        "{\n\t.reg .pred q1, q2;\n\t.reg .b32 t1, t2;\n\tand.b32 t1, %1, 0xFF80;\n\tsetp.ne.b32 q1, t1, 0;\n\t"
-        "and.b32 t2, %1, 0xF800;\n\tsetp.ne.b32 q2, t2, 0;\n\t"
-        "st.shared.u8 [%0], %2;\n\t@q1 st.shared.u8 [%0+1], %3;\n\t@q2 st.shared.u8 [%0+2], %4;\n\t"
-        "add.u32 %0, %0, 1;\n\t@q1 add.u32 %0, %0, 1;\n\t@q2 add.u32 %0, %0, 1;\n\t}"
-        : "+r"(o)
-        : "r"(w), "h"((unsigned short)b0), "h"((unsigned short)b1), "h"((unsigned short)b2)
-        : "memory");
-  }
-
   // One word of a register: its first byte b0 at o, and b1 at o+1 where (S & BIT) != 0; o
   // advances by the bytes written.
   template <uint32_t BIT>
@@ -137,15 +114,19 @@ struct Utf16ToUtf8Wide {
         : "memory");
   }
 
-  // The UTF-8 form of one word that is not part of a surrogate pair: b0..b2 of its one-, two-
-  // or three-byte form (a lone surrogate takes the three-byte form; what it writes lies past the
-  // first error).
-  __device__ __forceinline__ static void bmp_bytes(uint32_t w, uint32_t &b0, uint32_t &b1, uint32_t &b2) {
-    const uint32_t c6 = w & 0x3Fu, t6 = w >> 6;
-    const bool g1 = w >= 0x80u, g2 = w >= 0x800u;
-    b0 = g2 ? 0xE0u + (w >> 12) : (g1 ? 0xC0u + t6 : w);
-    b1 = g2 ? (0x80u | (t6 & 0x3Fu)) : 0x80u + c6;
-    b2 = 0x80u + c6;
+  // One word of a register: b0 at o, b1 at o+1 where (S1 & BIT) != 0, b2 at o+2 where
+  // (S2 & BIT) != 0 (S1, S2: its >= 0x80 and >= 0x800 flags); o advances by the bytes written.
+  template <uint32_t BIT>
+  __device__ __forceinline__ static void sts_123m(uint32_t &o, uint32_t S1, uint32_t S2, uint32_t b0, uint32_t b1,
+                                                  uint32_t b2) {
+    asm volatile(
+        "{\n\t.reg .pred q1, q2;\n\t.reg .b32 t1, t2;\n\tand.b32 t1, %1, %6;\n\tsetp.ne.b32 q1, t1, 0;\n\t"
+        "and.b32 t2, %2, %6;\n\tsetp.ne.b32 q2, t2, 0;\n\t"
+        "st.shared.u8 [%0], %3;\n\t@q1 st.shared.u8 [%0+1], %4;\n\t@q2 st.shared.u8 [%0+2], %5;\n\t"
+        "add.u32 %0, %0, 1;\n\t@q1 add.u32 %0, %0, 1;\n\t@q2 add.u32 %0, %0, 1;\n\t}"
+        : "+r"(o)
+        : "r"(S1), "r"(S2), "r"(b0), "r"(b1), "r"(b2), "n"(BIT)
+        : "memory");
   }
 
   __device__ __forceinline__ static Region wconvert(const Params &p, const uint32_t W[8], uint32_t prev,
@@ -187,22 +168,37 @@ struct Utf16ToUtf8Wide {
     Region g{rtot, 0u, 0u, rtot};
     uint32_t o = sbase + base + x0;
     if (!(rflags & (F_SUR | F_THREE))) {
-      // only words below 0x800 (Section 4's one-and-two-byte route)
+      // Only words below 0x800 (Section 4's one-and-two-byte route), two words per register:
+      // per 16-bit lane, the first byte is the word itself or C0 | w >> 6, the second 80 | w & 3F.
 #pragma unroll
-      for (int j = 0; j < 16; ++j) {
-        const uint32_t w = word(W, j);
-        sts_12(o, w, w >= 0x80u ? 0xC0u + (w >> 6) : w, 0x80u | (w & 0x3Fu));
+      for (int k = 0; k < 8; ++k) {
+        const uint32_t X = W[k];
+        const uint32_t g1 = lanes16_ge80(X);       // bit 15 of a lane: the word is >= 0x80
+        const uint32_t G1 = prmt(g1, 0u, 0xBB99u);  // the same as a lane mask
+        const uint32_t B0 = (((X >> 6) & 0x001F001Fu) | 0x00C000C0u) & G1 | (X & ~G1);
+        const uint32_t B1 = (X & 0x003F003Fu) | 0x00800080u;
+        sts_1or2<0x8000u>(o, g1, B0, B1);
+        sts_1or2<0x80000000u>(o, g1, B0 >> 16, B1 >> 16);
       }
       return g;
     }
     if (!(rflags & F_SUR)) {
-      // no surrogate in the region: every word is a character of one to three bytes
+      // No surrogate in the region: every word is a character of one to three bytes, two words
+      // per register.  Per 16-bit lane: the first byte is w, C0 | w >> 6 or E0 | w >> 12; the
+      // second 80 | w & 3F (two bytes) or 80 | (w >> 6) & 3F (three); the third 80 | w & 3F.
 #pragma unroll
-      for (int j = 0; j < 16; ++j) {
-        const uint32_t w = word(W, j);
-        uint32_t b0, b1, b2;
-        bmp_bytes(w, b0, b1, b2);
-        sts_123(o, w, b0, b1, b2);
+      for (int k = 0; k < 8; ++k) {
+        const uint32_t X = W[k];
+        const uint32_t g1 = lanes16_ge80(X), g2 = lanes16_ge800(X);
+        const uint32_t G1 = prmt(g1, 0u, 0xBB99u), G2 = prmt(g2, 0u, 0xBB99u);
+        const uint32_t A6 = X >> 6;
+        const uint32_t T2 = (A6 & 0x001F001Fu) | 0x00C000C0u;
+        const uint32_t T3 = ((X >> 12) & 0x000F000Fu) | 0x00E000E0u;
+        const uint32_t B0 = (T3 & G2) | (((T2 & G1) | (X & ~G1)) & ~G2);
+        const uint32_t B2 = (X & 0x003F003Fu) | 0x00800080u;
+        const uint32_t B1 = (((A6 & 0x003F003Fu) | 0x00800080u) & G2) | (B2 & ~G2);
+        sts_123m<0x8000u>(o, g1, g2, B0, B1, B2);
+        sts_123m<0x80000000u>(o, g1, g2, B0 >> 16, B1 >> 16, B2 >> 16);
       }
       return g;
     }
