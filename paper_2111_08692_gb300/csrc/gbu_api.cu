@@ -258,10 +258,10 @@ static int make_params(gbu_ctx *c, int k, const void *src, uint64_t n, uint32_t 
   if (unit_bytes == 2 && ((uintptr_t)src & 1)) return GBU_BAD_ARGUMENT;
   if (unit_bytes == 4 && ((uintptr_t)src & 3)) return GBU_BAD_ARGUMENT;
   memset(p, 0, sizeof(*p));
-  // the source rounded down to 16 bytes (32 for the UTF-8 <-> UTF-16LE transcoders, whose
-  // lanes read 32 bytes at a time)
+  // the source rounded down to 16 bytes (32 for the UTF-8 <-> UTF-16LE / UTF-16BE transcoders,
+  // whose lanes read 32 bytes at a time)
   const uintptr_t a = (uintptr_t)src;
-  const uintptr_t amask = (k == K_C8 || k == K_C16) ? 31 : 15;
+  const uintptr_t amask = (k == K_C8 || k == K_C16 || k == K_C8BE || k == K_C16BE) ? 31 : 15;
   p->base = (const uint8_t *)(a & ~amask);
   p->off0 = (uint32_t)(a & amask);
   p->n = n;

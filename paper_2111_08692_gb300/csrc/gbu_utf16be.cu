@@ -2,69 +2,70 @@
 //
 // UTF-16BE holds the same words as UTF-16LE (Section 3's ranges and pair formula) with each
 // word's most significant byte first, the byte order RFC 2781 names.  Both kernels are the
-// UTF-16LE partition loops with a codec that exchanges the two bytes of every word where words
-// meet memory: on loading UTF-16BE input (the count pass, the conversion pass and the
-// neighbouring words), and on the UTF-16 output staged for a region (after the region is
-// staged, before its bulk store) or widened straight from ASCII.
+// wide UTF-16LE partition loop (gbu_wide.cuh) with a codec that exchanges the two bytes of
+// every word where words meet memory: on loading UTF-16BE input (the count pass, the
+// conversion pass and the neighbouring words), and on the UTF-16 output staged for a region
+// (after the region is staged, before its bulk store) or widened straight from ASCII.
 #include <stdint.h>
 
-#include "gbu_codec_utf16.cuh"
-#include "gbu_codec_utf8.cuh"
 #include "gbu_kernels.h"
+#include "gbu_wide_utf16.cuh"
+#include "gbu_wide_utf8.cuh"
 
 namespace gbu {
 
 __device__ __forceinline__ uint32_t swap_words(uint32_t w) { return __byte_perm(w, 0, 0x2301); }
-__device__ __forceinline__ uint4 swap_words(uint4 v) {
-  return make_uint4(swap_words(v.x), swap_words(v.y), swap_words(v.z), swap_words(v.w));
-}
 
 // UTF-16BE input: the UTF-16LE codec on byte-exchanged words.
-struct Utf16BEToUtf8 : Utf16ToUtf8 {
+struct Utf16BEToUtf8Wide : Utf16ToUtf8Wide {
   static constexpr uint32_t ASCII_MASK = 0x80FF80FFu;  // nonzero in a raw word: a word >= 0x80
 
-  __device__ __forceinline__ static void ascii_direct(uint8_t *dst, uint4 v, uint32_t prev, long long c,
-                                                      unsigned long long &err_pos) {
-    Utf16ToUtf8::ascii_direct(dst, swap_words(v), prev, c, err_pos);
+  __device__ __forceinline__ static void swap8(const uint32_t W[8], uint32_t S[8]) {
+#pragma unroll
+    for (int k = 0; k < 8; ++k) S[k] = swap_words(W[k]);
   }
-  __device__ __forceinline__ static uint32_t count(const Params &p, uint4 v, long long c, bool edge,
-                                                   uint32_t &flags) {
-    return Utf16ToUtf8::count(p, swap_words(v), c, edge, flags);
+  __device__ __forceinline__ static void wascii_direct(uint8_t *dst, const uint32_t W[8], uint32_t prev, long long c,
+                                                       unsigned long long &err_pos) {
+    uint32_t S[8];
+    swap8(W, S);
+    Utf16ToUtf8Wide::wascii_direct(dst, S, prev, c, err_pos);
   }
-  __device__ __forceinline__ static Region convert(const Params &p, uint4 v, uint32_t prev, uint32_t next,
-                                                   long long c, bool edge, bool inside, uint8_t *st, uint32_t base,
-                                                   uint32_t x0, uint32_t rtot, uint32_t rflags,
-                                                   unsigned long long &err_pos) {
-    return Utf16ToUtf8::convert(p, swap_words(v), swap_words(prev), swap_words(next), c, edge, inside, st, base, x0,
-                                rtot, rflags, err_pos);
+  __device__ __forceinline__ static uint32_t wcount(const Params &p, const uint32_t W[8], long long c, bool edge,
+                                                    uint32_t &flags) {
+    uint32_t S[8];
+    swap8(W, S);
+    return Utf16ToUtf8Wide::wcount(p, S, c, edge, flags);
+  }
+  __device__ __forceinline__ static Region wconvert(const Params &p, const uint32_t W[8], uint32_t prev,
+                                                    uint32_t next, long long c, bool edge, bool inside, uint8_t *st,
+                                                    uint32_t base, uint32_t x0, uint32_t rtot, uint32_t rflags,
+                                                    unsigned long long &err_pos) {
+    uint32_t S[8];
+    swap8(W, S);
+    return Utf16ToUtf8Wide::wconvert(p, S, swap_words(prev), swap_words(next), c, edge, inside, st, base, x0, rtot,
+                                     rflags, err_pos);
   }
 };
 
 // UTF-16BE output: the UTF-8 -> UTF-16LE codec, then the staged words byte-exchanged.
-struct Utf8ToUtf16BE : Utf8ToUtf16 {
+struct Utf8ToUtf16BEWide : Utf8ToUtf16Wide {
   // An all-ASCII region widened straight to global memory, each byte as the word 00 xx.
-  __device__ __forceinline__ static void ascii_direct(uint16_t *dst, uint4 v, uint32_t prev, long long c,
-                                                      unsigned long long &err_pos) {
+  __device__ __forceinline__ static void wascii_direct(uint16_t *dst, const uint32_t W[8], uint32_t prev, long long c,
+                                                       unsigned long long &err_pos) {
     const int lane = threadIdx.x & 31;
-    if (lane == 0) {
-      const Flags8 fp = classify8(prev);
-      const uint32_t req = __funnelshift_l(fp.geC0, 0u, 8) | __funnelshift_l(fp.geE0, 0u, 16) |
-                           __funnelshift_l(fp.geF0, 0u, 24);
-      if (req && (unsigned long long)c < err_pos) err_pos = (unsigned long long)c;
-    }
-    const uint4 a = make_uint4(__byte_perm(v.x, 0, 0x1404), __byte_perm(v.x, 0, 0x3424),
-                               __byte_perm(v.y, 0, 0x1404), __byte_perm(v.y, 0, 0x3424));
-    const uint4 b = make_uint4(__byte_perm(v.z, 0, 0x1404), __byte_perm(v.z, 0, 0x3424),
-                               __byte_perm(v.w, 0, 0x1404), __byte_perm(v.w, 0, 0x3424));
-    uint4 *d = reinterpret_cast<uint4 *>(dst) + 2 * lane;
-    d[0] = a;
-    d[1] = b;
+    if (lane == 0) check_prev_lead(prev, c, err_pos);
+    uint4 *d = reinterpret_cast<uint4 *>(dst) + 4 * lane;
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+      d[i] = make_uint4(__byte_perm(W[2 * i], 0, 0x1404), __byte_perm(W[2 * i], 0, 0x3424),
+                        __byte_perm(W[2 * i + 1], 0, 0x1404), __byte_perm(W[2 * i + 1], 0, 0x3424));
   }
-  __device__ __forceinline__ static Region convert(const Params &p, uint4 v, uint32_t prev, uint32_t next,
-                                                   long long c, bool edge, bool inside, uint16_t *st, uint32_t base,
-                                                   uint32_t x0, uint32_t rtot, uint32_t rflags,
-                                                   unsigned long long &err_pos) {
-    const Region g = Utf8ToUtf16::convert(p, v, prev, next, c, edge, inside, st, base, x0, rtot, rflags, err_pos);
+  __device__ __forceinline__ static Region wconvert(const Params &p, const uint32_t W[8], uint32_t prev,
+                                                    uint32_t next, long long c, bool edge, bool inside, uint16_t *st,
+                                                    uint32_t base, uint32_t x0, uint32_t rtot, uint32_t rflags,
+                                                    unsigned long long &err_pos) {
+    const Region g =
+        Utf8ToUtf16Wide::wconvert(p, W, prev, next, c, edge, inside, st, base, x0, rtot, rflags, err_pos);
     // exchange the bytes of every staged word of the region (whole 32-bit words; a word of the
     // buffer outside the region's units is never stored)
     __syncwarp();
@@ -76,9 +77,9 @@ struct Utf8ToUtf16BE : Utf8ToUtf16 {
 };
 
 __global__ void __launch_bounds__(XT, XBLOCKS) utf16be_to_utf8_kernel(const Params p) {
-  extern __shared__ __align__(128) unsigned char smem_raw[];  // sizeof(XSmem), set at launch
-  XSmem<Utf16BEToUtf8> &sm = *reinterpret_cast<XSmem<Utf16BEToUtf8> *>(smem_raw);
-  transcode<Utf16BEToUtf8>(p, sm, [&](uint32_t status, unsigned long long key, unsigned long long tot) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];  // sizeof(WSmem), set at launch
+  WSmem<Utf16BEToUtf8Wide> &sm = *reinterpret_cast<WSmem<Utf16BEToUtf8Wide> *>(smem_raw);
+  wtranscode<Utf16BEToUtf8Wide>(p, sm, [&](uint32_t status, unsigned long long key, unsigned long long tot) {
     if (status) {
       write_result(p.result, GBU_TIMEOUT, 0);
     } else if (key != NO_ERROR) {
@@ -93,9 +94,9 @@ __global__ void __launch_bounds__(XT, XBLOCKS) utf16be_to_utf8_kernel(const Para
 }
 
 __global__ void __launch_bounds__(XT, XBLOCKS) utf8_to_utf16be_kernel(const Params p) {
-  extern __shared__ __align__(128) unsigned char smem_raw[];  // sizeof(XSmem), set at launch
-  XSmem<Utf8ToUtf16BE> &sm = *reinterpret_cast<XSmem<Utf8ToUtf16BE> *>(smem_raw);
-  transcode<Utf8ToUtf16BE>(p, sm, [&](uint32_t status, unsigned long long key, unsigned long long tot) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];  // sizeof(WSmem), set at launch
+  WSmem<Utf8ToUtf16BEWide> &sm = *reinterpret_cast<WSmem<Utf8ToUtf16BEWide> *>(smem_raw);
+  wtranscode<Utf8ToUtf16BEWide>(p, sm, [&](uint32_t status, unsigned long long key, unsigned long long tot) {
     if (status) {
       write_result(p.result, GBU_TIMEOUT, 0);
     } else if (key != NO_ERROR) {
@@ -110,8 +111,8 @@ __global__ void __launch_bounds__(XT, XBLOCKS) utf8_to_utf16be_kernel(const Para
 }
 
 const void *utf16be_to_utf8_kernel_ptr() { return (const void *)utf16be_to_utf8_kernel; }
-size_t utf16be_to_utf8_smem_bytes() { return sizeof(XSmem<Utf16BEToUtf8>); }
+size_t utf16be_to_utf8_smem_bytes() { return sizeof(WSmem<Utf16BEToUtf8Wide>); }
 const void *utf8_to_utf16be_kernel_ptr() { return (const void *)utf8_to_utf16be_kernel; }
-size_t utf8_to_utf16be_smem_bytes() { return sizeof(XSmem<Utf8ToUtf16BE>); }
+size_t utf8_to_utf16be_smem_bytes() { return sizeof(WSmem<Utf8ToUtf16BEWide>); }
 
 }  // namespace gbu
