@@ -64,6 +64,9 @@ def parse():
     ap.add_argument("--serving-streams", type=int, default=None)
     ap.add_argument("--serving-groups", type=int, default=None, help="launch groups in flight per stream")
     ap.add_argument("--serving-large-group", type=int, default=None)
+    ap.add_argument("--serving-rings", default="host,device",
+                    help="descriptor/result ring placements to measure (host: mapped pinned memory, device: device "
+                         "memory with copies); the first is the headline")
     return ap.parse_args()
 
 
@@ -721,7 +724,6 @@ def run_serving(args, dev, dist, world):
     import numpy as np
     import torch
     import workloads as W
-    from paper_2111_08692_gb300 import REQ_DISCARD_OUTPUT, Server
     host = W.serving_pools(64 << 20, seed=2000)
     pools = {}
     for prof, p in host.items():
@@ -730,8 +732,31 @@ def run_serving(args, dev, dist, world):
                        ("tag", "<u8")])
     comp_dt = np.dtype([("id", "<u8"), ("tag", "<u8"), ("status", "<i4"), ("res", "<i4"), ("count", "<u8"),
                         ("dst", "<u8"), ("arrival", "<u8"), ("admit", "<u8"), ("complete", "<u8")])
-    from paper_2111_08692_gb300 import OP_CODE, gbu_server_poll
-    scfg = {"budget_bytes": 8 << 30}
+    rings = [r for r in args.serving_rings.split(",") if r]
+    by_rings = {}
+    for ring in rings:
+        by_rings[ring], st, srv_cfg = _serving_loads(args, dev, host, pools, req_dt, comp_dt, ring)
+    out = by_rings[rings[0]]
+    return {"metric": "serving p50/p99 latency at each offered load", "loads": out,
+            "rings": rings[0], "loads_by_rings": by_rings,
+            "launches": int(st["launches"]), "groups": int(st["groups"]), "completed": int(st["completed"]),
+            "peak_budget_bytes": int(st["peak_budget_bytes"]),
+            "config": {"workload": "Poisson arrivals; input sizes log-uniform 16 B - 16 MiB; 10% validate-only, "
+                                   "45%/45% UTF-8->UTF-16LE / UTF-16LE->UTF-8; five profiles mixed; inputs "
+                                   "resident on the device, outputs discarded at completion",
+                       "budget_bytes": 8 << 30, "streams": srv_cfg.streams,
+                       "groups_per_stream": srv_cfg.groups_per_stream, "max_large_group": srv_cfg.max_large_group,
+                       "large_bytes": srv_cfg.large_bytes}}
+
+
+def _serving_loads(args, dev, host, pools, req_dt, comp_dt, ring):
+    """One serving run over every offered load with the given ring placement ("host": request
+    descriptors and results in mapped pinned host memory; "device": in device memory, copied
+    once each way per launch group).  Returns (per-load rows, final stats, the config)."""
+    import numpy as np
+    import workloads as W
+    from paper_2111_08692_gb300 import OP_CODE, REQ_DISCARD_OUTPUT, Server, gbu_server_poll
+    scfg = {"budget_bytes": 8 << 30, "device_rings": 1 if ring == "device" else 0}
     for key, val in (("streams", args.serving_streams), ("groups_per_stream", args.serving_groups),
                      ("max_large_group", args.serving_large_group)):
         if val is not None:
@@ -785,17 +810,10 @@ def run_serving(args, dev, dist, world):
                         "p99_us": round(float(np.percentile(lat_us, 99)), 1),
                         "max_us": round(float(lat_us.max()), 1)})
         st = srv.stats()
+        cfg = srv.cfg
     finally:
         srv.close()
-    return {"metric": "serving p50/p99 latency at each offered load", "loads": out,
-            "launches": int(st["launches"]), "groups": int(st["groups"]), "completed": int(st["completed"]),
-            "peak_budget_bytes": int(st["peak_budget_bytes"]),
-            "config": {"workload": "Poisson arrivals; input sizes log-uniform 16 B - 16 MiB; 10% validate-only, "
-                                   "45%/45% UTF-8->UTF-16LE / UTF-16LE->UTF-8; five profiles mixed; inputs "
-                                   "resident on the device, outputs discarded at completion",
-                       "budget_bytes": 8 << 30, "streams": srv.cfg.streams,
-                       "groups_per_stream": srv.cfg.groups_per_stream, "max_large_group": srv.cfg.max_large_group,
-                       "large_bytes": srv.cfg.large_bytes}}
+    return out, st, cfg
 
 
 def run_e2e(args, codec, bufs, stream, dist, world, call):

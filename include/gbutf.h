@@ -305,7 +305,12 @@ typedef struct {
   uint64_t large_bytes;       /* input bytes from which a request runs alone (default 64 KiB) */
   uint64_t max_request_units; /* largest request accepted, code units (default 16 Mi)       */
   uint32_t max_inflight;      /* admitted, not yet completed requests (default 65536)       */
-  uint32_t reserved;
+  uint32_t device_rings;      /* where a launch group's request descriptors and results live:
+                               * 0 = mapped pinned host memory, read and written by the kernels
+                               * over the host link (no copies); 1 = device memory, with one
+                               * host-to-device copy of the descriptors before the group's
+                               * launches and one device-to-host copy of the results after them
+                               * (default 0; see gbu_server_default_config) */
 } gbu_server_config;
 
 typedef struct {

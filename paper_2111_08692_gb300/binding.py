@@ -40,7 +40,7 @@ class GbuServerConfig(ctypes.Structure):
                 ("groups_per_stream", ctypes.c_int32), ("max_group", ctypes.c_uint32),
                 ("max_large_group", ctypes.c_uint32), ("large_bytes", ctypes.c_uint64),
                 ("max_request_units", ctypes.c_uint64), ("max_inflight", ctypes.c_uint32),
-                ("reserved", ctypes.c_uint32)]
+                ("device_rings", ctypes.c_uint32)]
 
 
 class GbuRequest(ctypes.Structure):

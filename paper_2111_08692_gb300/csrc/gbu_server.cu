@@ -14,9 +14,11 @@
 //      operation go together into ONE batched launch over device descriptors (warp per
 //      string, CTA per longer string); requests of at least large_bytes each get a
 //      single-buffer launch (all SMs on one string), several per group.  A group is: the
-//      launches and an event; descriptors and results stay in mapped pinned host memory,
-//      which the kernels read and write directly.  Groups are spread round-robin over several streams, so work admitted while
-//      earlier groups run overlaps with them on the device.
+//      launches and an event.  Its descriptors and results either stay in mapped pinned host
+//      memory, which the kernels read and write directly over the host link, or (device_rings)
+//      live in device memory, with one copy of the descriptors before the launches and one
+//      copy of the results after them.  Groups are spread round-robin over several streams,
+//      so work admitted while earlier groups run overlaps with them on the device.
 // Requests that arrive while the GPU is busy wait only for a free slot and memory, not for
 // the earlier groups to finish: that is the continuous batching.  Latency = completion
 // time (when the scheduler sees the event) - scheduled arrival time.
@@ -135,10 +137,11 @@ struct Slot {
   gbu_ctx *ctx;
   gbu::StringDesc *desc_h;  // pinned, mapped
   gbu_result *res_h;        // pinned, mapped
-  gbu::StringDesc *desc_d;  // the device's address of desc_h
-  gbu_result *res_d;        // the device's address of res_h
+  gbu::StringDesc *desc_d;  // what the kernels read: desc_h's device address, or a device copy
+  gbu_result *res_d;        // what the kernels write: res_h's device address, or device memory
   uint32_t *pstart_h;       // pinned, mapped: first launch partition of each large request
-  uint32_t *pstart_d;
+  uint32_t *pstart_d;       // as desc_d
+  void *rings_dev;          // device_rings: the device copies of desc, res and pstart (one allocation)
   gbu::SegState *seg_d;     // device: per-request error minimum / length / partitions done
   std::vector<Req> reqs;
   bool busy;
@@ -284,6 +287,18 @@ Slot *free_slot(gbu_server *s) {
   return nullptr;
 }
 
+// Device rings: copies a group's B descriptors (and B + 1 partition starts) from the pinned
+// staging into the slot's device memory on its stream, ahead of the launch that reads them.
+int copy_descriptors(gbu_server *s, Slot &sl, size_t B, bool pstart) {
+  if (!s->cfg.device_rings) return GBU_OK;
+  if (cudaMemcpyAsync(sl.desc_d, sl.desc_h, B * sizeof(gbu::StringDesc), cudaMemcpyHostToDevice, sl.stream) !=
+          cudaSuccess ||
+      (pstart && cudaMemcpyAsync(sl.pstart_d, sl.pstart_h, (B + 1) * sizeof(uint32_t), cudaMemcpyHostToDevice,
+                                 sl.stream) != cudaSuccess))
+    return GBU_CUDA_ERROR;
+  return GBU_OK;
+}
+
 // Enqueues the group in sl (descriptors or single-buffer launches already decided).
 void launch_group(gbu_server *s, Slot &sl, bool large) {
   const size_t B = sl.reqs.size();
@@ -303,7 +318,9 @@ void launch_group(gbu_server *s, Slot &sl, bool large) {
       ntiles += (uint32_t)gbu_internal_partitions(op0, q.r.src, q.r.n);
     }
     sl.pstart_h[B] = ntiles;
-    rc = gbu_internal_convert_segments(sl.ctx, op0, sl.desc_d, sl.pstart_d, (uint32_t)B, ntiles, sl.seg_d, sl.res_d,
+    rc = copy_descriptors(s, sl, B, true);
+    if (rc == GBU_OK)
+      rc = gbu_internal_convert_segments(sl.ctx, op0, sl.desc_d, sl.pstart_d, (uint32_t)B, ntiles, sl.seg_d, sl.res_d,
                                        sl.stream);
     s->stats.launches++;
   } else if (large) {
@@ -333,11 +350,15 @@ void launch_group(gbu_server *s, Slot &sl, bool large) {
       sl.desc_h[k].dst = q.out_off != ~0ull ? (void *)(s->arena_base + q.out_off) : nullptr;
       sl.desc_h[k].cap = out_bytes(op, q.r.n) ? out_cap(op, q.r.n) : 0;
     }
-    // the descriptors and results live in mapped pinned host memory: the kernel reads and
-    // writes them there, so a group costs its launches and one event, no copies
-    rc = gbu_internal_batch_desc(sl.ctx, op, sl.desc_d, B, sl.res_d, sl.stream);
+    // with host rings the kernel reads the descriptors and writes the results in mapped
+    // pinned host memory, so a group costs its launches and one event, no copies
+    rc = copy_descriptors(s, sl, B, false);
+    if (rc == GBU_OK) rc = gbu_internal_batch_desc(sl.ctx, op, sl.desc_d, B, sl.res_d, sl.stream);
     s->stats.launches++;
   }
+  if (rc == GBU_OK && s->cfg.device_rings &&
+      cudaMemcpyAsync(sl.res_h, sl.res_d, B * sizeof(gbu_result), cudaMemcpyDeviceToHost, sl.stream) != cudaSuccess)
+    rc = GBU_CUDA_ERROR;
   if (rc != GBU_OK) {
     // results of a group that could not be enqueued: report the failure, keep the slot usable
     cudaGetLastError();
@@ -410,6 +431,7 @@ void destroy_resources(gbu_server *s) {
     if (sl.res_h) cudaFreeHost(sl.res_h);
     if (sl.pstart_h) cudaFreeHost(sl.pstart_h);
     if (sl.seg_d) cudaFree(sl.seg_d);
+    if (sl.rings_dev) cudaFree(sl.rings_dev);
   }
   for (gbu_ctx *c : s->ctxs) gbu_destroy(c);
   for (cudaStream_t st : s->streams) cudaStreamDestroy(st);
@@ -478,6 +500,7 @@ extern "C" gbu_server *gbu_server_create(int device, const gbu_server_config *cf
     sl.pstart_h = nullptr;
     sl.pstart_d = nullptr;
     sl.seg_d = nullptr;
+    sl.rings_dev = nullptr;
     sl.stream = s->streams[i / cfg.groups_per_stream];
     sl.ctx = s->ctxs[i / cfg.groups_per_stream];
     sl.busy = false;
@@ -489,6 +512,16 @@ extern "C" gbu_server *gbu_server_create(int device, const gbu_server_config *cf
          cudaHostAlloc(&sl.pstart_h, (G + 1) * sizeof(uint32_t), cudaHostAllocMapped) == cudaSuccess &&
          cudaHostGetDevicePointer((void **)&sl.pstart_d, sl.pstart_h, 0) == cudaSuccess &&
          cudaMalloc(&sl.seg_d, G * sizeof(gbu::SegState)) == cudaSuccess;
+    if (ok && cfg.device_rings) {
+      // descriptors, results and partition starts in device memory instead (16-byte aligned parts)
+      const size_t dbytes = G * sizeof(gbu::StringDesc), rbytes = G * sizeof(gbu_result);
+      ok = cudaMalloc(&sl.rings_dev, dbytes + rbytes + (G + 1) * sizeof(uint32_t)) == cudaSuccess;
+      if (ok) {
+        sl.desc_d = static_cast<gbu::StringDesc *>(sl.rings_dev);
+        sl.res_d = reinterpret_cast<gbu_result *>(static_cast<uint8_t *>(sl.rings_dev) + dbytes);
+        sl.pstart_d = reinterpret_cast<uint32_t *>(static_cast<uint8_t *>(sl.rings_dev) + dbytes + rbytes);
+      }
+    }
     if (ok) {  // per-request states start {no error, 0, 0}
       std::vector<gbu::SegState> init(G);
       for (auto &e : init) e = gbu::SegState{gbu::NO_ERROR, 0ull, 0u, 0u};

@@ -96,10 +96,12 @@ def _expected(data, op):
     return r, (d[:r[1]] if r[0] == "OK" else np.zeros(0, d.dtype))
 
 
-def test_results_are_the_same_alone_and_in_the_mix(torch, lib, pools):
+@pytest.mark.parametrize("device_rings", [0, 1])
+def test_results_are_the_same_alone_and_in_the_mix(torch, lib, pools, device_rings):
+    """Descriptors and results in mapped host memory (0) or in device memory with copies (1)."""
     host, dev = pools
     trace = W.serving_trace(600, 2e5, host, seed=3100, max_bytes=512 << 10, p_bad=0.15)
-    srv = lib.Server(0, budget_bytes=256 << 20)
+    srv = lib.Server(0, budget_bytes=256 << 20, device_rings=device_rings)
     try:
         t0 = srv.now_ns() + 2_000_000
         reqs = [(OPS[trace["op"][i]], _request_tensor(dev, trace, i), t0 + int(trace["arrival_ns"][i]), i)
@@ -192,13 +194,14 @@ def test_cancel_and_refusals(torch, lib, pools):
         srv.close()
 
 
-def test_large_transcodings_share_partitioned_launches(torch, lib, pools):
+@pytest.mark.parametrize("device_rings", [0, 1])
+def test_large_transcodings_share_partitioned_launches(torch, lib, pools, device_rings):
     """Requests of 70 KiB to 1 MiB in both directions (clean and with injected errors) are
     grouped into one partitioned launch per direction; each result equals the oracle's."""
     host, dev = pools
     trace = W.serving_trace(40, 1e6, host, seed=3200, min_bytes=70 << 10, max_bytes=1 << 20, p_validate=0.0,
                             p_bad=0.3)
-    srv = lib.Server(0, budget_bytes=1 << 30)
+    srv = lib.Server(0, budget_bytes=1 << 30, device_rings=device_rings)
     try:
         reqs = [(OPS[trace["op"][i]], _request_tensor(dev, trace, i), 0, i) for i in range(len(trace["op"]))]
         first = srv.submit(reqs)
