@@ -307,7 +307,7 @@ def test_per_string_loop_matches_the_oracle_string_by_string(torch, codec):
                                     (4, oracle.utf8_length_from_utf16le, u16, s16, off16)):
         assert L.gbu_per_string_loop(codec.ctx, op, s_dev.data_ptr(), off.ctypes.data, B, None, None,
                                      res.data_ptr(), stream) == 0
-        got = res.cpu().numpy().view(np.uint64)[:, 0]
+        got = res.cpu().numpy().view(np.uint64).reshape(-1)[:B]  # lengths: a packed uint64 array
         assert np.array_equal(got, _oracle_lengths(fn, src, off))
     for op, conv, plen, lenf, src, s_dev, off, unit in (
             (2, oracle.convert_utf8_to_utf16le_batched, oracle.utf16_length_from_utf8, oracle.utf16_length_from_utf8,
