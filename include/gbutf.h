@@ -403,6 +403,39 @@ void gbu_arena_destroy(gbu_arena *arena);
 int gbu_convert_utf8_to_utf16le_noalloc(const uint8_t *src, uint64_t n, uint16_t *dst, uint64_t cap,
                                         gbu_result *result, gbu_stream stream);
 
+/* ---- Host-buffer form ----------------------------------------------------------------------
+ * The six single-buffer operations on HOST buffers, as one synchronous call: the problem as a
+ * program with its text in host memory meets it (paper §1, disk- and network-rate inputs).  The
+ * input is cut into pieces of at most piece_units code units at character starts (a UTF-8 cut
+ * moved back past at most three continuation bytes; a UTF-16 cut moved back off a second
+ * surrogate that follows a first one), and each piece goes through a host-to-device copy, the
+ * single-buffer call and a copy of its result (and output) back, on one of `streams` CUDA
+ * streams, so that the copies of one piece overlap the kernels of the others.  The result is the
+ * whole input's, as the single-buffer call would give it: the first error (its kind, and its
+ * offset in the whole input: the pieces are judged in order), else the output length (units the
+ * length calls count, or the transcoders write).  A transcoder writes dst[0 : length] (on an
+ * input error, dst[0 : valid prefix]; past cap nothing, and the result is then
+ * GBU_OUTPUT_TOO_SMALL with the full length).
+ *
+ * Host buffers should be pinned (cudaHostAlloc or cudaHostRegister) for the copies to overlap the
+ * kernels.  A pipe owns, from creation, one context and one set of device buffers per stream
+ * (2 x piece_units + 3 x piece_units + 64 bytes each) and its streams; nothing is allocated by
+ * a call.  Calls on one pipe must not overlap.  Returns GBU_OK, GBU_BAD_ARGUMENT (NULL pipe,
+ * result or src with n > 0; NULL dst with cap > 0; an odd uint16_t pointer) or GBU_CUDA_ERROR;
+ * *result is host memory. */
+typedef struct gbu_pipe gbu_pipe;
+/* piece_units 4096 .. 2^32 (default when 0: 64 Mi); streams 1..8 (default when 0: 3).  NULL on failure. */
+gbu_pipe *gbu_pipe_create(int device, uint64_t piece_units, int streams);
+void gbu_pipe_destroy(gbu_pipe *pipe);
+int gbu_pipe_validate_utf8(gbu_pipe *pipe, const uint8_t *src, uint64_t n, gbu_result *result);
+int gbu_pipe_validate_utf16le(gbu_pipe *pipe, const uint16_t *src, uint64_t n, gbu_result *result);
+int gbu_pipe_utf16_length_from_utf8(gbu_pipe *pipe, const uint8_t *src, uint64_t n, gbu_result *result);
+int gbu_pipe_utf8_length_from_utf16le(gbu_pipe *pipe, const uint16_t *src, uint64_t n, gbu_result *result);
+int gbu_pipe_convert_utf8_to_utf16le(gbu_pipe *pipe, const uint8_t *src, uint64_t n, uint16_t *dst, uint64_t cap,
+                                     gbu_result *result);
+int gbu_pipe_convert_utf16le_to_utf8(gbu_pipe *pipe, const uint16_t *src, uint64_t n, uint8_t *dst, uint64_t cap,
+                                     gbu_result *result);
+
 /* ---- Sharded form --------------------------------------------------------------------------
  * One buffer split into P shards at character boundaries, so that each shard can be handled by
  * an ordinary single-buffer call (on its own stream and context, or on its own GPU), and the

@@ -16,4 +16,4 @@ from .binding import (  # noqa: F401
     gbu_convert_utf8_to_utf16le_noalloc, gbu_create, gbu_debug_skip_publish, gbu_destroy,
     gbu_launch_config, gbu_launch_count, gbu_reset, gbu_set_wait_limit, gbu_utf16_length_from_utf8,
     gbu_utf8_length_from_utf16le, gbu_validate_utf16le, gbu_validate_utf8, lib, library_path,
-    result_tuple, shard_cuts_host, combine_shards, gbu_set_early_exit, Chunked)
+    result_tuple, shard_cuts_host, combine_shards, gbu_set_early_exit, Chunked, Pipe)

@@ -213,6 +213,17 @@ def lib() -> ctypes.CDLL:
                 getattr(L, name).argtypes = [vp]
             L.gbu_arena_destroy.restype = None
             L.gbu_arena_destroy.argtypes = [vp]
+            L.gbu_pipe_create.restype = vp
+            L.gbu_pipe_create.argtypes = [i32, u64, i32]
+            L.gbu_pipe_destroy.restype = None
+            L.gbu_pipe_destroy.argtypes = [vp]
+            for name in ("gbu_pipe_validate_utf8", "gbu_pipe_validate_utf16le", "gbu_pipe_utf16_length_from_utf8",
+                         "gbu_pipe_utf8_length_from_utf16le"):
+                getattr(L, name).restype = i32
+                getattr(L, name).argtypes = [vp, vp, u64, ctypes.POINTER(GbuResult)]
+            for name in ("gbu_pipe_convert_utf8_to_utf16le", "gbu_pipe_convert_utf16le_to_utf8"):
+                getattr(L, name).restype = i32
+                getattr(L, name).argtypes = [vp, vp, u64, vp, u64, ctypes.POINTER(GbuResult)]
             L.gbu_convert_utf8_to_utf16le_noalloc.restype = i32
             L.gbu_convert_utf8_to_utf16le_noalloc.argtypes = [vp, u64, vp, u64, vp, vp]
             _lib = L
@@ -765,6 +776,57 @@ class Chunked:
     def close(self):
         if self.handle:
             lib().gbu_chunked_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Pipe:
+    """The host-buffer form (gbu_pipe_*): the six operations on host arrays (numpy uint8 for
+    UTF-8, uint16 for UTF-16LE; pinned memory for the copies to overlap the kernels), one
+    synchronous call each.  Each method returns (status name, count) with the meaning of the
+    single-buffer call on the whole input; the transcoders write into the given host array."""
+
+    def __init__(self, device: int = 0, piece_units: int = 0, streams: int = 0):
+        self.handle = lib().gbu_pipe_create(device, piece_units, streams)
+        if not self.handle:
+            raise GbuError("gbu_pipe_create failed")
+
+    @staticmethod
+    def _ptr(a):
+        return a.ctypes.data if a is not None and a.size else None
+
+    def _call(self, name, src, *rest):
+        res = GbuResult()
+        _check(getattr(lib(), "gbu_pipe_" + name)(self.handle, self._ptr(src), src.size, *rest, ctypes.byref(res)),
+               "gbu_pipe_" + name)
+        return STATUS.get(res.status, res.status), int(res.count)
+
+    def validate_utf8(self, src):
+        return self._call("validate_utf8", src)
+
+    def validate_utf16le(self, src):
+        return self._call("validate_utf16le", src)
+
+    def utf16_length_from_utf8(self, src):
+        return self._call("utf16_length_from_utf8", src)
+
+    def utf8_length_from_utf16le(self, src):
+        return self._call("utf8_length_from_utf16le", src)
+
+    def convert_utf8_to_utf16le(self, src, dst, cap=None):
+        return self._call("convert_utf8_to_utf16le", src, self._ptr(dst), dst.size if cap is None else cap)
+
+    def convert_utf16le_to_utf8(self, src, dst, cap=None):
+        return self._call("convert_utf16le_to_utf8", src, self._ptr(dst), dst.size if cap is None else cap)
+
+    def close(self):
+        if self.handle:
+            lib().gbu_pipe_destroy(self.handle)
             self.handle = None
 
     def __del__(self):

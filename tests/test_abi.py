@@ -1,5 +1,6 @@
 """CPU checks of the C ABI library: it builds, loads, and exports every entry point that
 include/*.h declares; the product code never reaches the reference codec."""
+import ctypes
 import glob
 import os
 import re
@@ -165,3 +166,24 @@ def test_sync_forms_return_bad_argument_by_value_for_a_null_context():
     for name in ("gbu_convert_utf8_to_utf16le_sync", "gbu_convert_utf16le_to_utf8_sync"):
         r = getattr(L, name)(None, None, 0, None, 0, None)
         assert (r.status, r.reserved, r.count) == (17, 0, 0), name
+
+
+def test_pipe_refuses_bad_arguments_before_the_device():
+    """The host-buffer form: a NULL pipe or result is GBU_BAD_ARGUMENT, a NULL pipe handle is
+    ignored by destroy, and creation refuses a piece below 4096 units or a stream count outside
+    1..8 before any device call (and returns NULL without a device)."""
+    import torch
+    import paper_2111_08692_gb300 as g
+    L = g.lib()
+    res = g.GbuResult()
+    for name in ("gbu_pipe_validate_utf8", "gbu_pipe_validate_utf16le", "gbu_pipe_utf16_length_from_utf8",
+                 "gbu_pipe_utf8_length_from_utf16le"):
+        assert getattr(L, name)(None, None, 0, ctypes.byref(res)) == 17, name
+    for name in ("gbu_pipe_convert_utf8_to_utf16le", "gbu_pipe_convert_utf16le_to_utf8"):
+        assert getattr(L, name)(None, None, 0, None, 0, ctypes.byref(res)) == 17, name
+    L.gbu_pipe_destroy(None)
+    assert not L.gbu_pipe_create(0, 4095, 1)
+    assert not L.gbu_pipe_create(0, 4096, 9)
+    assert not L.gbu_pipe_create(0, 4096, -1)
+    if not torch.cuda.is_available():
+        assert not L.gbu_pipe_create(0, 0, 0)

@@ -205,6 +205,18 @@ def test_utf16_errors_near_tile_boundaries(codec, torch):
         check_utf16_input(codec, torch, data)
 
 
+def test_utf16_errors_at_the_start_of_an_aligned_buffer(codec, torch):
+    """Unpaired surrogates in the first chunks of a buffer whose first word starts a 16-byte
+    chunk (no word before it), and pairs cut by the chunk boundaries there."""
+    _, base = W.profile_buffers("emoji", 0, 1 << 15, 17, cache=False)
+    for i in range(0, 18):
+        for bad in ([0xDC00], [0xD800], [0xD800, 0x41], [0xDFFF, 0xDFFF], [0xD83D, 0xDE00]):
+            data = base.copy()
+            data[i:i + len(bad)] = bad
+            for src_off in (0, 8):
+                check_utf16_input(codec, torch, data, src_off=src_off)
+
+
 def test_surrogate_pairs_straddling_tiles(codec, torch):
     # pairs everywhere: each tile boundary splits some pair for one of the shifts
     pairs = np.tile(np.array([0xD83D, 0xDE00], np.uint16), 3 * 2048)
