@@ -409,8 +409,9 @@ int gbu_convert_utf8_to_utf16le_noalloc(const uint8_t *src, uint64_t n, uint16_t
  * input is cut into pieces of at most piece_units code units at character starts (a UTF-8 cut
  * moved back past at most three continuation bytes; a UTF-16 cut moved back off a second
  * surrogate that follows a first one), and each piece goes through a host-to-device copy, the
- * single-buffer call and a copy of its result (and output) back, on one of `streams` CUDA
- * streams, so that the copies of one piece overlap the kernels of the others.  The result is the
+ * single-buffer call and a copy of its result (and output) back, in one of `streams` lanes (a
+ * copy stream for the input and a stream for the kernel and the copies back), so that the
+ * copies of one piece overlap the kernels and copies of the others.  The result is the
  * whole input's, as the single-buffer call would give it: the first error (its kind, and its
  * offset in the whole input: the pieces are judged in order), else the output length (units the
  * length calls count, or the transcoders write).  A transcoder writes dst[0 : length] (on an
@@ -418,7 +419,7 @@ int gbu_convert_utf8_to_utf16le_noalloc(const uint8_t *src, uint64_t n, uint16_t
  * GBU_OUTPUT_TOO_SMALL with the full length).
  *
  * Host buffers should be pinned (cudaHostAlloc or cudaHostRegister) for the copies to overlap the
- * kernels.  A pipe owns, from creation, one context and one set of device buffers per stream
+ * kernels.  A pipe owns, from creation, one context and one set of device buffers per lane
  * (2 x piece_units + 3 x piece_units + 64 bytes each) and its streams; nothing is allocated by
  * a call.  Calls on one pipe must not overlap.  Returns GBU_OK, GBU_BAD_ARGUMENT (NULL pipe,
  * result or src with n > 0; NULL dst with cap > 0; an odd uint16_t pointer) or GBU_CUDA_ERROR;

@@ -160,19 +160,6 @@ __device__ __forceinline__ uint32_t utf16_len8_inside(const uint32_t W[4]) {
   return 8u + ((acc - sub) >> 7);
 }
 
-// Whether any of the 8 words is a surrogate (a test for "some lane is zero": exact as a
-// whole, although the per-lane bits it computes may not be).  A chunk without surrogate words
-// has no error: its neighbours judge their own words.
-__device__ __forceinline__ bool any_surrogate16(const uint32_t W[4]) {
-  uint32_t z = 0;
-#pragma unroll
-  for (int k = 0; k < 4; ++k) {
-    const uint32_t t = (W[k] & 0xF800F800u) ^ 0xD800D800u;
-    z |= (t - 0x00010001u) & ~t;
-  }
-  return (z & 0x80008000u) != 0;
-}
-
 // Unpaired surrogates among the 8 words of a chunk inside the buffer, given the word before
 // (prevw's high half) and after (nextw's low half): a first surrogate whose next word is not
 // a second one, or a second surrogate whose previous word is not a first one.  The surrogate
@@ -199,12 +186,54 @@ __device__ __forceinline__ bool utf16_pair_errors_inside(const uint32_t W[4], ui
   return err != 0;
 }
 
+// Surrogate flags of the four bytes of P (bit 7 of each byte): the byte is D8-DF, i.e. it is
+// the high byte of a surrogate word.  Exact per byte (a zero-byte test on (b & F8) ^ D8).
+__device__ __forceinline__ uint32_t bytes_sur(uint32_t P) {
+  const uint32_t t = (P & 0xF8F8F8F8u) ^ 0xD8D8D8D8u;
+  return ~(((t & 0x7F7F7F7Fu) + 0x7F7F7F7Fu) | t) & 0x80808080u;
+}
+
+// The high bytes of the 8 words of a chunk, four to a register in word order (the high byte
+// of a UTF-16LE word is its second byte).
+__device__ __forceinline__ void utf16_high_bytes(const uint32_t W[4], uint32_t &P0, uint32_t &P1) {
+  P0 = __byte_perm(W[0], W[1], 0x7531);
+  P1 = __byte_perm(W[2], W[3], 0x7531);
+}
+
+// Unpaired surrogates among the 8 words of a chunk inside the buffer, judged on the words'
+// high bytes alone (a word is a surrogate exactly when its high byte is D8-DF, a first one
+// when that byte's bit 2 is clear).  S0, S1: bytes_sur of the high bytes P0, P1; prevw's
+// high half and nextw's low half are the words before and after the chunk.  The pair rule
+// for two adjacent words a, b is: a is a first surrogate exactly when b is a second one, so
+// one XOR per pair judges the nine pairs from (word before, first word) to (last word, word
+// after).  A pair across a chunk boundary is judged by both chunks; the smaller chunk start
+// is the one the first-error search keeps, and it scans on from there.
+__device__ __forceinline__ bool utf16_pair_errors_bytes(uint32_t P0, uint32_t P1, uint32_t S0, uint32_t S1,
+                                                        uint32_t prevw, uint32_t nextw) {
+  const uint32_t Pe = __byte_perm(prevw, nextw, 0x3445);  // byte 0: the word after; byte 3: the word before
+  const uint32_t Se = bytes_sur(Pe) & 0x80000080u;
+  const uint32_t b0 = P0 << 5, b1 = P1 << 5, be = Pe << 5;  // bit 2 of each byte at bit 7
+  const uint32_t H0 = S0 & ~b0, L0 = S0 & b0, H1 = S1 & ~b1, L1 = S1 & b1;
+  const uint32_t He = Se & ~be, Le = Se & be;
+  // word i's second-surrogate flag against word i-1's first-surrogate flag, i = 0..7, then
+  // the word after against the last word
+  uint32_t err = L0 ^ __funnelshift_l(He, H0, 8);
+  err |= L1 ^ __funnelshift_l(H0, H1, 8);
+  err |= (Le & 0x80u) ^ (H1 >> 24);
+  return err != 0;
+}
+
 // Unpaired surrogates among the 8 words of a chunk, given the word before (prevw's high
 // half) and after (nextw's low half); words outside [lo, hi) are not judged.
 __device__ __forceinline__ bool utf16_chunk_errors(const uint32_t W[4], uint32_t prevw,
                                                    uint32_t nextw, long long c, bool edge,
                                                    long long lo, long long hi) {
-  if (!edge) return any_surrogate16(W) && utf16_pair_errors_inside(W, prevw, nextw);
+  if (!edge) {
+    uint32_t P0, P1;
+    utf16_high_bytes(W, P0, P1);
+    const uint32_t S0 = bytes_sur(P0), S1 = bytes_sur(P1);
+    return (S0 | S1) != 0 && utf16_pair_errors_bytes(P0, P1, S0, S1, prevw, nextw);
+  }
   // fast exit: no surrogate word in the chunk, and the word before is not a first surrogate
   // followed by our first word (that one is judged by the chunk that owns it)
   const uint32_t any = (W[0] | W[1] | W[2] | W[3]);

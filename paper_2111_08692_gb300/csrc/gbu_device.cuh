@@ -239,6 +239,14 @@ __device__ __forceinline__ void st_global_32B(void *p, uint4 a, uint4 b) {
                : "memory");
 }
 
+// The same with an L2 cache policy (output that no later work reads: an evict-first policy
+// keeps it from displacing input lines that are read again).
+__device__ __forceinline__ void st_global_32B_hint(void *p, uint4 a, uint4 b, uint64_t pol) {
+  asm volatile("st.global.L2::cache_hint.v8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8}, %9;" ::"l"(p), "r"(a.x),
+               "r"(a.y), "r"(a.z), "r"(a.w), "r"(b.x), "r"(b.y), "r"(b.z), "r"(b.w), "l"(pol)
+               : "memory");
+}
+
 // 16-byte streaming load with an L2 cache policy
 __device__ __forceinline__ uint4 ldg_stream_hint(const uint8_t *p, uint64_t pol) {
   uint4 v;

@@ -1,13 +1,14 @@
 // gbu_pipe.cu -- the host-buffer form: the six single-buffer operations on host memory, one
 // synchronous call each, pipelined over the device.
 //
-// The input is cut into pieces at character starts; piece i runs on stream i mod S: a copy of
-// its units to the device, the single-buffer call (its own context per stream), and a copy of
-// the call's result word back.  The host retires pieces in order: it waits for piece i's result,
-// queues the copy of its output to the right place of dst (the sum of the earlier pieces'
-// lengths, known by then), and queues piece i + S on the same stream, which therefore starts
-// only after piece i's buffers are free.  While the host waits for one piece, the copy engines
-// and the SMs work on the next ones.  The first piece with an input error decides the result,
+// The input is cut into pieces at character starts; piece i runs in lane i mod S: a copy of
+// its units to the device (on the lane's copy stream), the single-buffer call (its own context
+// per lane) and a copy of the call's result word back (on the lane's stream).  The host retires
+// pieces in order: it waits for piece i's result, queues the copy of its output to the right
+// place of dst (the sum of the earlier pieces' lengths, known by then), and queues piece i + S
+// in the same lane: its input copy waits only for piece i's kernel, its kernel for piece i's
+// output copy.  While the host waits for one piece, the copy engines and the SMs work on the
+// next ones.  The first piece with an input error decides the result,
 // with its offset moved by the piece's start (pieces start at character starts, so a sequence
 // that a cut meets is judged whole in the piece that holds its leading byte).
 #include <cuda_runtime.h>
@@ -23,7 +24,10 @@ namespace {
 enum PipeOp { P_V8, P_V16, P_L16, P_L8, P_C8, P_C16 };
 
 struct Lane {
-  cudaStream_t stream = nullptr;
+  cudaStream_t stream = nullptr;     // the piece's kernel, result copy and output copy
+  cudaStream_t in_stream = nullptr;  // the piece's input copy
+  cudaEvent_t in_ready = nullptr;    // the input copy has landed
+  cudaEvent_t kernel_done = nullptr; // the kernel has read din (the next input copy may start)
   cudaEvent_t done = nullptr;  // the piece's result word has reached host memory
   gbu_ctx *ctx = nullptr;
   uint8_t *din = nullptr;      // the piece's input (up to 2 x piece bytes)
@@ -66,7 +70,10 @@ namespace {
 void destroy_lanes(gbu_pipe *p) {
   for (Lane &l : p->lanes) {
     if (l.done) cudaEventDestroy(l.done);
+    if (l.in_ready) cudaEventDestroy(l.in_ready);
+    if (l.kernel_done) cudaEventDestroy(l.kernel_done);
     if (l.stream) cudaStreamDestroy(l.stream);
+    if (l.in_stream) cudaStreamDestroy(l.in_stream);
     if (l.ctx) gbu_destroy(l.ctx);
     if (l.din) cudaFree(l.din);
     if (l.dout) cudaFree(l.dout);
@@ -102,7 +109,10 @@ extern "C" gbu_pipe *gbu_pipe_create(int device, uint64_t piece_units, int strea
   bool ok = true;
   for (Lane &l : p->lanes) {
     ok = ok && cudaStreamCreateWithFlags(&l.stream, cudaStreamNonBlocking) == cudaSuccess &&
+         cudaStreamCreateWithFlags(&l.in_stream, cudaStreamNonBlocking) == cudaSuccess &&
          cudaEventCreateWithFlags(&l.done, cudaEventDisableTiming) == cudaSuccess &&
+         cudaEventCreateWithFlags(&l.in_ready, cudaEventDisableTiming) == cudaSuccess &&
+         cudaEventCreateWithFlags(&l.kernel_done, cudaEventDisableTiming) == cudaSuccess &&
          cudaMalloc(&l.din, 2 * piece_units) == cudaSuccess &&
          cudaMalloc(&l.dout, 3 * piece_units + 64) == cudaSuccess &&
          cudaMalloc(&l.dres, sizeof(gbu_result)) == cudaSuccess &&
@@ -122,21 +132,29 @@ extern "C" gbu_pipe *gbu_pipe_create(int device, uint64_t piece_units, int strea
 extern "C" void gbu_pipe_destroy(gbu_pipe *p) {
   if (!p) return;
   DeviceScope scope(p->device);
-  for (Lane &l : p->lanes)
+  for (Lane &l : p->lanes) {
     if (l.stream) cudaStreamSynchronize(l.stream);
+    if (l.in_stream) cudaStreamSynchronize(l.in_stream);
+  }
   destroy_lanes(p);
   delete p;
 }
 
 namespace {
 
-// The piece now in lane l: input copy, the single-buffer call, result copy, event.
+// The piece now in lane l: its input copy on the lane's copy stream, once the lane's previous
+// kernel has read din (so input copies run ahead of the output copies the host queues later on
+// the lane's stream), then the single-buffer call, the kernel_done event, the result copy and
+// the done event on the lane's stream.
 int enqueue_piece(PipeOp op, Lane &l, const void *src, uint64_t start, uint64_t len) {
   const uint64_t ub = is16(op) ? 2 : 1;
   l.start = start;
   l.len = len;
-  if (cudaMemcpyAsync(l.din, static_cast<const uint8_t *>(src) + start * ub, len * ub, cudaMemcpyHostToDevice,
-                      l.stream) != cudaSuccess)
+  if (cudaStreamWaitEvent(l.in_stream, l.kernel_done, 0) != cudaSuccess ||
+      cudaMemcpyAsync(l.din, static_cast<const uint8_t *>(src) + start * ub, len * ub, cudaMemcpyHostToDevice,
+                      l.in_stream) != cudaSuccess ||
+      cudaEventRecord(l.in_ready, l.in_stream) != cudaSuccess ||
+      cudaStreamWaitEvent(l.stream, l.in_ready, 0) != cudaSuccess)
     return GBU_CUDA_ERROR;
   int rc = GBU_OK;
   switch (op) {
@@ -159,7 +177,8 @@ int enqueue_piece(PipeOp op, Lane &l, const void *src, uint64_t start, uint64_t 
       break;
   }
   if (rc != GBU_OK) return rc;
-  if (cudaMemcpyAsync(l.hres, l.dres, sizeof(gbu_result), cudaMemcpyDeviceToHost, l.stream) != cudaSuccess ||
+  if (cudaEventRecord(l.kernel_done, l.stream) != cudaSuccess ||
+      cudaMemcpyAsync(l.hres, l.dres, sizeof(gbu_result), cudaMemcpyDeviceToHost, l.stream) != cudaSuccess ||
       cudaEventRecord(l.done, l.stream) != cudaSuccess)
     return GBU_CUDA_ERROR;
   return GBU_OK;
@@ -242,7 +261,8 @@ int run(gbu_pipe *p, PipeOp op, const void *src, uint64_t n, void *dst, uint64_t
   }
   // every piece still in flight ends before the call returns (the caller's buffers are free)
   for (Lane &l : p->lanes)
-    if (cudaStreamSynchronize(l.stream) != cudaSuccess) rc = GBU_CUDA_ERROR;
+    if (cudaStreamSynchronize(l.in_stream) != cudaSuccess || cudaStreamSynchronize(l.stream) != cudaSuccess)
+      rc = GBU_CUDA_ERROR;
   if (rc != GBU_OK) {
     cudaGetLastError();
     return rc;

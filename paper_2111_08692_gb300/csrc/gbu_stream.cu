@@ -111,6 +111,39 @@ __global__ void __launch_bounds__(STREAM_THREADS, stream_min_blocks<KMODE>()) st
         continue;
       }
     }
+    if (MODE == S_V16 && fast) {
+      // A warp tile inside the buffer: surrogate flags of every word's high byte first; a tile
+      // without a surrogate word has no error and needs no neighbouring words, and in any
+      // other tile every chunk is judged, its neighbours taken from the adjacent lanes.
+      uint32_t anys = 0;
+#pragma unroll
+      for (int r = 0; r < ST_ROUNDS; ++r) {
+        const uint32_t Wd[4] = {v[r].x, v[r].y, v[r].z, v[r].w};
+        uint32_t P0, P1;
+        utf16_high_bytes(Wd, P0, P1);
+        anys |= bytes_sur(P0) | bytes_sur(P1);
+      }
+      if (__any_sync(0xffffffffu, anys != 0)) {
+#pragma unroll
+        for (int r = 0; r < ST_ROUNDS; ++r) {
+          const uint32_t Wd[4] = {v[r].x, v[r].y, v[r].z, v[r].w};
+          const uint32_t up = __shfl_up_sync(0xffffffffu, v[r].w, 1);
+          const uint32_t down = __shfl_down_sync(0xffffffffu, v[r].x, 1);
+          const uint32_t before = r == 0 ? pre : __shfl_sync(0xffffffffu, v[r > 0 ? r - 1 : 0].w, 31);
+          const uint32_t after =
+              r == ST_ROUNDS - 1 ? post : __shfl_sync(0xffffffffu, v[r < ST_ROUNDS - 1 ? r + 1 : r].x, 0);
+          uint32_t P0, P1;
+          utf16_high_bytes(Wd, P0, P1);
+          const uint32_t S0 = bytes_sur(P0), S1 = bytes_sur(P1);
+          const bool bad = ((S0 | S1) != 0) & utf16_pair_errors_bytes(P0, P1, S0, S1, lane == 0 ? before : up,
+                                                                    lane == 31 ? after : down);
+          const long long c = t0 + 512 * r + 16 * lane;
+          if (bad && (unsigned long long)c < err_pos) err_pos = (unsigned long long)c;
+        }
+      }
+      if (early && stop_after_tile(wt, snap)) break;
+      continue;
+    }
 #pragma unroll
     for (int r = 0; r < ST_ROUNDS; ++r) {
       const long long c = t0 + 512 * r + 16 * lane;
@@ -194,24 +227,24 @@ __global__ void __launch_bounds__(STREAM_THREADS, stream_min_blocks<KMODE>()) st
 #pragma unroll
         for (int k = 0; k < 5; ++k) f[k] = classify8(W[k]);
         total += utf8_count_units(f, c, edge, lo, hi);
-      } else if (MODE == S_V16 || MODE == S_L8) {
+      } else if (MODE == S_V16) {
         const uint32_t Wd[4] = {W[1], W[2], W[3], W[4]};
-        if (MODE == S_L8) {
-          uint32_t cnt = 0;
-          if (!edge) {
-            cnt = utf16_len8_inside(Wd);
-          } else {
+        if (utf16_chunk_errors(Wd, W[0], W[5], c, edge, lo, hi) && (unsigned long long)c < err_pos)
+          err_pos = (unsigned long long)c;
+      } else if (MODE == S_L8) {
+        const uint32_t Wd[4] = {W[1], W[2], W[3], W[4]};
+        uint32_t cnt = 0;
+        if (!edge) {
+          cnt = utf16_len8_inside(Wd);
+        } else {
 #pragma unroll
-            for (int j = 0; j < 8; ++j) {
-              const uint32_t w = (Wd[j >> 1] >> (16 * (j & 1))) & 0xFFFFu;
-              const bool valid = c + 2 * j >= lo && c + 2 * j < hi;
-              cnt += valid ? len8_of_word(w) : 0u;
-            }
+          for (int j = 0; j < 8; ++j) {
+            const uint32_t w = (Wd[j >> 1] >> (16 * (j & 1))) & 0xFFFFu;
+            const bool valid = c + 2 * j >= lo && c + 2 * j < hi;
+            cnt += valid ? len8_of_word(w) : 0u;
           }
-          total += cnt;
-        } else if (utf16_chunk_errors(Wd, W[0], W[5], c, edge, lo, hi)) {
-          if ((unsigned long long)c < err_pos) err_pos = (unsigned long long)c;
         }
+        total += cnt;
       }
     }
     if (early && stop_after_tile(wt, snap)) break;

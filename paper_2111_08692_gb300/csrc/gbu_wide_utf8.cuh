@@ -68,7 +68,9 @@ struct Utf8ToUtf16Wide {
 
   // An all-ASCII region inside the buffer whose output starts at dst, 16-byte aligned: each
   // lane widens its 32 bytes and stores them with two 32-byte stores (or four 16-byte ones)
-  // (Section 4's ASCII path).
+  // (Section 4's ASCII path).  The 32-byte stores carry an evict-first L2 policy: the output,
+  // twice the input, would otherwise push out of L2 the input lines the count pass has read
+  // for the conversion to read again.
   __device__ __forceinline__ static void wascii_direct(uint16_t *dst, const uint32_t W[8], uint32_t prev, long long c,
                                                        unsigned long long &err_pos) {
     const int lane = threadIdx.x & 31;
@@ -80,8 +82,9 @@ struct Utf8ToUtf16Wide {
                         __byte_perm(W[2 * i + 1], 0, 0x4140), __byte_perm(W[2 * i + 1], 0, 0x4342));
     uint4 *d = reinterpret_cast<uint4 *>(dst) + 4 * lane;
     if (((uintptr_t)dst & 31) == 0) {
-      st_global_32B(d, q[0], q[1]);
-      st_global_32B(d + 2, q[2], q[3]);
+      const uint64_t pol = l2_policy_last_use();
+      st_global_32B_hint(d, q[0], q[1], pol);
+      st_global_32B_hint(d + 2, q[2], q[3], pol);
     } else {
 #pragma unroll
       for (int i = 0; i < 4; ++i) d[i] = q[i];
