@@ -144,6 +144,9 @@ __global__ void __launch_bounds__(STREAM_THREADS, stream_min_blocks<KMODE>()) st
       if (early && stop_after_tile(wt, snap)) break;
       continue;
     }
+    // UTF-8 validation: the rounds whose chunk of this lane holds an error; the first one gives
+    // the lane's error position after the tile (one test per tile instead of one per round)
+    uint32_t em = 0;
 #pragma unroll
     for (int r = 0; r < ST_ROUNDS; ++r) {
       const long long c = t0 + 512 * r + 16 * lane;
@@ -179,7 +182,7 @@ __global__ void __launch_bounds__(STREAM_THREADS, stream_min_blocks<KMODE>()) st
             err |= __funnelshift_l(geC0[k - 1], geC0[k], 8) ^ isC;
             err |= geC0[k] & ~((W[k] & 0x3E3E3E3Eu) + 0x7F7F7F7Fu);  // C0, C1
           }
-          if (err && (unsigned long long)c < err_pos) err_pos = (unsigned long long)c;
+          em |= err ? 1u << r : 0u;
           continue;
         }
         // No leading byte >= F0 in the region (CJK and other text of one to three bytes):
@@ -204,7 +207,7 @@ __global__ void __launch_bounds__(STREAM_THREADS, stream_min_blocks<KMODE>()) st
             c2 |= g[k].geC0 & ~g[k].geE0;
           }
           err |= utf8_special_errors(W, g, __any_sync(0xffffffffu, c2 != 0), true, false);
-          if (err && (unsigned long long)c < err_pos) err_pos = (unsigned long long)c;
+          em |= err ? 1u << r : 0u;
           continue;
         }
         // leading bytes >= F0 occur in the region: all three flags
@@ -219,7 +222,7 @@ __global__ void __launch_bounds__(STREAM_THREADS, stream_min_blocks<KMODE>()) st
           c3 |= g[k].geE0 & ~g[k].geF0;
         }
         err |= utf8_special_errors(W, g, __any_sync(0xffffffffu, c2 != 0), __any_sync(0xffffffffu, c3 != 0), true);
-        if (err && (unsigned long long)c < err_pos) err_pos = (unsigned long long)c;
+        em |= err ? 1u << r : 0u;
         continue;
       }
       if (MODE == S_L16) {
@@ -246,6 +249,10 @@ __global__ void __launch_bounds__(STREAM_THREADS, stream_min_blocks<KMODE>()) st
         }
         total += cnt;
       }
+    }
+    if (MODE == S_V8 && em) {
+      const unsigned long long c = (unsigned long long)(t0 + 512 * (__ffs(em) - 1) + 16 * lane);
+      if (c < err_pos) err_pos = c;
     }
     if (early && stop_after_tile(wt, snap)) break;
   }
