@@ -64,6 +64,7 @@ size_t kernel_smem(int k) {
 }
 int kernel_threads(int k) { return is_transcoder(k) ? gbu::XT : gbu::STREAM_THREADS; }
 uint32_t kernel_tile_bytes(int k) {
+  if (k == K_C16 || k == K_C16BE) return gbu::WIDE16_PART_BYTES;
   return is_transcoder(k) ? gbu::PART_BYTES : gbu::stream_tile_bytes();
 }
 

@@ -35,6 +35,9 @@ constexpr uint32_t CHUNK = 16;                // input bytes per thread per roun
 constexpr uint32_t ROUND_BYTES = XT * CHUNK;  // 2 KB
 constexpr int PART_ROUNDS = 8;
 constexpr uint32_t PART_BYTES = ROUND_BYTES * PART_ROUNDS;  // 16 KB per partition
+// The partition of the single-buffer UTF-16 -> UTF-8 transcoders (the wide loop with 8 KiB warp
+// slices); the UTF-8 -> UTF-16 ones use PART_BYTES.
+constexpr uint32_t WIDE16_PART_BYTES = 2 * PART_BYTES;
 
 // Scan state word: [63:62] flag, [61:44] epoch, [43:0] value.
 constexpr uint64_t ST_FLAG_AGG = 1ull << 62;

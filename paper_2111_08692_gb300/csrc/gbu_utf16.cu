@@ -9,6 +9,9 @@
 
 namespace gbu {
 
+// the host sizes the launch's partitions (Params::ntiles) with WIDE16_PART_BYTES
+static_assert(WGeom<Utf16ToUtf8Wide::WSLICE_ROUNDS>::PART == WIDE16_PART_BYTES, "UTF-16 -> UTF-8 partition size");
+
 __global__ void __launch_bounds__(XT, XBLOCKS) utf16_to_utf8_kernel(const Params p) {
   extern __shared__ __align__(128) unsigned char smem_raw[];  // sizeof(WSmem), set at launch
   WSmem<Utf16ToUtf8Wide> &sm = *reinterpret_cast<WSmem<Utf16ToUtf8Wide> *>(smem_raw);

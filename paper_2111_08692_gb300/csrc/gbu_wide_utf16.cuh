@@ -25,6 +25,7 @@ struct Utf16ToUtf8Wide {
   // a region of 512 words yields at most 1536 bytes, +2 for a pair cut at its end, plus 15
   // bytes of alignment offset
   static constexpr uint32_t WSTAGE = 3 * 512 + 32;
+  static constexpr int WSLICE_ROUNDS = 8;  // 32 KiB partitions
   static_assert(3 * 512 + 2 + 15 + 1 <= WSTAGE, "staging buffer too small");
 
   static constexpr uint32_t F_SUR = Narrow::F_SUR;
