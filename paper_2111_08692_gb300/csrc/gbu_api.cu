@@ -21,7 +21,6 @@ enum Kernel {
   K_V16BE = K_COUNT, K_L16BE, K_C16BE, K_C8BE,
   K_V32, K_L8F32, K_L32, K_C32, K_C8T32,  // validate, UTF-8 length, UTF-32 length, 32 -> 8, 8 -> 32
   K_L16F32, K_L32F16, K_C32T16, K_C16T32,  // UTF-16 length, UTF-32 length of UTF-16, 32 -> 16, 16 -> 32
-  K_C16L,                                  // 16 -> 8 on 32 KiB partitions (large inputs)
   K_ALL
 };
 
@@ -45,18 +44,16 @@ const void *kernel_ptr(int k) {
     case K_L32F16: return gbu::utf32_stream_kernel_ptr(4);
     case K_C32T16: return gbu::utf32_to_utf16_kernel_ptr();
     case K_C16T32: return gbu::utf16_to_utf32_kernel_ptr();
-    case K_C16L: return gbu::utf16_to_utf8_large_kernel_ptr();
     default: return gbu::utf16_to_utf8_kernel_ptr();
   }
 }
 bool is_transcoder(int k) {
-  return k == K_C8 || k == K_C16 || k == K_C16L || k == K_C16BE || k == K_C8BE || k == K_C32 || k == K_C8T32 || k == K_C32T16 ||
+  return k == K_C8 || k == K_C16 || k == K_C16BE || k == K_C8BE || k == K_C32 || k == K_C8T32 || k == K_C32T16 ||
          k == K_C16T32;
 }
 size_t kernel_smem(int k) {
   if (k == K_C8) return gbu::utf8_to_utf16_smem_bytes();
   if (k == K_C16) return gbu::utf16_to_utf8_smem_bytes();
-  if (k == K_C16L) return gbu::utf16_to_utf8_large_smem_bytes();
   if (k == K_C16BE) return gbu::utf16be_to_utf8_smem_bytes();
   if (k == K_C8BE) return gbu::utf8_to_utf16be_smem_bytes();
   if (k == K_C32) return gbu::utf32_to_utf8_smem_bytes();
@@ -67,7 +64,6 @@ size_t kernel_smem(int k) {
 }
 int kernel_threads(int k) { return is_transcoder(k) ? gbu::XT : gbu::STREAM_THREADS; }
 uint32_t kernel_tile_bytes(int k) {
-  if (k == K_C16L) return gbu::WIDE16_PART_BYTES;
   return is_transcoder(k) ? gbu::PART_BYTES : gbu::stream_tile_bytes();
 }
 
@@ -265,7 +261,7 @@ static int make_params(gbu_ctx *c, int k, const void *src, uint64_t n, uint32_t 
   // the source rounded down to 16 bytes (32 for the UTF-8 <-> UTF-16LE / UTF-16BE transcoders,
   // whose lanes read 32 bytes at a time)
   const uintptr_t a = (uintptr_t)src;
-  const uintptr_t amask = (k == K_C8 || k == K_C16 || k == K_C16L || k == K_C8BE || k == K_C16BE) ? 31 : 15;
+  const uintptr_t amask = (k == K_C8 || k == K_C16 || k == K_C8BE || k == K_C16BE) ? 31 : 15;
   p->base = (const uint8_t *)(a & ~amask);
   p->off0 = (uint32_t)(a & amask);
   p->n = n;
@@ -368,13 +364,12 @@ extern "C" int gbu_convert_utf8_to_utf16le(gbu_ctx *c, const uint8_t *src, uint6
 extern "C" int gbu_convert_utf16le_to_utf8(gbu_ctx *c, const uint16_t *src, uint64_t n, uint8_t *dst,
                                            uint64_t cap, gbu_result *result, gbu_stream stream) {
   gbu::Params p;
-  const int k = n >= gbu::WIDE16_LARGE_MIN_UNITS ? K_C16L : K_C16;
-  int rc = make_params(c, k, src, n, 2, false, &p);
+  int rc = make_params(c, K_C16, src, n, 2, false, &p);
   if (rc != GBU_OK) return rc;
   if (!result || (cap > 0 && !dst)) return GBU_BAD_ARGUMENT;
   p.result = result;
   set_dst(&p, dst, cap, 1);
-  return launch(c, k, p, stream);
+  return launch(c, K_C16, p, stream);
 }
 
 // ---- host-synchronising forms ---------------------------------------------------------------

@@ -35,11 +35,6 @@ constexpr uint32_t CHUNK = 16;                // input bytes per thread per roun
 constexpr uint32_t ROUND_BYTES = XT * CHUNK;  // 2 KB
 constexpr int PART_ROUNDS = 8;
 constexpr uint32_t PART_BYTES = ROUND_BYTES * PART_ROUNDS;  // 16 KB per partition
-// The partition of the single-buffer UTF-16 -> UTF-8 transcoder on large inputs (the wide loop
-// with 8 KiB warp slices), used from WIDE16_LARGE_MIN_UNITS words on; other inputs, and the other
-// wide transcoders, use PART_BYTES.
-constexpr uint32_t WIDE16_PART_BYTES = 2 * PART_BYTES;
-constexpr uint64_t WIDE16_LARGE_MIN_UNITS = 64ull << 20;
 
 // Scan state word: [63:62] flag, [61:44] epoch, [43:0] value.
 constexpr uint64_t ST_FLAG_AGG = 1ull << 62;

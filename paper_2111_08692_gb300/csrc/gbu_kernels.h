@@ -17,8 +17,6 @@ const void *utf8_to_utf16_kernel_ptr();
 const void *utf16_to_utf8_kernel_ptr();
 size_t utf8_to_utf16_smem_bytes();
 size_t utf16_to_utf8_smem_bytes();
-const void *utf16_to_utf8_large_kernel_ptr();  // 32 KiB partitions, for large inputs
-size_t utf16_to_utf8_large_smem_bytes();
 // the transcoders between UTF-8 and UTF-16BE (same launch shape as the UTF-16LE ones)
 const void *utf16be_to_utf8_kernel_ptr();
 size_t utf16be_to_utf8_smem_bytes();

@@ -9,15 +9,10 @@
 
 namespace gbu {
 
-// the host sizes the launches' partitions (Params::ntiles) with PART_BYTES and WIDE16_PART_BYTES
-static_assert(WGeom<Utf16ToUtf8Wide::WSLICE_ROUNDS>::PART == PART_BYTES, "UTF-16 -> UTF-8 partition size");
-static_assert(WGeom<Utf16ToUtf8WideL::WSLICE_ROUNDS>::PART == WIDE16_PART_BYTES, "large-input partition size");
-
-template <class Codec>
-__device__ __forceinline__ void utf16_to_utf8_body(const Params &p) {
+__global__ void __launch_bounds__(XT, XBLOCKS) utf16_to_utf8_kernel(const Params p) {
   extern __shared__ __align__(128) unsigned char smem_raw[];  // sizeof(WSmem), set at launch
-  WSmem<Codec> &sm = *reinterpret_cast<WSmem<Codec> *>(smem_raw);
-  wtranscode<Codec>(p, sm, [&](uint32_t status, unsigned long long key, unsigned long long tot) {
+  WSmem<Utf16ToUtf8Wide> &sm = *reinterpret_cast<WSmem<Utf16ToUtf8Wide> *>(smem_raw);
+  wtranscode<Utf16ToUtf8Wide>(p, sm, [&](uint32_t status, unsigned long long key, unsigned long long tot) {
     if (status) {
       write_result(p.result, GBU_TIMEOUT, 0);
     } else if (key != NO_ERROR) {
@@ -29,15 +24,6 @@ __device__ __forceinline__ void utf16_to_utf8_body(const Params &p) {
       write_result(p.result, tot > p.cap ? GBU_OUTPUT_TOO_SMALL : GBU_OK, tot);
     }
   });
-}
-
-__global__ void __launch_bounds__(XT, XBLOCKS) utf16_to_utf8_kernel(const Params p) {
-  utf16_to_utf8_body<Utf16ToUtf8Wide>(p);
-}
-
-// Inputs of at least WIDE16_LARGE_MIN_UNITS words: 32 KiB partitions.
-__global__ void __launch_bounds__(XT, XBLOCKS) utf16_to_utf8_large_kernel(const Params p) {
-  utf16_to_utf8_body<Utf16ToUtf8WideL>(p);
 }
 
 // Several strings per launch (the serving loop's large requests): one result per string.
@@ -63,8 +49,6 @@ __global__ void __launch_bounds__(XT, XBLOCKS) utf16_to_utf8_segments_kernel(con
 
 const void *utf16_to_utf8_kernel_ptr() { return (const void *)utf16_to_utf8_kernel; }
 size_t utf16_to_utf8_smem_bytes() { return sizeof(WSmem<Utf16ToUtf8Wide>); }
-const void *utf16_to_utf8_large_kernel_ptr() { return (const void *)utf16_to_utf8_large_kernel; }
-size_t utf16_to_utf8_large_smem_bytes() { return sizeof(WSmem<Utf16ToUtf8WideL>); }
 size_t utf16_to_utf8_segments_smem_bytes() { return sizeof(XSmem<Utf16ToUtf8>); }
 
 const void *utf16_to_utf8_segments_kernel_ptr() { return (const void *)utf16_to_utf8_segments_kernel; }

@@ -9,9 +9,6 @@
 
 namespace gbu {
 
-// the host sizes the launch's partitions (Params::ntiles) with PART_BYTES
-static_assert(WGeom<Utf8ToUtf16Wide::WSLICE_ROUNDS>::PART == PART_BYTES, "UTF-8 -> UTF-16 partition size");
-
 __global__ void __launch_bounds__(XT, XBLOCKS) utf8_to_utf16_kernel(const Params p) {
   extern __shared__ __align__(128) unsigned char smem_raw[];  // sizeof(WSmem), set at launch
   WSmem<Utf8ToUtf16Wide> &sm = *reinterpret_cast<WSmem<Utf8ToUtf16Wide> *>(smem_raw);

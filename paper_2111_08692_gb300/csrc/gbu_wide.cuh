@@ -1,8 +1,8 @@
 // gbu_wide.cuh -- the partition loop of the single-buffer UTF-8 <-> UTF-16LE transcoders, with
 // 32 input bytes per lane and 1 KiB warp regions.
 //
-// The loop has the shape of gbu_xcode.cuh's: a CTA of XT threads claims partitions from a
-// ticket counter, counts the output of the NEXT partition (a read from HBM) and publishes
+// The loop has the shape of gbu_xcode.cuh's: a CTA of XT threads claims 16 KiB partitions from
+// a ticket counter, counts the output of the NEXT partition (a read from HBM) and publishes
 // that aggregate before it takes the CURRENT partition's output offset from the CTA-wide
 // decoupled look-back, then converts the current partition (a re-read, normally from L2)
 // through per-warp staging buffers and bulk stores.  What differs is the grain, chosen so that
@@ -12,9 +12,7 @@
 //   * a lane owns 32 consecutive bytes of its region, read by one 256-bit load; the words just
 //     before and after them come from the adjacent lanes, or from the previous region's lane 31
 //     and the next region's lane 0;
-//   * warp w owns the w-th slice of the partition, WSLICE_ROUNDS regions of 1 KiB (4 for
-//     UTF-8 -> UTF-16, a 16 KiB partition; 8 for UTF-16 -> UTF-8, 32 KiB, whose smaller output
-//     leaves room in L2 for the larger partition's input between its count and its conversion);
+//   * warp w owns the w-th 4 KiB slice of the partition, four regions of 1 KiB;
 //   * the count pass keeps, per region, every lane's exclusive output offset and the region's
 //     total and codec flags, and per slice its total; a warp finds its regions' offsets from
 //     the slice totals of the warps before it and a running sum over its own regions.
@@ -22,7 +20,6 @@
 //   struct Codec {
 //     using Out = uint8_t or uint16_t;
 //     static constexpr uint32_t WSTAGE;           // staged units per warp buffer
-//     static constexpr int WSLICE_ROUNDS;         // 1 KiB regions per warp slice
 //     static constexpr uint32_t ASCII_MASK;       // nonzero in an input word: a unit >= 0x80
 //     static constexpr uint32_t LANE_UNITS;       // units out of 32 bytes of ASCII input
 //     static constexpr uint32_t WREGION_UNITS;    // units out of an all-ASCII region
@@ -49,28 +46,21 @@ namespace gbu {
 
 constexpr uint32_t WLANE = 32;                        // input bytes per lane per region
 constexpr uint32_t WREGION = 32 * WLANE;              // 1 KiB per warp region
-// The partition geometry, from the regions a warp's slice holds (a codec's WSLICE_ROUNDS).
-template <int R>
-struct WGeom {
-  static constexpr int ROUNDS = R;                          // regions per warp slice
-  static constexpr uint32_t SLICE = WREGION * R;            // input bytes per warp slice
-  static constexpr uint32_t PART = SLICE * XWARPS;          // input bytes per partition
-  static constexpr int REGIONS = R * XWARPS;                // regions per partition
-  static constexpr int BATCH = R < 4 ? R : 4;               // regions whose loads are in flight together
-  static_assert(R % BATCH == 0 && BATCH % 2 == 0, "the count pass scans two regions at a time");
-};
+constexpr int WROUNDS = (int)(SLICE_BYTES / WREGION); // regions per warp slice
+constexpr int WREGIONS = WROUNDS * XWARPS;            // regions per partition
+static_assert(SLICE_BYTES == WREGION * WROUNDS, "a slice is whole regions");
+static_assert(WROUNDS % 2 == 0, "the count pass scans two regions at a time");
 
-template <int R>
 struct __align__(16) WideCounts {
-  uint16_t lane_off[R * XWARPS][32];  // each lane's exclusive offset inside its region
-  uint32_t rinfo[R * XWARPS];         // region total (bits 0-15) | codec flags << 16
-  uint32_t slice[XWARPS];             // slice total (bits 0-30) | 1 << 31 for an all-ASCII slice inside the buffer
+  uint16_t lane_off[WREGIONS][32];  // each lane's exclusive offset inside its region
+  uint32_t rinfo[WREGIONS];         // region total (bits 0-15) | codec flags << 16
+  uint32_t slice[XWARPS];           // slice total (bits 0-30) | 1 << 31 for an all-ASCII slice inside the buffer
 };
 
 template <class Codec>
 struct __align__(128) WSmem {
   typename Codec::Out staging[XWARPS][2][Codec::WSTAGE];
-  WideCounts<Codec::WSLICE_ROUNDS> counts[2];
+  WideCounts counts[2];
   LookbackSmem<XT> lb;
   unsigned long long red[XWARPS];
   uint32_t ticket;
@@ -99,62 +89,47 @@ __device__ __forceinline__ void load32(const Params &p, long long c, bool inside
 }
 
 // Virtual position of lane `lane`'s 32 bytes in region r of warp w's slice of partition part.
-template <class G>
 __device__ __forceinline__ long long wchunk_pos(uint32_t part, int w, int r, int lane) {
-  return (long long)part * G::PART + (long long)w * G::SLICE + (long long)r * WREGION + (long long)lane * WLANE;
-}
-
-// Whether partition `part` lies inside the buffer with a word to spare at each end.
-template <class G>
-__device__ __forceinline__ bool wpart_inside(const Params &p, uint32_t part) {
-  const long long p0 = (long long)part * G::PART;
-  return p0 - 4 >= (long long)p.off0 && p0 + (long long)G::PART + 4 <= (long long)p.vbytes;
+  return (long long)part * PART_BYTES + (long long)w * SLICE_BYTES + (long long)r * WREGION +
+         (long long)lane * WLANE;
 }
 
 // Counts partition `part` into pc (all threads; the caller puts a barrier after it).  INSIDE:
 // the partition lies inside the buffer with a word to spare at each end.
 template <class Codec, bool INSIDE>
-__device__ __forceinline__ void wcount_partition(const Params &p, uint32_t part,
-                                                 WideCounts<Codec::WSLICE_ROUNDS> &pc) {
-  using G = WGeom<Codec::WSLICE_ROUNDS>;
+__device__ __forceinline__ void wcount_partition(const Params &p, uint32_t part, WideCounts &pc) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const long long s0 = wchunk_pos<G>(part, warp, 0, 0);
+  const long long s0 = wchunk_pos(part, warp, 0, 0);
   const long long lo = p.off0, hi = (long long)p.vbytes;
-  const bool inside = INSIDE || (s0 >= lo && s0 + (long long)G::SLICE <= hi);
+  const bool inside = INSIDE || (s0 >= lo && s0 + (long long)SLICE_BYTES <= hi);
   // the slice is read again by its conversion one partition later: keep it in L2
   const uint64_t keep = l2_policy_keep();
-  uint32_t stot = 0, any_slice = 0;
+  uint32_t v[WROUNDS][8];
 #pragma unroll
-  for (int b = 0; b < G::ROUNDS; b += G::BATCH) {
-    uint32_t v[G::BATCH][8];
+  for (int r = 0; r < WROUNDS; ++r) load32(p, s0 + (long long)r * WREGION + WLANE * lane, inside, keep, v[r]);
+  bool slice_ascii = false;
+  if (INSIDE) {
+    uint32_t any = 0;
 #pragma unroll
-    for (int r = 0; r < G::BATCH; ++r)
-      load32(p, s0 + (long long)(b + r) * WREGION + WLANE * lane, inside, keep, v[r]);
-    bool batch_ascii = false;
-    if (INSIDE) {
-      uint32_t any = 0;
+    for (int r = 0; r < WROUNDS; ++r)
 #pragma unroll
-      for (int r = 0; r < G::BATCH; ++r)
+      for (int k = 0; k < 8; ++k) any |= v[r][k];
+    slice_ascii = __all_sync(0xffffffffu, (any & Codec::ASCII_MASK) == 0);
+  }
+  uint32_t stot = 0;
+  if (slice_ascii) {
+    // every lane gives LANE_UNITS units: no scan needed
 #pragma unroll
-        for (int k = 0; k < 8; ++k) any |= v[r][k];
-      any_slice |= any;
-      batch_ascii = __all_sync(0xffffffffu, (any & Codec::ASCII_MASK) == 0);
-    }
-    if (batch_ascii) {
-      // every lane gives LANE_UNITS units: no scan needed
+    for (int r = 0; r < WROUNDS; ++r) pc.lane_off[warp * WROUNDS + r][lane] = (uint16_t)(lane * Codec::LANE_UNITS);
+    if (lane < WROUNDS) pc.rinfo[warp * WROUNDS + lane] = Codec::WREGION_UNITS;
+    stot = WROUNDS * Codec::WREGION_UNITS;
+  } else {
 #pragma unroll
-      for (int r = 0; r < G::BATCH; ++r)
-        pc.lane_off[warp * G::ROUNDS + b + r][lane] = (uint16_t)(lane * Codec::LANE_UNITS);
-      if (lane < G::BATCH) pc.rinfo[warp * G::ROUNDS + b + lane] = Codec::WREGION_UNITS;
-      stot += G::BATCH * Codec::WREGION_UNITS;
-      continue;
-    }
-#pragma unroll
-    for (int r = 0; r < G::BATCH; r += 2) {
+    for (int r = 0; r < WROUNDS; r += 2) {
       uint32_t a[2], f[2];
 #pragma unroll
       for (int q = 0; q < 2; ++q) {
-        const long long c = s0 + (long long)(b + r + q) * WREGION + WLANE * lane;
+        const long long c = s0 + (long long)(r + q) * WREGION + WLANE * lane;
         const bool edge = !inside && (c < lo || c + (long long)WLANE > hi);
         a[q] = Codec::wcount(p, v[r + q], c, edge, f[q]);
       }
@@ -173,7 +148,7 @@ __device__ __forceinline__ void wcount_partition(const Params &p, uint32_t part,
         }
       }
       const uint32_t ex = incl - x;
-      const int ri = warp * G::ROUNDS + b + r;
+      const int ri = warp * WROUNDS + r;
       pc.lane_off[ri][lane] = (uint16_t)(ex & 0xFFFFu);
       pc.lane_off[ri + 1][lane] = (uint16_t)(ex >> 16);
       const uint32_t fr0 = __reduce_or_sync(0xffffffffu, f[0]), fr1 = __reduce_or_sync(0xffffffffu, f[1]);
@@ -184,26 +159,23 @@ __device__ __forceinline__ void wcount_partition(const Params &p, uint32_t part,
       stot += (incl & 0xFFFFu) + (incl >> 16);  // meaningful in lane 31
     }
   }
-  const bool slice_ascii = INSIDE && __all_sync(0xffffffffu, (any_slice & Codec::ASCII_MASK) == 0);
   if (lane == 31) pc.slice[warp] = stot | (slice_ascii ? 0x80000000u : 0u);
 }
 
 // Step 3 for partition `part` (all threads; each warp on its slice): transcodes the
 // partition, whose output starts at unit S0, with the counts of its count pass in pc.
 template <class Codec, bool INSIDE>
-__device__ __forceinline__ void wconvert_partition(const Params &p, uint32_t part,
-                                                   const WideCounts<Codec::WSLICE_ROUNDS> &pc, uint64_t S0,
+__device__ __forceinline__ void wconvert_partition(const Params &p, uint32_t part, const WideCounts &pc, uint64_t S0,
                                                    WSmem<Codec> &sm, uint32_t &use, unsigned long long &err_pos) {
-  using G = WGeom<Codec::WSLICE_ROUNDS>;
   using Out = typename Codec::Out;
   constexpr uint32_t V = 16 / sizeof(Out);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const long long lo = p.off0, hi = (long long)p.vbytes;
-  const long long s0 = wchunk_pos<G>(part, warp, 0, 0);
-  const bool slice_inside = INSIDE || (s0 - 4 >= lo && s0 + (long long)G::SLICE + 4 <= hi);
+  const long long s0 = wchunk_pos(part, warp, 0, 0);
+  const bool slice_inside = INSIDE || (s0 - 4 >= lo && s0 + (long long)SLICE_BYTES + 4 <= hi);
   const uint32_t before = slice_inside ? ldg_word(p.base + s0 - 4) : load_word_checked(p, s0 - 4);
   const uint32_t after =
-      slice_inside ? ldg_word(p.base + s0 + G::SLICE) : load_word_checked(p, s0 + G::SLICE);
+      slice_inside ? ldg_word(p.base + s0 + SLICE_BYTES) : load_word_checked(p, s0 + SLICE_BYTES);
   // the slice's first output unit inside the partition: the totals of the slices before it
   uint32_t sbase = 0;
 #pragma unroll
@@ -220,26 +192,23 @@ __device__ __forceinline__ void wconvert_partition(const Params &p, uint32_t par
   const uint64_t last_use = l2_policy_last_use();
   const uint8_t *const src = p.base + s0 + WLANE * lane;  // the lane's 32 bytes of region 0
   if (INSIDE && (sinfo >> 31) && ((uint32_t)D0 & (Codec::WDIRECT_ALIGN - 1)) == 0 &&
-      room0 >= (uint32_t)G::ROUNDS * Codec::WREGION_UNITS) {
+      room0 >= (uint32_t)WROUNDS * Codec::WREGION_UNITS) {
     // an all-ASCII slice whose output is aligned and fits: every region goes straight to
     // global memory; only the word before the slice can hold a leading byte that wants
     // continuation bytes in it
+    uint32_t w[WROUNDS][8];
 #pragma unroll
-    for (int b = 0; b < G::ROUNDS; b += G::BATCH) {
-      uint32_t w[G::BATCH][8];
+    for (int r = 0; r < WROUNDS; ++r) ldg32_hint(src + r * WREGION, last_use, w[r]);
 #pragma unroll
-      for (int r = 0; r < G::BATCH; ++r) ldg32_hint(src + (b + r) * WREGION, last_use, w[r]);
-#pragma unroll
-      for (int r = 0; r < G::BATCH; ++r)
-        Codec::wascii_direct(dslice + (b + r) * Codec::WREGION_UNITS, w[r], b + r == 0 ? before : 0u,
-                             s0 + (long long)(b + r) * WREGION + WLANE * lane, err_pos);
-    }
+    for (int r = 0; r < WROUNDS; ++r)
+      Codec::wascii_direct(dslice + r * Codec::WREGION_UNITS, w[r], r == 0 ? before : 0u,
+                           s0 + (long long)r * WREGION + WLANE * lane, err_pos);
     return;
   }
   uint32_t prev_last = before;  // last word of the previous region (lane 31's), for lane 0
   uint32_t off = 0;             // the region's first unit inside the slice's output
 #pragma unroll 1
-  for (int r = 0; r < G::ROUNDS; ++r) {
+  for (int r = 0; r < WROUNDS; ++r) {
     const long long c = s0 + (long long)r * WREGION + WLANE * lane;
     const bool edge = !INSIDE && (c < lo || c + (long long)WLANE > hi);
     // the lane's 32 bytes (other warps cover the L2 latency; a load kept a region ahead would
@@ -248,7 +217,7 @@ __device__ __forceinline__ void wconvert_partition(const Params &p, uint32_t par
     uint32_t v[8];
     load32(p, c, slice_inside, last_use, v);
     uint32_t next_first = after;
-    if (lane == 31 && r + 1 < G::ROUNDS)
+    if (lane == 31 && r + 1 < WROUNDS)
       next_first = slice_inside ? ldg_word(p.base + c + WLANE) : load_word_checked(p, c + WLANE);
     uint32_t prev = __shfl_up_sync(0xffffffffu, v[7], 1);
     uint32_t next = __shfl_down_sync(0xffffffffu, v[0], 1);
@@ -256,7 +225,7 @@ __device__ __forceinline__ void wconvert_partition(const Params &p, uint32_t par
     if (lane == 31) next = next_first;
     prev_last = __shfl_sync(0xffffffffu, v[7], 31);
 
-    const int ri = warp * G::ROUNDS + r;
+    const int ri = warp * WROUNDS + r;
     const uint32_t info = pc.rinfo[ri];
     const uint32_t rtot = info & 0xFFFFu, rflags = info >> 16;
     const uint32_t dlo = (uint32_t)D0 + off;  // low bits of the region's destination unit
@@ -284,22 +253,20 @@ __device__ __forceinline__ void wconvert_partition(const Params &p, uint32_t par
 }
 
 template <class Codec>
-__device__ __forceinline__ void wcount_part(const Params &p, uint32_t part, WideCounts<Codec::WSLICE_ROUNDS> &pc) {
-  if (wpart_inside<WGeom<Codec::WSLICE_ROUNDS>>(p, part)) wcount_partition<Codec, true>(p, part, pc);
+__device__ __forceinline__ void wcount_part(const Params &p, uint32_t part, WideCounts &pc) {
+  if (part_inside(p, part)) wcount_partition<Codec, true>(p, part, pc);
   else wcount_partition<Codec, false>(p, part, pc);
 }
 
 template <class Codec>
-__device__ __forceinline__ void wconvert_part(const Params &p, uint32_t part, const WideCounts<Codec::WSLICE_ROUNDS> &pc,
-                                              uint64_t S0,
+__device__ __forceinline__ void wconvert_part(const Params &p, uint32_t part, const WideCounts &pc, uint64_t S0,
                                               WSmem<Codec> &sm, uint32_t &use, unsigned long long &err_pos) {
-  if (wpart_inside<WGeom<Codec::WSLICE_ROUNDS>>(p, part)) wconvert_partition<Codec, true>(p, part, pc, S0, sm, use, err_pos);
+  if (part_inside(p, part)) wconvert_partition<Codec, true>(p, part, pc, S0, sm, use, err_pos);
   else wconvert_partition<Codec, false>(p, part, pc, S0, sm, use, err_pos);
 }
 
 // The partition's total output (after the barrier that follows its count pass).
-template <int R>
-__device__ __forceinline__ uint32_t wpart_total(const WideCounts<R> &pc) {
+__device__ __forceinline__ uint32_t wpart_total(const WideCounts &pc) {
   uint32_t t = 0;
 #pragma unroll
   for (int w = 0; w < XWARPS; ++w) t += pc.slice[w] & 0x7FFFFFFFu;
@@ -356,7 +323,7 @@ __device__ __forceinline__ void wtranscode(const Params &p, WSmem<Codec> &sm, Fi
     }
     const uint64_t S0 = lookback_cta<XT>(p, cur, cur_total, epoch, sm.lb);
 
-    if ((unsigned long long)cur * WGeom<Codec::WSLICE_ROUNDS>::PART <= known) {  // uniform over the CTA
+    if ((unsigned long long)cur * PART_BYTES <= known) {  // uniform over the CTA
       wconvert_part<Codec>(p, cur, sm.counts[cb], S0, sm, use, err_pos);
       if (p.early_exit && err_pos < published) {  // rare: this thread flagged a new error
         atomicMin(&p.ws->errkey, err_pos);

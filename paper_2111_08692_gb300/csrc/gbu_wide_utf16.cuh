@@ -25,7 +25,6 @@ struct Utf16ToUtf8Wide {
   // a region of 512 words yields at most 1536 bytes, +2 for a pair cut at its end, plus 15
   // bytes of alignment offset
   static constexpr uint32_t WSTAGE = 3 * 512 + 32;
-  static constexpr int WSLICE_ROUNDS = 4;  // 16 KiB partitions
   static_assert(3 * 512 + 2 + 15 + 1 <= WSTAGE, "staging buffer too small");
 
   static constexpr uint32_t F_SUR = Narrow::F_SUR;
@@ -302,13 +301,6 @@ struct Utf16ToUtf8Wide {
     if (err && (unsigned long long)c < err_pos) err_pos = (unsigned long long)c;
     return g;
   }
-};
-
-// The same codec on 32 KiB partitions (eight regions per warp slice), for large inputs: half the
-// partitions' claims, barriers and look-backs per byte, but half as many partitions to spread over
-// the CTAs, so it is used only from WIDE16_LARGE_MIN_UNITS words on.
-struct Utf16ToUtf8WideL : Utf16ToUtf8Wide {
-  static constexpr int WSLICE_ROUNDS = 8;
 };
 
 }  // namespace gbu

@@ -43,7 +43,6 @@ struct Utf8ToUtf16Wide {
   // valid, so a lane's own staging always fits: 32 x 31 + 1 + 64, plus 7 words of alignment
   // offset, <= WSTAGE.  Words past the buffer can only come after the first error.
   static constexpr uint32_t WSTAGE = 1024 + 48;
-  static constexpr int WSLICE_ROUNDS = 4;  // 16 KiB partitions
   static_assert(32 * 31 + 1 + 64 + 7 <= WSTAGE, "staging buffer too small");
 
   static constexpr uint32_t F_NONASCII = Narrow::F_NONASCII;
