@@ -151,3 +151,29 @@ def test_pipe_on_pinned_buffers_with_the_default_pieces():
         assert np.array_equal(dst, odst)
     finally:
         p.close()
+
+
+def test_pipe_refuses_misaligned_and_missing_buffers(pipe):
+    """A UTF-16 source or UTF-16 destination at an odd address, a NULL result, and a NULL
+    destination with cap > 0 are GBU_BAD_ARGUMENT, with nothing written; empty inputs give
+    {OK, 0}."""
+    import ctypes
+    from paper_2111_08692_gb300 import GbuResult, lib
+    L = lib()
+    raw = np.zeros(64, np.uint8)
+    base = raw.ctypes.data
+    odd = base + 1 if base % 2 == 0 else base
+    res = GbuResult()
+    assert L.gbu_pipe_validate_utf16le(pipe.handle, odd, 8, ctypes.byref(res)) == 17
+    assert L.gbu_pipe_utf8_length_from_utf16le(pipe.handle, odd, 8, ctypes.byref(res)) == 17
+    out = np.full(64, CANARY8, np.uint8)
+    assert L.gbu_pipe_convert_utf8_to_utf16le(pipe.handle, base, 8, out.ctypes.data + 1, 8, ctypes.byref(res)) == 17
+    assert np.all(out == CANARY8)
+    assert L.gbu_pipe_convert_utf16le_to_utf8(pipe.handle, base, 8, None, 8, ctypes.byref(res)) == 17
+    assert L.gbu_pipe_validate_utf8(pipe.handle, base, 8, None) == 17
+    assert L.gbu_pipe_validate_utf8(pipe.handle, None, 8, ctypes.byref(res)) == 17
+    for name in ("validate_utf8", "validate_utf16le", "utf16_length_from_utf8", "utf8_length_from_utf16le"):
+        empty = np.zeros(0, np.uint16 if "16le" in name else np.uint8)
+        assert getattr(pipe, name)(empty) == ("OK", 0), name
+    assert pipe.convert_utf8_to_utf16le(np.zeros(0, np.uint8), np.zeros(0, np.uint16)) == ("OK", 0)
+    assert pipe.convert_utf16le_to_utf8(np.zeros(0, np.uint16), np.zeros(0, np.uint8)) == ("OK", 0)
